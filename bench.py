@@ -1,0 +1,412 @@
+#!/usr/bin/env python3
+"""Benchmark of the M-HDC SpMV library on one GB300 (or N replicas).
+
+One step = one y = A x with the M-HDC kernel (mhdc_spmv) on the 27-point
+stencil matrix of a 128^3 grid (2,097,152 rows, ~39.9M nonzeros, FP64) with
+partial diagonal structure (each off-centre offset dropped in a random 30% of
+4096-row blocks, 2 random off-band entries in 1% of rows), built with
+n_b = 4096 and theta = 0.6.  The matrix is converted once before timing.
+The metric is the paper's P = 2 nnz / T (Eq. 1) in GFLOP/s; beside it the
+same line reports the plain FP64 CSR kernel and the HDC (B-HDC) kernel on the
+same matrix and GPU, the achieved HBM bandwidth against the measured peak,
+the end-to-end rate through host buffers, and the CPU oracle's rate.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica (independent problems,
+no exchange): value = total flops of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "M-HDC SpMV GFLOP/s and % HBM peak vs plain FP64 CSR, same GB300, stated tol"
+WORKLOAD = ("stencil27_128: 27-point 3D stencil on a 128^3 grid (2,097,152 rows, FP64 values), "
+            "each off-centre offset dropped in a random 30% of 4096-row blocks, 2 uniform-random "
+            "off-band entries in 1% of rows, seed 1; M-HDC n_b=4096, theta=0.6")
+N_B, THETA = 4096, 0.6
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="time only the M-HDC kernel (profiling runs)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        sm, smax, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                pw.append(float(r[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples under load: the upper half of the observed clock values
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
+
+
+def gflops(nnz, sec):
+    return 2.0 * nnz / sec / 1e9
+
+
+def time_launches(fn, steps, warmup, stream, torch):
+    """K back-to-back launches: total time over the region and the mean of
+    per-launch event durations (both on the launching stream)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    per = [a.elapsed_time(b) for a, b in ev]
+    return total_ms, float(np.mean(per)), float(np.median(per))
+
+
+def cpu_baseline(A, budget_s, log):
+    """The oracle's M-HDC product (plain C, OpenMP over row blocks), as it
+    stands, on all host cores, on a bounded number of full products."""
+    import oracle
+    M = oracle.convert(A, N_B, THETA, "f64")
+    prep = oracle.Prepared(M)
+    x = np.ascontiguousarray(np.linspace(-1, 1, A.n))
+    y = np.empty(A.n)
+    nb = (A.n + N_B - 1) // N_B
+    prep.spmv_blocks(x, y, 0, nb)  # warm-up
+    reps, t0 = 0, time.perf_counter()
+    best = float("inf")
+    while True:
+        s = time.perf_counter()
+        prep.spmv_blocks(x, y, 0, nb)
+        best = min(best, time.perf_counter() - s)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s or reps >= 2000:
+            break
+    el = time.perf_counter() - t0
+    log(f"cpu oracle: {reps} products in {el:.2f}s")
+    return {"value": round(gflops(A.nnz, el / reps), 3), "unit": "GFLOP/s",
+            "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{reps} full products of the same matrix (mean; best {gflops(A.nnz, best):.3f})",
+            "cpu": _cpu_model()}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return os.uname().machine
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on this machine's host
+    cores, for the same workload and metric; each step is a bounded sample
+    (a contiguous range of row blocks) of one product."""
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            dist.destroy_process_group()
+            return
+    import oracle
+    import synth
+    A = synth.config_matrix("stencil27_128")
+    M = oracle.convert(A, N_B, THETA, "f64")
+    prep = oracle.Prepared(M)
+    nb = (A.n + N_B - 1) // N_B
+    x = np.ascontiguousarray(np.linspace(-1, 1, A.n))
+    y = np.empty(A.n)
+    s = time.perf_counter()
+    prep.spmv_blocks(x, y, 0, nb)
+    t_full = time.perf_counter() - s
+    budget = 120.0
+    frac = min(1.0, budget / max(1e-9, (args.steps + args.warmup) * t_full))
+    blocks = max(1, int(nb * frac))
+    rp = A.row_ptr
+    nnz_sample = int(rp[min(A.n, blocks * N_B)] - rp[0])
+    for _ in range(args.warmup):
+        prep.spmv_blocks(x, y, 0, blocks)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        prep.spmv_blocks(x, y, 0, blocks)
+    el = time.perf_counter() - t0
+    ms = el / args.steps * 1e3
+    val = gflops(nnz_sample, el / args.steps)
+    cores = oracle.max_threads()
+    sample = (f"row blocks [0, {blocks}) of {nb} ({nnz_sample} nonzeros) per step, "
+              "FP64 oracle M-HDC product")
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "GFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "n_b": N_B, "theta": THETA,
+                       "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": round(val, 4), "unit": "GFLOP/s", "cores": cores,
+                             "kind": "oracle", "sample": sample, "cpu": _cpu_model()},
+            "e2e": {"value": round(val, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def log(msg):
+        if rank == 0:
+            print(msg, file=sys.stderr, flush=True)
+
+    import paper_2105_04937_gb300 as mh
+    import synth
+    mh.lib()
+    stream = torch.cuda.current_stream()
+
+    A = synth.config_matrix("stencil27_128")
+    rp = torch.from_numpy(A.row_ptr).cuda()
+    col = torch.from_numpy(A.col).cuda()
+    val = torch.from_numpy(A.val).cuda()
+    x_host = synth.uniform_vector(A.n, 1)
+    x = torch.from_numpy(x_host).cuda()
+    y = torch.empty(A.n, dtype=torch.float64, device="cuda")
+
+    torch.cuda.synchronize()
+    tb = time.perf_counter()
+    H = mh.mhdc_build(A.n, rp, col, val, N_B, THETA, "f64")
+    build_ms = (time.perf_counter() - tb) * 1e3
+    info = H.info
+    log(f"built: P={info['P']} nnz_rem={info['nnz_rem']} alpha={info['alpha']:.3f} "
+        f"beta={info['beta']:.4f} bytes_model={info['bytes_model']} in {build_ms:.1f} ms")
+
+    peak, peak_src = measured_peak()
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    sampler = ClockSampler(vis[local].strip() if local < len(vis) else local)
+    if rank == 0:
+        sampler.start()
+
+    # ---- the timed region: K steps of mhdc_spmv
+    def step():
+        mh.mhdc_spmv(H, x, y, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler.mark("t0")
+    ev0.record(stream)
+    for a, b in evs:
+        a.record(stream)
+        step()
+        b.record(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark("t1")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = ev0.elapsed_time(ev1)
+    kern_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    clocks = sampler.stop() if rank == 0 else None
+
+    ms_step = total_ms / args.steps
+    value = gflops(A.nnz, ms_step / 1e3) * ws
+    achieved = info["bytes_model"] / (kern_ms / 1e3) / 1e9
+
+    extra = {}
+    if not args.skip_extra:
+        # plain FP64 CSR on the same matrix and GPU (Fig. 2)
+        def csr_step():
+            mh.csr_spmv(A.n, rp, col, val, x, y, stream)
+        tot, mean, _ = time_launches(csr_step, min(args.steps, 5000), args.warmup, stream, torch)
+        csr_bytes = 12 * A.nnz + 4 * (A.n + 1) + 16 * A.n
+        extra["csr_fp64"] = {"gflops": round(gflops(A.nnz, mean / 1e3), 2),
+                             "gbs": round(csr_bytes / (mean / 1e3) / 1e9, 1),
+                             "hbm_frac": round(csr_bytes / (mean / 1e3) / 1e9 / peak, 4),
+                             "kernel_us": round(mean * 1e3, 2), "bytes": csr_bytes}
+        # HDC (global selection, B-HDC kernel) on the same matrix (Sec. 3.4, Fig. 10)
+        Hh = mh.hdc_build(A.n, rp, col, val, N_B, THETA, "f64")
+        ih = Hh.info
+
+        def hdc_step():
+            mh.mhdc_spmv(Hh, x, y, stream)
+        tot, mean, _ = time_launches(hdc_step, min(args.steps, 5000), args.warmup, stream, torch)
+        extra["hdc_fp64"] = {"gflops": round(gflops(A.nnz, mean / 1e3), 2),
+                             "gbs": round(ih["bytes_model"] / (mean / 1e3) / 1e9, 1),
+                             "kernel_us": round(mean * 1e3, 2), "bytes": ih["bytes_model"],
+                             "alpha": round(ih["alpha"], 4), "beta": round(ih["beta"], 4)}
+        Hh.destroy()
+        extra["mhdc_vs_csr_speedup"] = round(extra["csr_fp64"]["kernel_us"] / (kern_ms * 1e3), 3)
+
+    # ---- end to end through the host-buffer entry point (pinned memory)
+    xh = torch.from_numpy(x_host).pin_memory()
+    yh = torch.empty(A.n, dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 200))
+    for _ in range(3):
+        mh.mhdc_spmv_host(H, xh, yh, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        mh.mhdc_spmv_host(H, xh, yh, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e = {"value": round(gflops(A.nnz, e2e_ms / 1e3) * ws, 3), "unit": "GFLOP/s",
+           "h2d_bytes_per_step": 8 * A.n, "d2h_bytes_per_step": 8 * A.n,
+           "ms_per_step": round(e2e_ms, 4), "steps": e2e_steps,
+           "api": "mhdc_spmv_host (x pinned host -> device, product, y device -> pinned host)"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(A, args.cpu_seconds, log)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "n_b": N_B, "theta": THETA,
+                       "P": info["P"], "nnz_rem": info["nnz_rem"],
+                       "alpha": round(info["alpha"], 4), "beta": round(info["beta"], 5),
+                       "l2": "inputs larger than L2 (M-HDC arrays "
+                             f"{info['bytes_model'] / 1e6:.0f} MB > 129 MB L2); no flush",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": None, "kernel": "k_mhdc_spmv<double,2,true>",
+                         "bytes_per_launch": info["bytes_model"],
+                         "kernel_us": round(kern_ms * 1e3, 3), "peak_source": peak_src},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "build_ms": round(build_ms, 1),
+            "baselines": extra,
+        }
+        print(json.dumps(line), flush=True)
+    H.destroy()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * mhdc.h -- C ABI of the M-HDC sparse matrix-vector library (sm_103a).
+ *
+ * Method: Fukaya, Ishida, Miura, Iwashita, Nakashima, "Accelerating the SpMV
+ * kernel on standard CPUs by exploiting the partially diagonal structures"
+ * (arXiv 2105.04937).  The product is y = A x for an n x n real sparse A
+ * (Sec. 3.1).  In the M-HDC format (Sec. 4.3, Figs. 11-12) the rows are cut
+ * into blocks of n_b rows (the paper's "bl"); inside each block the partial
+ * diagonals that are dense enough are stored DIA-style (one offset and n_b
+ * contiguous values each) and every other nonzero goes to a CSR remainder.
+ *
+ * Conventions for every call:
+ *   - Indices are zero-based int32, sizes int64.  A diagonal's offset is
+ *     off = j - i (the kernels of Figs. 5, 9, 10, 13 read x[i + off]).
+ *   - Pointers named d_* are device pointers on the current CUDA device;
+ *     pointers named h_* are host pointers.  `stream` is a cudaStream_t (NULL
+ *     for the legacy default stream).
+ *   - The caller keeps ownership of every array it passes; a handle owns the
+ *     device arrays it holds and frees them in mhdc_destroy.
+ *   - Calls return MHDC_OK (0) or a negative error code; nothing throws across
+ *     the ABI.  mhdc_strerror() names a code.
+ *   - Value dtype is fixed per handle: F64 handles take FP64 x and write FP64
+ *     y; F32 handles take FP32 x and write FP32 y; BF16 handles take BF16 x
+ *     and write FP32 y.  Accumulation is FP64 for F64 and FP32 otherwise.
+ */
+#ifndef MHDC_H
+#define MHDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mhdc_matrix *mhdc_handle;
+
+/* Storage precision of matrix values and x. */
+enum mhdc_dtype { MHDC_F64 = 0, MHDC_F32 = 1, MHDC_BF16 = 2 };
+
+/* Which diagonals go to the DIA part (see mhdc_build / hdc_build). */
+enum mhdc_mode { MHDC_MODE_BLOCK = 0, MHDC_MODE_GLOBAL = 1 };
+
+enum mhdc_status {
+    MHDC_OK = 0,
+    MHDC_ERR_INVALID_ARG = -1,   /* bad size, null pointer, unknown dtype, ... */
+    MHDC_ERR_BAD_CSR = -2,       /* CSR input fails the checks of mhdc_build */
+    MHDC_ERR_OOM = -3,           /* a device allocation failed */
+    MHDC_ERR_CUDA = -4,          /* a CUDA runtime call or launch failed */
+    MHDC_ERR_UNSUPPORTED = -5,   /* valid request this build does not handle */
+    MHDC_ERR_DEVICE_CHECK = -6,  /* a kernel's own bounds check fired */
+    MHDC_ERR_TIMEOUT = -7        /* a bounded device-side wait gave up */
+};
+
+/* Summary of a built handle (mhdc_info). */
+typedef struct {
+    int64_t n;             /* rows = columns */
+    int64_t nnz;           /* stored entries of the input CSR */
+    int64_t nnz_rem;       /* entries in the CSR remainder */
+    int64_t P;             /* number of partial diagonals (sum over blocks) */
+    int64_t n_blocks;      /* ceil(n / n_b) */
+    int32_t n_b;           /* rows per block */
+    int32_t dtype;         /* enum mhdc_dtype */
+    int32_t mode;          /* enum mhdc_mode */
+    int32_t reserved;
+    double theta;          /* density threshold used */
+    double alpha;          /* filling rate: (nnz - nnz_rem) / (P * n_b)   (Sec. 5.3.3) */
+    double beta;           /* CSR rate: nnz_rem / nnz                     (Sec. 5.3.1) */
+    int64_t bytes_model;   /* algorithmic bytes of one y = A x: V_A + V_x + V_y (Sec. 5.1),
+                              x read once; csr_row_ptr counted for blocks with a
+                              nonempty remainder plus two words per block */
+    int64_t bytes_device;  /* device memory held by the handle */
+} mhdc_info_t;
+
+/*
+ * mhdc_build -- convert a CSR matrix to M-HDC (Sec. 4.3; selection rule of
+ * Sec. 4.3, storage of Fig. 12), entirely on the device.
+ *
+ *   n            rows (= columns), 0 <= n < 2^31 - 1
+ *   d_row_ptr    int32[n + 1], row_ptr[0] = 0, nondecreasing, row_ptr[n] = nnz < 2^31
+ *   d_col        int32[nnz], columns of each row strictly increasing, in [0, n)
+ *   d_val        double[nnz]
+ *   n_b          rows per block, >= 1 (the paper's bl)
+ *   theta        density threshold, finite and >= 0: in block ib the partial
+ *                diagonal of offset d is kept iff its count N(d, ib) >= 1 and
+ *                (double)N >= theta * rows(ib), rows(ib) = min(n_b, n - ib*n_b)
+ *   dtype        enum mhdc_dtype: values are rounded to it once, at build
+ *                (FP64 -> FP32 nearest-even, then FP32 -> BF16 nearest-even)
+ *   stream       stream to run on; the call synchronizes it (sizes are read back)
+ *   out          receives the new handle (unchanged on error)
+ *
+ * The input arrays are only read and may be freed after the call.  Invalid
+ * CSR (decreasing row_ptr, column out of range, unsorted or duplicate columns)
+ * returns MHDC_ERR_BAD_CSR and builds nothing.  Layout built (device):
+ * dia_ptr int32[n_blocks + 1]; dia_offset int32[P], ascending inside a block;
+ * dia_val dtype[P * n_b] with dia_val[p * n_b + t] = a(r0 + t, r0 + t + off_p)
+ * (+0.0 where that entry is absent or outside the matrix); remainder
+ * csr_row_ptr int32[n + 1], csr_col int32[nnz_rem], csr_val dtype[nnz_rem] in
+ * the input's order.
+ */
+int mhdc_build(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+               int32_t n_b, double theta, int32_t dtype, void *stream, mhdc_handle *out);
+
+/*
+ * hdc_build -- the HDC format (Sec. 3.4) stored blocked for the B-HDC kernel
+ * (Sec. 4.2, Fig. 10): diagonals are chosen over the whole matrix (count
+ * N(d) >= 1 and >= theta * n) and every block of n_b rows holds its piece of
+ * each chosen diagonal.  Arguments, layout and errors as mhdc_build; the
+ * handle works with every other call.
+ */
+int hdc_build(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+              int32_t n_b, double theta, int32_t dtype, void *stream, mhdc_handle *out);
+
+/*
+ * mhdc_spmv -- y = A x with the M-HDC kernel (Fig. 13): for every row block,
+ * the remainder rows plus, for each of the block's diagonals, dia_val * x
+ * shifted by its offset; y is written once per row (overwritten).
+ *
+ *   d_x   n values of the handle's x dtype (device)
+ *   d_y   n values of the handle's y dtype (device); must not overlap d_x
+ * Asynchronous on `stream`.
+ */
+int mhdc_spmv(mhdc_handle A, const void *d_x, void *d_y, void *stream);
+
+/*
+ * mhdc_spmv_host -- mhdc_spmv on host buffers: copies h_x (n values, pinned
+ * host memory recommended) to a device buffer owned by the handle, runs the
+ * product and copies y back to h_y, all on `stream`, then synchronizes it.
+ */
+int mhdc_spmv_host(mhdc_handle A, const void *h_x, void *h_y, void *stream);
+
+/*
+ * mhdc_spmm -- Y = A X for k right-hand sides (the M-HDC kernel of Fig. 13
+ * applied to k vectors at once, reading A once).
+ *
+ *   k        number of right-hand sides, 1 <= k <= 64
+ *   d_X      row-major n x k block of x dtype, leading dimension ldx >= k
+ *   d_Y      row-major n x k block of y dtype, leading dimension ldy >= k
+ * Asynchronous on `stream`.
+ */
+int mhdc_spmm(mhdc_handle A, int32_t k, const void *d_X, int64_t ldx, void *d_Y, int64_t ldy,
+              void *stream);
+
+/*
+ * csr_spmv -- the plain FP64 CSR kernel (Sec. 3.2, Fig. 2): y[i] =
+ * sum_k val[k] x[col[k]] over row i.  Arrays as mhdc_build's input (not
+ * checked here); d_x, d_y double[n].  Asynchronous on `stream`.
+ */
+int csr_spmv(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+             const double *d_x, double *d_y, void *stream);
+
+/*
+ * mhdc_export -- copy a handle's arrays to host memory (for parity checks).
+ * Any pointer may be NULL to skip that array.  Sizes from mhdc_info:
+ * dia_ptr int32[n_blocks + 1], dia_offset int32[P], dia_val dtype[P * n_b],
+ * csr_row_ptr int32[n + 1], csr_col int32[nnz_rem], csr_val dtype[nnz_rem].
+ * Synchronous.
+ */
+int mhdc_export(mhdc_handle A, int32_t *h_dia_ptr, int32_t *h_dia_offset, void *h_dia_val,
+                int32_t *h_csr_row_ptr, int32_t *h_csr_col, void *h_csr_val);
+
+/* mhdc_info -- fill *out with the handle's sizes and statistics. */
+int mhdc_info(mhdc_handle A, mhdc_info_t *out);
+
+/* mhdc_destroy -- free the handle and its device arrays (NULL is a no-op). */
+int mhdc_destroy(mhdc_handle A);
+
+/* mhdc_strerror -- static text for a status code. */
+const char *mhdc_strerror(int code);
+
+/* mhdc_last_error -- details of the last failed call on this host thread
+ * (which call or kernel, and the CUDA error text); "" if none yet. */
+const char *mhdc_last_error(void);
+
+/*
+ * mhdc_stream_bench -- the paper's memory benchmarks (Sec. 6.2, Figs. 19-20)
+ * on the device: C[i] += A[i] * B[i] (indirect == 0) or C[i] += A[i] * B[I[i]]
+ * (indirect != 0), FP64 arrays of N elements and an int32 index array.
+ * Used to measure the effective bandwidth w_mem of Eq. (2).  Asynchronous.
+ */
+int mhdc_stream_bench(int64_t N, const double *d_A, const double *d_B, const int32_t *d_I,
+                      double *d_C, int32_t indirect, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MHDC_H */

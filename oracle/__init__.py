@@ -5,8 +5,7 @@ benchmark's CPU-baseline leg, never by the product package, and sharing no
 code with it.  All arithmetic is FP64 in plain C (see mhdc_oracle.c for the
 paper passages each function follows); this module only marshals arrays.
 
-Also here (plain numpy, FP64): the per-row error bounds used as tolerances,
-and the selector network's forward and backward pass (``mlp_*``).
+Also here (plain numpy, FP64): the per-row error bounds used as tolerances.
 """
 from __future__ import annotations
 
@@ -68,6 +67,7 @@ def _declare(L):
         "orc_fill": (I64, [I64, P, P, P, I64, C.c_int, P, P, P, P, P, P]),
         "orc_hdc_global": (I64, [I64, P, P, P, D, P, I64, P, P, P, P, P]),
         "orc_mhdc_spmv": (None, [I64, I64, P, P, P, P, P, P, P, P, C.c_int]),
+        "orc_mhdc_spmv_range": (None, [I64, I64, I64, I64, P, P, P, P, P, P, P, P, C.c_int]),
         "orc_mhdc_to_coo": (I64, [I64, I64, P, P, P, P, P, P, I64, P, P, P]),
         "orc_mhdc_absrow": (None, [I64, I64, P, P, P, P, P, P, P, P, P]),
         "orc_stream_direct": (None, [I64, P, P, P]),
@@ -184,11 +184,11 @@ def widen(a, dtype: str) -> np.ndarray:
 def select(A, bl: int, theta: float, mode: str = "block"):
     n_blocks = (A.n + bl - 1) // bl
     dia_ptr = np.zeros(n_blocks + 1, dtype=np.int32)
-    cap = max(1, A.nnz) if mode == "block" else None
-    if mode == "global":
-        # every block gets the same list of at most (2n - 1) offsets
-        cap_g = max(1, min(2 * A.n - 1, A.nnz))
-        cap = cap_g * n_blocks
+    cap = max(1, A.nnz)
+    if mode == "global" and n_blocks > 1:
+        # every block gets the same list: size it from the single-block call
+        _, one = select(A, max(1, A.n), theta, "global")
+        cap = max(1, one.size * n_blocks)
     dia_offset = np.zeros(cap, dtype=np.int32)
     Pt = lib().orc_select(A.n, _p(_i32(A.row_ptr)), _p(_i32(A.col) if A.nnz else
                                                       np.zeros(1, np.int32)),
@@ -255,6 +255,22 @@ def mhdc_spmv(M: dict, x, nthreads: int = 0) -> np.ndarray:
     lib().orc_mhdc_spmv(M["n"], M["bl"], _p(_i32(M["dia_ptr"])), _p(do), _p(dv),
                         _p(_i32(M["csr_row_ptr"])), _p(cc), _p(cv), _p(x), _p(y), nthreads)
     return y
+
+
+class Prepared:
+    """An M-HDC structure with its arrays widened to FP64 once, for repeated
+    timed products (the CPU baseline)."""
+
+    def __init__(self, M: dict):
+        self.M = M
+        self.dv, self.cv, self.cc, self.do = _wide_arrays(M)
+        self.dp = _i32(M["dia_ptr"])
+        self.crp = _i32(M["csr_row_ptr"])
+
+    def spmv_blocks(self, x, y, ib_begin: int, ib_end: int, nthreads: int = 0):
+        lib().orc_mhdc_spmv_range(self.M["n"], self.M["bl"], ib_begin, ib_end, _p(self.dp),
+                                  _p(self.do), _p(self.dv), _p(self.crp), _p(self.cc),
+                                  _p(self.cv), _p(x), _p(y), nthreads)
 
 
 def mhdc_to_coo(M: dict):

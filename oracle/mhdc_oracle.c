@@ -362,21 +362,22 @@ int64_t orc_hdc_global(int64_t n, const int32_t *row_ptr, const int32_t *col, co
 }
 
 /* ------------------------------------------------------------------------ */
-/* The M-HDC kernel (Fig. 13), FP64.  Per block: the CSR rows of the block
- * first (y[i] = s), then y[i] += dia_val[k][i - r0] * x[i + off] over the
- * block's diagonals k, for the rows i of the block with 0 <= i + off < n.
- * Reduced-precision handles are evaluated here on their stored values
- * widened to FP64. */
-void orc_mhdc_spmv(int64_t n, int64_t bl, const int32_t *dia_ptr, const int32_t *dia_offset,
-                   const double *dia_val, const int32_t *csr_row_ptr, const int32_t *csr_col,
-                   const double *csr_val, const double *x, double *y, int nthreads)
+/* The M-HDC kernel (Fig. 13), FP64, over the row blocks [ib_begin, ib_end).
+ * Per block: the CSR rows of the block first (y[i] = s), then
+ * y[i] += dia_val[k][i - r0] * x[i + off] over the block's diagonals k, for
+ * the rows i of the block with 0 <= i + off < n.  Reduced-precision handles
+ * are evaluated here on their stored values widened to FP64. */
+void orc_mhdc_spmv_range(int64_t n, int64_t bl, int64_t ib_begin, int64_t ib_end,
+                         const int32_t *dia_ptr, const int32_t *dia_offset,
+                         const double *dia_val, const int32_t *csr_row_ptr,
+                         const int32_t *csr_col, const double *csr_val, const double *x,
+                         double *y, int nthreads)
 {
-    int64_t n_blocks = (n + bl - 1) / bl;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(static)
 #endif
-    for (int64_t ib = 0; ib < n_blocks; ib++) {
+    for (int64_t ib = ib_begin; ib < ib_end; ib++) {
         int64_t r0 = ib * bl, r1 = r0 + rows_of_block(n, bl, ib);
         for (int64_t i = r0; i < r1; i++) {
             double s = 0.0;
@@ -392,6 +393,14 @@ void orc_mhdc_spmv(int64_t n, int64_t bl, const int32_t *dia_ptr, const int32_t 
                 y[i] += dia_val[k * bl + (i - r0)] * x[i + off];
         }
     }
+}
+
+void orc_mhdc_spmv(int64_t n, int64_t bl, const int32_t *dia_ptr, const int32_t *dia_offset,
+                   const double *dia_val, const int32_t *csr_row_ptr, const int32_t *csr_col,
+                   const double *csr_val, const double *x, double *y, int nthreads)
+{
+    orc_mhdc_spmv_range(n, bl, 0, (n + bl - 1) / bl, dia_ptr, dia_offset, dia_val, csr_row_ptr,
+                        csr_col, csr_val, x, y, nthreads);
 }
 
 /* Round trip: list the nonzero entries held by an M-HDC structure (DIA

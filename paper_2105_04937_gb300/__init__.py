@@ -1,0 +1,277 @@
+"""Python binding of the M-HDC SpMV library (include/mhdc.h).
+
+Argument marshalling only: every function passes device pointers (from torch
+tensors), sizes and the current CUDA stream to the C ABI of the same name;
+every step of the computation runs in the library's sm_103a kernels.  There
+is no CPU path: if the compiled library is missing, or no GPU is present, the
+compute calls raise.
+
+Method: Fukaya et al., "Accelerating the SpMV kernel on standard CPUs by
+exploiting the partially diagonal structures" (arXiv 2105.04937), Sec. 4.3.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from .build import SO, build as _build_library  # noqa: F401  (re-exported for build steps)
+
+__all__ = [
+    "MHDC_F64", "MHDC_F32", "MHDC_BF16", "MhdcError", "Matrix", "lib", "mhdc_build",
+    "hdc_build", "mhdc_spmv", "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
+    "mhdc_info", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
+]
+
+MHDC_F64, MHDC_F32, MHDC_BF16 = 0, 1, 2
+DTYPES = {"f64": MHDC_F64, "f32": MHDC_F32, "bf16": MHDC_BF16}
+_NP_STORE = {MHDC_F64: np.float64, MHDC_F32: np.float32, MHDC_BF16: np.uint16}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MhdcError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {mhdc_strerror(code)} ({code})" + (f": {detail}" if detail else ""))
+
+
+class _Info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_rem", C.c_int64), ("P", C.c_int64),
+                ("n_blocks", C.c_int64), ("n_b", C.c_int32), ("dtype", C.c_int32),
+                ("mode", C.c_int32), ("reserved", C.c_int32), ("theta", C.c_double),
+                ("alpha", C.c_double), ("beta", C.c_double), ("bytes_model", C.c_int64),
+                ("bytes_device", C.c_int64)]
+
+
+_P, _I64, _I32, _D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+_SIGS = {
+    "mhdc_build": [_I64, _P, _P, _P, _I32, _D, _I32, _P, C.POINTER(C.c_void_p)],
+    "hdc_build": [_I64, _P, _P, _P, _I32, _D, _I32, _P, C.POINTER(C.c_void_p)],
+    "mhdc_spmv": [_P, _P, _P, _P],
+    "mhdc_spmv_host": [_P, _P, _P, _P],
+    "mhdc_spmm": [_P, _I32, _P, _I64, _P, _I64, _P],
+    "csr_spmv": [_I64, _P, _P, _P, _P, _P, _P],
+    "mhdc_export": [_P, _P, _P, _P, _P, _P, _P],
+    "mhdc_info": [_P, C.POINTER(_Info)],
+    "mhdc_destroy": [_P],
+    "mhdc_strerror": [C.c_int],
+    "mhdc_last_error": [],
+    "mhdc_stream_bench": [_I64, _P, _P, _P, _P, _I32, _P],
+}
+
+
+def lib(build_if_missing: bool = False):
+    """The loaded library; raises if it has not been compiled (see build.py)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(SO):
+                if not build_if_missing:
+                    raise RuntimeError(
+                        f"M-HDC CUDA library not built ({SO} missing): run "
+                        "paper_2105_04937_gb300.build.build() (or __graft_entry__.build())")
+                _build_library()
+            L = C.CDLL(SO)
+            for name, args in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = C.c_char_p if name in ("mhdc_strerror", "mhdc_last_error") else C.c_int
+            _lib = L
+    return _lib
+
+
+def mhdc_strerror(code: int) -> str:
+    return lib().mhdc_strerror(code).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise MhdcError(rc, where, lib().mhdc_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+def _check_dev(t, dtype, n=None, name="array"):
+    import torch
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {n}")
+    del torch
+
+
+class Matrix:
+    """Owner of an mhdc_handle (freed by destroy() or when collected)."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = handle
+        self.n = n
+        self._info = None
+
+    @property
+    def info(self) -> dict:
+        if self._info is None:
+            self._info = mhdc_info(self)
+        return self._info
+
+    @property
+    def dtype(self) -> int:
+        return self.info["dtype"]
+
+    def destroy(self):
+        if self.handle:
+            lib().mhdc_destroy(C.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+
+def _build(fn, n, row_ptr, col, val, n_b, theta, dtype, stream):
+    import torch
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    _check_dev(row_ptr, torch.int32, n + 1, "row_ptr")
+    _check_dev(col, torch.int32, None, "col")
+    _check_dev(val, torch.float64, None, "val")
+    h = C.c_void_p()
+    rc = getattr(lib(), fn)(n, _ptr(row_ptr), _ptr(col), _ptr(val), int(n_b), float(theta),
+                            int(dtype), _stream(stream), C.byref(h))
+    _check(rc, fn)
+    return Matrix(h.value, n)
+
+
+def mhdc_build(n, row_ptr, col, val, n_b, theta, dtype="f64", stream=None) -> Matrix:
+    """CSR (device int32 row_ptr/col, float64 val) -> M-HDC handle (Sec. 4.3)."""
+    return _build("mhdc_build", n, row_ptr, col, val, n_b, theta, dtype, stream)
+
+
+def hdc_build(n, row_ptr, col, val, n_b, theta, dtype="f64", stream=None) -> Matrix:
+    """CSR -> HDC (global selection, Sec. 3.4) stored blocked for the B-HDC kernel."""
+    return _build("hdc_build", n, row_ptr, col, val, n_b, theta, dtype, stream)
+
+
+def _xy_types(A: Matrix):
+    import torch
+    d = A.dtype
+    xt = {MHDC_F64: torch.float64, MHDC_F32: torch.float32, MHDC_BF16: torch.bfloat16}[d]
+    yt = torch.float64 if d == MHDC_F64 else torch.float32
+    return xt, yt
+
+
+def mhdc_spmv(A: Matrix, x, y, stream=None):
+    """y = A x on the device (Fig. 13)."""
+    xt, yt = _xy_types(A)
+    _check_dev(x, xt, A.n, "x")
+    _check_dev(y, yt, A.n, "y")
+    _check(lib().mhdc_spmv(C.c_void_p(A.handle), _ptr(x), _ptr(y), _stream(stream)), "mhdc_spmv")
+    return y
+
+
+def mhdc_spmv_host(A: Matrix, x, y, stream=None):
+    """y = A x with host (CPU, preferably pinned) torch tensors x and y."""
+    xt, yt = _xy_types(A)
+    for t, dt, nm in ((x, xt, "x"), (y, yt, "y")):
+        if t.is_cuda or t.dtype != dt or not t.is_contiguous() or t.numel() < A.n:
+            raise ValueError(f"{nm} must be a contiguous host tensor of {dt} with n elements")
+    _check(lib().mhdc_spmv_host(C.c_void_p(A.handle), _ptr(x), _ptr(y), _stream(stream)),
+           "mhdc_spmv_host")
+    return y
+
+
+def mhdc_spmm(A: Matrix, X, Y, stream=None):
+    """Y = A X for row-major n x k device tensors X and Y."""
+    xt, yt = _xy_types(A)
+    _check_dev(X, xt, None, "X")
+    _check_dev(Y, yt, None, "Y")
+    if X.dim() != 2 or Y.dim() != 2 or X.shape[0] < A.n or Y.shape[0] < A.n or X.shape[1] != Y.shape[1]:
+        raise ValueError("X and Y must be n x k")
+    k = X.shape[1]
+    _check(lib().mhdc_spmm(C.c_void_p(A.handle), k, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0),
+                           _stream(stream)), "mhdc_spmm")
+    return Y
+
+
+def csr_spmv(n, row_ptr, col, val, x, y, stream=None):
+    """The plain FP64 CSR kernel (Fig. 2) on device tensors."""
+    import torch
+    _check_dev(row_ptr, torch.int32, n + 1, "row_ptr")
+    _check_dev(x, torch.float64, n, "x")
+    _check_dev(y, torch.float64, n, "y")
+    _check(lib().csr_spmv(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(x), _ptr(y),
+                          _stream(stream)), "csr_spmv")
+    return y
+
+
+def mhdc_info(A: Matrix) -> dict:
+    inf = _Info()
+    _check(lib().mhdc_info(C.c_void_p(A.handle), C.byref(inf)), "mhdc_info")
+    return {name: getattr(inf, name) for name, _ in _Info._fields_ if name != "reserved"}
+
+
+def mhdc_export(A: Matrix) -> dict:
+    """Copy the handle's arrays to host numpy arrays (parity checks)."""
+    inf = A.info
+    sd = _NP_STORE[inf["dtype"]]
+    out = dict(
+        dia_ptr=np.zeros(inf["n_blocks"] + 1, np.int32),
+        dia_offset=np.zeros(max(1, inf["P"]), np.int32),
+        dia_val=np.zeros(max(1, inf["P"] * inf["n_b"]), sd),
+        csr_row_ptr=np.zeros(inf["n"] + 1, np.int32),
+        csr_col=np.zeros(max(1, inf["nnz_rem"]), np.int32),
+        csr_val=np.zeros(max(1, inf["nnz_rem"]), sd),
+    )
+    rc = lib().mhdc_export(C.c_void_p(A.handle), *(out[k].ctypes.data_as(C.c_void_p) for k in
+                                                   ("dia_ptr", "dia_offset", "dia_val",
+                                                    "csr_row_ptr", "csr_col", "csr_val")))
+    _check(rc, "mhdc_export")
+    out["dia_offset"] = out["dia_offset"][:inf["P"]]
+    out["dia_val"] = out["dia_val"][:inf["P"] * inf["n_b"]]
+    out["csr_col"] = out["csr_col"][:inf["nnz_rem"]]
+    out["csr_val"] = out["csr_val"][:inf["nnz_rem"]]
+    return out
+
+
+def mhdc_destroy(A: Matrix):
+    A.destroy()
+
+
+def mhdc_stream_bench(A, B, I, Cv, indirect: bool, stream=None):
+    """C += A * B (or A * B[I]) on device float64 tensors (Sec. 6.2)."""
+    import torch
+    N = Cv.numel()
+    for t, nm in ((A, "A"), (B, "B"), (Cv, "C")):
+        _check_dev(t, torch.float64, N, nm)
+    if indirect:
+        _check_dev(I, torch.int32, N, "I")
+    _check(lib().mhdc_stream_bench(N, _ptr(A), _ptr(B), _ptr(I) if indirect else None, _ptr(Cv),
+                                   1 if indirect else 0, _stream(stream)), "mhdc_stream_bench")
+    return Cv

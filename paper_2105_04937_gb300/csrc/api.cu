@@ -1,0 +1,174 @@
+// extern "C" entry points of include/mhdc.h: argument checks, dispatch to the
+// kernels, and per-thread error text.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "mhdc_internal.cuh"
+
+namespace mhdc {
+
+static thread_local char g_last_error[256] = "";
+
+void set_error(const char *where, cudaError_t e)
+{
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s (%d)", where, cudaGetErrorString(e),
+             (int)e);
+}
+
+void set_error_msg(const char *msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+
+}  // namespace mhdc
+
+using namespace mhdc;
+
+extern "C" {
+
+const char *mhdc_last_error(void) { return g_last_error; }
+
+const char *mhdc_strerror(int code)
+{
+    switch (code) {
+    case MHDC_OK: return "ok";
+    case MHDC_ERR_INVALID_ARG: return "invalid argument";
+    case MHDC_ERR_BAD_CSR: return "invalid CSR input";
+    case MHDC_ERR_OOM: return "device out of memory";
+    case MHDC_ERR_CUDA: return "CUDA error";
+    case MHDC_ERR_UNSUPPORTED: return "unsupported";
+    case MHDC_ERR_DEVICE_CHECK: return "device-side check failed";
+    case MHDC_ERR_TIMEOUT: return "device-side wait timed out";
+    default: return "unknown status";
+    }
+}
+
+int mhdc_build(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+               int32_t n_b, double theta, int32_t dtype, void *stream, mhdc_handle *out)
+{
+    return build_matrix(n, d_row_ptr, d_col, d_val, n_b, theta, dtype, MHDC_MODE_BLOCK,
+                        (cudaStream_t)stream, out);
+}
+
+int hdc_build(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+              int32_t n_b, double theta, int32_t dtype, void *stream, mhdc_handle *out)
+{
+    return build_matrix(n, d_row_ptr, d_col, d_val, n_b, theta, dtype, MHDC_MODE_GLOBAL,
+                        (cudaStream_t)stream, out);
+}
+
+int mhdc_spmv(mhdc_handle A, const void *d_x, void *d_y, void *stream)
+{
+    if (!A || (A->n > 0 && (!d_x || !d_y))) {
+        set_error_msg("mhdc_spmv: null argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    return launch_spmv(A, d_x, d_y, (cudaStream_t)stream);
+}
+
+int mhdc_spmv_host(mhdc_handle A, const void *h_x, void *h_y, void *stream)
+{
+    if (!A || (A->n > 0 && (!h_x || !h_y))) {
+        set_error_msg("mhdc_spmv_host: null argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bx = value_size(A->dtype) * (size_t)A->n, by = y_size(A->dtype) * (size_t)A->n;
+    if (!A->x_stage) MHDC_CUDA_TRY(cudaMalloc(&A->x_stage, bx ? bx : 16));
+    if (!A->y_stage) MHDC_CUDA_TRY(cudaMalloc(&A->y_stage, by ? by : 16));
+    MHDC_CUDA_TRY(cudaMemcpyAsync(A->x_stage, h_x, bx, cudaMemcpyHostToDevice, st));
+    int rc = launch_spmv(A, A->x_stage, A->y_stage, st);
+    if (rc != MHDC_OK) return rc;
+    MHDC_CUDA_TRY(cudaMemcpyAsync(h_y, A->y_stage, by, cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    return MHDC_OK;
+}
+
+int mhdc_spmm(mhdc_handle A, int32_t k, const void *d_X, int64_t ldx, void *d_Y, int64_t ldy,
+              void *stream)
+{
+    if (!A || k < 1 || k > 64 || ldx < k || ldy < k || (A->n > 0 && (!d_X || !d_Y))) {
+        set_error_msg("mhdc_spmm: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    return launch_spmm(A, k, d_X, ldx, d_Y, ldy, (cudaStream_t)stream);
+}
+
+int csr_spmv(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+             const double *d_x, double *d_y, void *stream)
+{
+    if (n < 0 || (n > 0 && (!d_row_ptr || !d_x || !d_y))) {
+        set_error_msg("csr_spmv: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    return launch_csr(n, d_row_ptr, d_col, d_val, d_x, d_y, (cudaStream_t)stream);
+}
+
+int mhdc_export(mhdc_handle A, int32_t *h_dia_ptr, int32_t *h_dia_offset, void *h_dia_val,
+                int32_t *h_csr_row_ptr, int32_t *h_csr_col, void *h_csr_val)
+{
+    if (!A) {
+        set_error_msg("mhdc_export: null handle");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    const size_t sv = value_size(A->dtype);
+    MHDC_CUDA_TRY(cudaDeviceSynchronize());
+    if (h_dia_ptr)
+        MHDC_CUDA_TRY(cudaMemcpy(h_dia_ptr, A->dia_ptr, sizeof(int32_t) * (A->n_blocks + 1),
+                                 cudaMemcpyDeviceToHost));
+    if (h_dia_offset && A->P)
+        MHDC_CUDA_TRY(cudaMemcpy(h_dia_offset, A->dia_offset, sizeof(int32_t) * A->P,
+                                 cudaMemcpyDeviceToHost));
+    if (h_dia_val && A->P)
+        MHDC_CUDA_TRY(cudaMemcpy(h_dia_val, A->dia_val, sv * (size_t)A->P * (size_t)A->n_b,
+                                 cudaMemcpyDeviceToHost));
+    if (h_csr_row_ptr)
+        MHDC_CUDA_TRY(cudaMemcpy(h_csr_row_ptr, A->csr_row_ptr, sizeof(int32_t) * (A->n + 1),
+                                 cudaMemcpyDeviceToHost));
+    if (h_csr_col && A->nnz_rem)
+        MHDC_CUDA_TRY(cudaMemcpy(h_csr_col, A->csr_col, sizeof(int32_t) * A->nnz_rem,
+                                 cudaMemcpyDeviceToHost));
+    if (h_csr_val && A->nnz_rem)
+        MHDC_CUDA_TRY(cudaMemcpy(h_csr_val, A->csr_val, sv * (size_t)A->nnz_rem,
+                                 cudaMemcpyDeviceToHost));
+    return MHDC_OK;
+}
+
+int mhdc_info(mhdc_handle A, mhdc_info_t *out)
+{
+    if (!A || !out) {
+        set_error_msg("mhdc_info: null argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    memset(out, 0, sizeof *out);
+    out->n = A->n;
+    out->nnz = A->nnz;
+    out->nnz_rem = A->nnz_rem;
+    out->P = A->P;
+    out->n_blocks = A->n_blocks;
+    out->n_b = A->n_b;
+    out->dtype = A->dtype;
+    out->mode = A->mode;
+    out->theta = A->theta;
+    out->alpha = A->P ? (double)(A->nnz - A->nnz_rem) / ((double)A->P * (double)A->n_b) : 0.0;
+    out->beta = A->nnz ? (double)A->nnz_rem / (double)A->nnz : 0.0;
+    out->bytes_model = A->bytes_model;
+    out->bytes_device = A->bytes_device;
+    return MHDC_OK;
+}
+
+int mhdc_destroy(mhdc_handle A)
+{
+    free_matrix(A);
+    return MHDC_OK;
+}
+
+int mhdc_stream_bench(int64_t N, const double *d_A, const double *d_B, const int32_t *d_I,
+                      double *d_C, int32_t indirect, void *stream)
+{
+    if (N < 0 || (N > 0 && (!d_A || !d_B || !d_C || (indirect && !d_I)))) {
+        set_error_msg("mhdc_stream_bench: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    return launch_stream_bench(N, d_A, d_B, d_I, d_C, indirect, (cudaStream_t)stream);
+}
+
+}  // extern "C"

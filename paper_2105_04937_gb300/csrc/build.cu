@@ -1,0 +1,691 @@
+// CSR -> M-HDC / blocked HDC conversion on the device (Sec. 3.4, 4.3; Fig. 12).
+//
+// Steps (one stream, the host only reads sizes back to allocate):
+//   1. k_validate       CSR checks (row_ptr bounds, columns in range, strictly
+//                       increasing inside a row).
+//   2. k_count_select   M-HDC: one CTA per row block counts N(d, ib) for every
+//                       offset d = j - i in a hash table (shared memory; a
+//                       block with too many distinct offsets is redone with a
+//                       table in global memory), keeps d iff N >= 1 and
+//                       N >= theta * rows(ib), and sorts the kept offsets.
+//      k_count_all      HDC: N(d) over the whole matrix in a dense array, kept
+//                       iff N >= 1 and N >= theta * n, compacted in order.
+//   3. scan             dia_ptr = exclusive prefix sum of the kept counts.
+//   4. k_scatter        one CTA per block: dia_val zero-filled, then every
+//                       entry either lands in dia_val[p * n_b + (i - r0)] or
+//                       is flagged for the remainder.
+//   5. scan + k_rem_*   remainder positions by an exclusive prefix sum of the
+//                       flags, which keeps the input order; csr_row_ptr[i] is
+//                       that prefix sum at row_ptr[i].
+#include <climits>
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "mhdc_internal.cuh"
+
+namespace mhdc {
+namespace {
+
+constexpr int32_t EMPTY_KEY = INT32_MIN;  // no offset d = j - i equals it (|d| < 2^31 - 1)
+constexpr int HCAP = 16384;               // shared-memory hash slots
+constexpr int HLIMIT = 12288;             // distinct offsets a shared table accepts
+constexpr int CS_THREADS = 512;
+constexpr int CS_WARPS = CS_THREADS / 32;
+constexpr size_t CS_SMEM = 3 * HCAP * sizeof(int32_t);
+
+// 32-bit finaliser of MurmurHash3 (Appleby): spreads offsets that differ only
+// in high bits (stencil offsets like -16384, 0, 16384) over the table.
+__device__ __forceinline__ uint32_t mix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__global__ void k_validate(int64_t n, const int32_t *__restrict__ rp,
+                           const int32_t *__restrict__ col, int32_t nnz, int *err)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t a = rp[i], b = rp[i + 1];
+    if (i == 0 && a != 0) atomicOr(err, 1);
+    if (a < 0 || b < a || b > nnz) {
+        atomicOr(err, 2);
+        return;
+    }
+    int64_t prev = -1;
+    for (int32_t k = a; k < b; k++) {
+        const int32_t c = col[k];
+        if (c < 0 || (int64_t)c >= n) {
+            atomicOr(err, 4);
+            return;
+        }
+        if ((int64_t)c <= prev) {
+            atomicOr(err, 8);
+            return;
+        }
+        prev = c;
+    }
+}
+
+// Insert one occurrence of `off`.  With limit > 0 a new key first reserves
+// room (used < limit < capacity, so an empty slot always exists); the probe
+// loop is bounded by the capacity in any case.  Returns false on overflow.
+__device__ __forceinline__ bool table_insert(volatile int32_t *keys, int32_t *cnt, uint32_t mask,
+                                             int32_t off, int *used, int limit)
+{
+    uint32_t h = mix32((uint32_t)off) & mask;
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+        const int32_t k = keys[h];
+        if (k == off) {
+            atomicAdd(&cnt[h], 1);
+            return true;
+        }
+        if (k == EMPTY_KEY) {
+            if (limit > 0 && atomicAdd(used, 1) >= limit) return false;
+            const int32_t prev = atomicCAS((int32_t *)&keys[h], EMPTY_KEY, off);
+            if (prev == EMPTY_KEY) {
+                atomicAdd(&cnt[h], 1);
+                return true;
+            }
+            if (limit > 0) atomicSub(used, 1);
+            if (prev == off) {
+                atomicAdd(&cnt[h], 1);
+                return true;
+            }
+        }
+        h = (h + 1) & mask;
+    }
+    return false;
+}
+
+// Ascending bitonic sort of a[0..P2) (P2 a power of two) by the whole CTA.
+__device__ void cta_bitonic_sort(int32_t *a, int64_t P2)
+{
+    for (int64_t k = 2; k <= P2; k <<= 1) {
+        for (int64_t j = k >> 1; j > 0; j >>= 1) {
+            for (int64_t i = threadIdx.x; i < P2; i += blockDim.x) {
+                const int64_t l = i ^ j;
+                if (l > i) {
+                    const int32_t x = a[i], y = a[l];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        a[i] = y;
+                        a[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// M-HDC selection for one row block per CTA.  GLOBAL_TABLE == false: the
+// table lives in shared memory and the CTA processes block blockIdx.x; a
+// block with more than HLIMIT distinct offsets sets overflow[ib] and stops.
+// GLOBAL_TABLE == true: CTA c processes block ids[c] with a table of
+// 2^tab_log2[c] slots at tab_base[c] in global memory.
+template <bool GLOBAL_TABLE>
+__global__ void __launch_bounds__(CS_THREADS)
+k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
+               const int32_t *__restrict__ col, double theta, const int32_t *__restrict__ ids,
+               int32_t *gkeys, int32_t *gcnt, const int64_t *__restrict__ tab_base,
+               const int32_t *__restrict__ tab_log2, int32_t *sel_out, int32_t *sel_cnt,
+               int32_t *overflow)
+{
+    extern __shared__ int32_t smem[];
+    __shared__ int used, nsel;
+    __shared__ volatile int ovf;
+    const int64_t ib = GLOBAL_TABLE ? (int64_t)ids[blockIdx.x] : (int64_t)blockIdx.x;
+    const int64_t r0 = ib * (int64_t)n_b;
+    const int64_t rows = (n - r0 < n_b) ? (n - r0) : n_b;
+    int32_t *keys, *cnt;
+    int64_t cap;
+    int limit;
+    if (GLOBAL_TABLE) {
+        keys = gkeys + tab_base[blockIdx.x];
+        cnt = gcnt + tab_base[blockIdx.x];
+        cap = (int64_t)1 << tab_log2[blockIdx.x];
+        limit = 0;
+    } else {
+        keys = smem;
+        cnt = smem + HCAP;
+        cap = HCAP;
+        limit = HLIMIT;
+    }
+    const uint32_t mask = (uint32_t)(cap - 1);
+    for (int64_t s = threadIdx.x; s < cap; s += blockDim.x) {
+        keys[s] = EMPTY_KEY;
+        cnt[s] = 0;
+    }
+    if (threadIdx.x == 0) {
+        used = 0;
+        nsel = 0;
+        ovf = 0;
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t i = r0 + warp; i < r0 + rows; i += CS_WARPS) {
+        if (ovf) break;
+        const int32_t a = rp[i], b = rp[i + 1];
+        for (int32_t k = a + lane; k < b; k += 32) {
+            const int32_t off = col[k] - (int32_t)i;
+            if (!table_insert(keys, cnt, mask, off, &used, limit)) {
+                ovf = 1;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    if (ovf) {
+        if (threadIdx.x == 0) {
+            overflow[ib] = 1;
+            sel_cnt[ib] = 0;
+        }
+        return;
+    }
+
+    // keep d iff N(d, ib) >= 1 and N >= theta * rows(ib)
+    const double thr = theta * (double)rows;
+    int32_t *sel = GLOBAL_TABLE ? (sel_out + rp[r0]) : (smem + 2 * HCAP);
+    for (int64_t s = threadIdx.x; s < cap; s += blockDim.x) {
+        const int32_t k = ((volatile int32_t *)keys)[s];
+        if (k != EMPTY_KEY) {
+            const int32_t c = ((volatile int32_t *)cnt)[s];
+            if (c >= 1 && (double)c >= thr) sel[atomicAdd(&nsel, 1)] = k;
+        }
+    }
+    __syncthreads();
+    const int64_t S = nsel;
+    int64_t P2 = 1;
+    while (P2 < S) P2 <<= 1;
+    int32_t *buf = GLOBAL_TABLE ? keys : sel;  // the table is no longer needed
+    if (GLOBAL_TABLE) {
+        for (int64_t s = threadIdx.x; s < S; s += blockDim.x) buf[s] = sel[s];
+    }
+    for (int64_t s = S + threadIdx.x; s < P2; s += blockDim.x) buf[s] = INT32_MAX;
+    __syncthreads();
+    cta_bitonic_sort(buf, P2);
+    int32_t *dst = sel_out + rp[r0];
+    for (int64_t s = threadIdx.x; s < S; s += blockDim.x) dst[s] = buf[s];
+    if (threadIdx.x == 0) {
+        sel_cnt[ib] = (int32_t)S;
+        overflow[ib] = 0;
+    }
+}
+
+// HDC: N(d) for d in [-(n-1), n-1] at cnt[d + n - 1].
+__global__ void k_count_all(int64_t n, const int32_t *__restrict__ rp,
+                            const int32_t *__restrict__ col, int32_t *cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+        const int32_t a = rp[i], b = rp[i + 1];
+        for (int32_t k = a + lane; k < b; k += 32)
+            atomicAdd(&cnt[(int64_t)col[k] - i + n - 1], 1);
+    }
+}
+
+__global__ void k_flag_global(int64_t m, const int32_t *__restrict__ cnt, double thr,
+                              int32_t *flags)
+{
+    const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= m) return;
+    const int32_t c = cnt[d];
+    flags[d] = (c >= 1 && (double)c >= thr) ? 1 : 0;
+}
+
+__global__ void k_compact_global(int64_t m, int64_t n, const int32_t *__restrict__ flags,
+                                 const int32_t *__restrict__ pos, int32_t *sel)
+{
+    const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= m) return;
+    if (flags[d]) sel[pos[d]] = (int32_t)(d - (n - 1));
+}
+
+__global__ void k_uniform_ptr(int64_t n_blocks, int32_t S, int32_t *dia_ptr)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b <= n_blocks) dia_ptr[b] = (int32_t)(b * S);
+}
+
+template <typename VT>
+__device__ __forceinline__ VT round_store(double v);
+template <>
+__device__ __forceinline__ double round_store<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float round_store<float>(double v) { return __double2float_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 round_store<__nv_bfloat16>(double v)
+{
+    return __float2bfloat16_rn(__double2float_rn(v));
+}
+
+// Position of d in the ascending list s[0..m), or -1.
+__device__ __forceinline__ int64_t find_sorted(const int32_t *__restrict__ s, int64_t m, int32_t d)
+{
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (s[mid] < d) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < m && s[lo] == d) ? lo : -1;
+}
+
+// One CTA per row block: write the block's dia_offset, zero its dia_val,
+// then place every entry (warp per row).  flags[k] = 1 marks a remainder entry.
+template <typename VT>
+__global__ void __launch_bounds__(256)
+k_scatter(int64_t n, int32_t n_b, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+          const double *__restrict__ val, const int32_t *__restrict__ dia_ptr,
+          const int32_t *__restrict__ sel_list, const int32_t *__restrict__ sel_base_rp,
+          int32_t *__restrict__ dia_offset, VT *__restrict__ dia_val, int32_t *__restrict__ flags)
+{
+    const int64_t ib = blockIdx.x;
+    const int64_t r0 = ib * (int64_t)n_b;
+    const int64_t rows = (n - r0 < n_b) ? (n - r0) : n_b;
+    const int64_t p0 = dia_ptr[ib];
+    const int64_t S = dia_ptr[ib + 1] - p0;
+    // M-HDC: the block's sorted list sits at sel_list + row_ptr[r0]; HDC: one shared list
+    const int32_t *sel = sel_list + (sel_base_rp ? (int64_t)sel_base_rp[r0] : 0);
+    for (int64_t s = threadIdx.x; s < S; s += blockDim.x) dia_offset[p0 + s] = sel[s];
+    VT *dv = dia_val + p0 * (int64_t)n_b;
+    for (int64_t s = threadIdx.x; s < S * (int64_t)n_b; s += blockDim.x) dv[s] = round_store<VT>(0.0);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    for (int64_t i = r0 + (threadIdx.x >> 5); i < r0 + rows; i += nw) {
+        const int32_t a = rp[i], b = rp[i + 1];
+        for (int32_t k = a + lane; k < b; k += 32) {
+            const int32_t off = col[k] - (int32_t)i;
+            const int64_t p = find_sorted(sel, S, off);
+            if (p >= 0) {
+                dv[p * n_b + (i - r0)] = round_store<VT>(val[k]);
+                flags[k] = 0;
+            } else {
+                flags[k] = 1;
+            }
+        }
+    }
+}
+
+template <typename VT>
+__global__ void k_rem_scatter(int64_t nnz, const int32_t *__restrict__ flags,
+                              const int32_t *__restrict__ pos, const int32_t *__restrict__ col,
+                              const double *__restrict__ val, int32_t *__restrict__ csr_col,
+                              VT *__restrict__ csr_val)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnz || !flags[k]) return;
+    const int32_t q = pos[k];
+    csr_col[q] = col[k];
+    csr_val[q] = round_store<VT>(val[k]);
+}
+
+__global__ void k_rem_rowptr(int64_t n, const int32_t *__restrict__ rp,
+                             const int32_t *__restrict__ pos, int32_t *__restrict__ csr_row_ptr)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) csr_row_ptr[i] = pos[rp[i]];
+}
+
+__global__ void k_block_bounds(int64_t n, int32_t n_b, int64_t n_blocks,
+                               const int32_t *__restrict__ rowptr, int32_t *__restrict__ out)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > n_blocks) return;
+    int64_t r = b * (int64_t)n_b;
+    if (r > n) r = n;
+    out[b] = rowptr[r];
+}
+
+inline unsigned grid_for(int64_t m, int threads) { return (unsigned)((m + threads - 1) / threads); }
+
+// Device buffer freed on scope exit.
+struct Buf {
+    void *p = nullptr;
+    ~Buf()
+    {
+        if (p) cudaFree(p);
+    }
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+int dalloc(Buf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        set_error("cudaMalloc", e);
+        return cuda_status(e);
+    }
+    return MHDC_OK;
+}
+
+int dalloc_raw(void **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error("cudaMalloc", e);
+        return cuda_status(e);
+    }
+    return MHDC_OK;
+}
+
+#define RC(expr)                          \
+    do {                                  \
+        int rc_ = (expr);                 \
+        if (rc_ != MHDC_OK) return rc_;   \
+    } while (0)
+
+template <typename VT>
+int scatter_all(mhdc_matrix *A, const int32_t *rp, const int32_t *col, const double *val,
+                const int32_t *sel_list, const int32_t *sel_base_rp, cudaStream_t st)
+{
+    const int64_t n = A->n, nnz = A->nnz;
+    Buf flags, pos, scr;
+    RC(dalloc(flags, sizeof(int32_t) * (size_t)nnz));
+    RC(dalloc(pos, sizeof(int32_t) * (size_t)(nnz + 1)));
+    RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(nnz)));
+    if (A->n_blocks > 0) {
+        k_scatter<VT><<<(unsigned)A->n_blocks, 256, 0, st>>>(
+            n, A->n_b, rp, col, val, A->dia_ptr, sel_list, sel_base_rp, A->dia_offset,
+            static_cast<VT *>(A->dia_val), flags.as<int32_t>());
+        MHDC_LAUNCH_CHECK("k_scatter");
+    }
+    RC(exclusive_scan_i32(flags.as<int32_t>(), pos.as<int32_t>(), nnz, scr.as<int32_t>(), st));
+    int32_t nr = 0;
+    MHDC_CUDA_TRY(cudaMemcpyAsync(&nr, pos.as<int32_t>() + nnz, sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    A->nnz_rem = nr;
+    RC(dalloc_raw((void **)&A->csr_col, sizeof(int32_t) * (size_t)nr));
+    RC(dalloc_raw(&A->csr_val, sizeof(VT) * (size_t)nr));
+    RC(dalloc_raw((void **)&A->csr_row_ptr, sizeof(int32_t) * (size_t)(n + 1)));
+    if (nnz > 0) {
+        k_rem_scatter<VT><<<grid_for(nnz, 256), 256, 0, st>>>(
+            nnz, flags.as<int32_t>(), pos.as<int32_t>(), col, val, A->csr_col,
+            static_cast<VT *>(A->csr_val));
+        MHDC_LAUNCH_CHECK("k_rem_scatter");
+    }
+    k_rem_rowptr<<<grid_for(n + 1, 256), 256, 0, st>>>(n, rp, pos.as<int32_t>(), A->csr_row_ptr);
+    MHDC_LAUNCH_CHECK("k_rem_rowptr");
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    return MHDC_OK;
+}
+
+int select_block_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Buf &sel_out,
+                      cudaStream_t st)
+{
+    const int64_t n = A->n, nnz = A->nnz, nb = A->n_blocks;
+    Buf sel_cnt, ovf, scr;
+    RC(dalloc(sel_out, sizeof(int32_t) * (size_t)nnz));
+    RC(dalloc(sel_cnt, sizeof(int32_t) * (size_t)nb));
+    RC(dalloc(ovf, sizeof(int32_t) * (size_t)nb));
+    MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_select<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CS_SMEM));
+    k_count_select<false><<<(unsigned)nb, CS_THREADS, CS_SMEM, st>>>(
+        n, A->n_b, rp, col, A->theta, nullptr, nullptr, nullptr, nullptr, nullptr,
+        sel_out.as<int32_t>(), sel_cnt.as<int32_t>(), ovf.as<int32_t>());
+    MHDC_LAUNCH_CHECK("k_count_select");
+    // blocks whose distinct offsets overflowed the shared table: redo with global tables
+    std::vector<int32_t> h_ovf((size_t)nb), h_bounds((size_t)nb + 1);
+    Buf bounds;
+    RC(dalloc(bounds, sizeof(int32_t) * (size_t)(nb + 1)));
+    k_block_bounds<<<grid_for(nb + 1, 256), 256, 0, st>>>(n, A->n_b, nb, rp, bounds.as<int32_t>());
+    MHDC_LAUNCH_CHECK("k_block_bounds");
+    MHDC_CUDA_TRY(cudaMemcpyAsync(h_ovf.data(), ovf.p, sizeof(int32_t) * nb,
+                                  cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaMemcpyAsync(h_bounds.data(), bounds.p, sizeof(int32_t) * (nb + 1),
+                                  cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int32_t> ids, lg;
+    std::vector<int64_t> base;
+    int64_t total = 0;
+    for (int64_t b = 0; b < nb; b++) {
+        if (!h_ovf[b]) continue;
+        const int64_t m = (int64_t)h_bounds[b + 1] - h_bounds[b];
+        int l = 10;
+        while (((int64_t)1 << l) < 2 * m) l++;
+        ids.push_back((int32_t)b);
+        lg.push_back(l);
+        base.push_back(total);
+        total += (int64_t)1 << l;
+    }
+    if (!ids.empty()) {
+        Buf gk, gc, d_ids, d_lg, d_base;
+        RC(dalloc(gk, sizeof(int32_t) * (size_t)total));
+        RC(dalloc(gc, sizeof(int32_t) * (size_t)total));
+        RC(dalloc(d_ids, sizeof(int32_t) * ids.size()));
+        RC(dalloc(d_lg, sizeof(int32_t) * lg.size()));
+        RC(dalloc(d_base, sizeof(int64_t) * base.size()));
+        MHDC_CUDA_TRY(cudaMemcpyAsync(d_ids.p, ids.data(), sizeof(int32_t) * ids.size(),
+                                      cudaMemcpyHostToDevice, st));
+        MHDC_CUDA_TRY(cudaMemcpyAsync(d_lg.p, lg.data(), sizeof(int32_t) * lg.size(),
+                                      cudaMemcpyHostToDevice, st));
+        MHDC_CUDA_TRY(cudaMemcpyAsync(d_base.p, base.data(), sizeof(int64_t) * base.size(),
+                                      cudaMemcpyHostToDevice, st));
+        k_count_select<true><<<(unsigned)ids.size(), CS_THREADS, 0, st>>>(
+            n, A->n_b, rp, col, A->theta, d_ids.as<int32_t>(), gk.as<int32_t>(),
+            gc.as<int32_t>(), d_base.as<int64_t>(), d_lg.as<int32_t>(), sel_out.as<int32_t>(),
+            sel_cnt.as<int32_t>(), ovf.as<int32_t>());
+        MHDC_LAUNCH_CHECK("k_count_select<global>");
+        // a global table cannot overflow (its capacity is at least twice the
+        // block's entries); check the flags anyway
+        MHDC_CUDA_TRY(cudaMemcpyAsync(h_ovf.data(), ovf.p, sizeof(int32_t) * nb,
+                                      cudaMemcpyDeviceToHost, st));
+        MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int32_t b : ids) {
+            if (h_ovf[b]) {
+                set_error_msg("k_count_select: global table overflow");
+                return MHDC_ERR_DEVICE_CHECK;
+            }
+        }
+    }
+    RC(dalloc_raw((void **)&A->dia_ptr, sizeof(int32_t) * (size_t)(nb + 1)));
+    RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(nb)));
+    RC(exclusive_scan_i32(sel_cnt.as<int32_t>(), A->dia_ptr, nb, scr.as<int32_t>(), st));
+    int32_t P = 0;
+    MHDC_CUDA_TRY(cudaMemcpyAsync(&P, A->dia_ptr + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    A->P = P;
+    return MHDC_OK;
+}
+
+int select_global_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Buf &sel_out,
+                       cudaStream_t st)
+{
+    const int64_t n = A->n, nb = A->n_blocks;
+    const int64_t m = 2 * n - 1;
+    Buf cnt, flags, pos, scr;
+    RC(dalloc(cnt, sizeof(int32_t) * (size_t)m));
+    RC(dalloc(flags, sizeof(int32_t) * (size_t)m));
+    RC(dalloc(pos, sizeof(int32_t) * (size_t)(m + 1)));
+    RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(m)));
+    MHDC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * (size_t)m, st));
+    k_count_all<<<1024, 256, 0, st>>>(n, rp, col, cnt.as<int32_t>());
+    MHDC_LAUNCH_CHECK("k_count_all");
+    k_flag_global<<<grid_for(m, 256), 256, 0, st>>>(m, cnt.as<int32_t>(), A->theta * (double)n,
+                                                     flags.as<int32_t>());
+    MHDC_LAUNCH_CHECK("k_flag_global");
+    RC(exclusive_scan_i32(flags.as<int32_t>(), pos.as<int32_t>(), m, scr.as<int32_t>(), st));
+    int32_t S = 0;
+    MHDC_CUDA_TRY(cudaMemcpyAsync(&S, pos.as<int32_t>() + m, sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    if ((int64_t)S * nb >= INT32_MAX) {
+        set_error_msg("hdc_build: number of partial diagonals exceeds int32");
+        return MHDC_ERR_UNSUPPORTED;
+    }
+    RC(dalloc(sel_out, sizeof(int32_t) * (size_t)S));
+    k_compact_global<<<grid_for(m, 256), 256, 0, st>>>(m, n, flags.as<int32_t>(),
+                                                        pos.as<int32_t>(), sel_out.as<int32_t>());
+    MHDC_LAUNCH_CHECK("k_compact_global");
+    RC(dalloc_raw((void **)&A->dia_ptr, sizeof(int32_t) * (size_t)(nb + 1)));
+    k_uniform_ptr<<<grid_for(nb + 1, 256), 256, 0, st>>>(nb, S, A->dia_ptr);
+    MHDC_LAUNCH_CHECK("k_uniform_ptr");
+    A->P = (int64_t)S * nb;
+    return MHDC_OK;
+}
+
+int finish_stats(mhdc_matrix *A, cudaStream_t st)
+{
+    const int64_t nb = A->n_blocks;
+    std::vector<int32_t> h((size_t)nb + 1);
+    Buf bounds;
+    RC(dalloc(bounds, sizeof(int32_t) * (size_t)(nb + 1)));
+    k_block_bounds<<<grid_for(nb + 1, 256), 256, 0, st>>>(A->n, A->n_b, nb, A->csr_row_ptr,
+                                                          bounds.as<int32_t>());
+    MHDC_LAUNCH_CHECK("k_block_bounds");
+    MHDC_CUDA_TRY(cudaMemcpyAsync(h.data(), bounds.p, sizeof(int32_t) * (nb + 1),
+                                  cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    int64_t rr = 0;
+    for (int64_t b = 0; b < nb; b++) {
+        if (h[b + 1] != h[b]) {
+            const int64_t r0 = b * (int64_t)A->n_b;
+            rr += (A->n - r0 < A->n_b) ? (A->n - r0) : A->n_b;
+        }
+    }
+    A->rem_block_rows = rr;
+    const int64_t sv = (int64_t)value_size(A->dtype), sy = (int64_t)y_size(A->dtype);
+    // V = V_A + V_x + V_y (Sec. 5.1; terms of Sec. 5.3.3): dia_val, dia_offset,
+    // dia_ptr, csr_val + csr_col_ind, csr_row_ptr (blocks with a remainder,
+    // plus the two bounds each block reads), x once, y once.
+    A->bytes_model = sv * A->P * A->n_b + 4 * A->P + 4 * (nb + 1) + (sv + 4) * A->nnz_rem +
+                     4 * (rr + 2 * nb) + sv * A->n + sy * A->n;
+    A->bytes_device = (int64_t)(sv * A->P * A->n_b + 4 * A->P + 4 * (nb + 1) +
+                                (sv + 4) * A->nnz_rem + 4 * (A->n + 1));
+    return MHDC_OK;
+}
+
+}  // namespace
+
+void free_matrix(mhdc_matrix *A)
+{
+    if (!A) return;
+    cudaFree(A->dia_ptr);
+    cudaFree(A->dia_offset);
+    cudaFree(A->dia_val);
+    cudaFree(A->csr_row_ptr);
+    cudaFree(A->csr_col);
+    cudaFree(A->csr_val);
+    cudaFree(A->x_stage);
+    cudaFree(A->y_stage);
+    delete A;
+}
+
+static int build_into(mhdc_matrix *A, const int32_t *rp, const int32_t *col, const double *val,
+                      cudaStream_t st)
+{
+    const int64_t n = A->n;
+    if (n == 0) {
+        RC(dalloc_raw((void **)&A->dia_ptr, sizeof(int32_t)));
+        RC(dalloc_raw((void **)&A->csr_row_ptr, sizeof(int32_t)));
+        RC(dalloc_raw((void **)&A->dia_offset, 0));
+        RC(dalloc_raw(&A->dia_val, 0));
+        RC(dalloc_raw((void **)&A->csr_col, 0));
+        RC(dalloc_raw(&A->csr_val, 0));
+        MHDC_CUDA_TRY(cudaMemsetAsync(A->dia_ptr, 0, sizeof(int32_t), st));
+        MHDC_CUDA_TRY(cudaMemsetAsync(A->csr_row_ptr, 0, sizeof(int32_t), st));
+        MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+        return MHDC_OK;
+    }
+    int32_t nnz = 0;
+    MHDC_CUDA_TRY(cudaMemcpyAsync(&nnz, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (nnz < 0) {
+        set_error_msg("mhdc_build: row_ptr[n] < 0");
+        return MHDC_ERR_BAD_CSR;
+    }
+    A->nnz = nnz;
+    {
+        Buf err;
+        RC(dalloc(err, sizeof(int)));
+        MHDC_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+        if (n > 0) {
+            k_validate<<<grid_for(n, 256), 256, 0, st>>>(n, rp, col, nnz, err.as<int>());
+            MHDC_LAUNCH_CHECK("k_validate");
+        }
+        int h = 0;
+        MHDC_CUDA_TRY(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (h) {
+            char msg[128];
+            snprintf(msg, sizeof msg, "mhdc_build: invalid CSR (flags 0x%x: %s%s%s%s)", h,
+                     (h & 1) ? "row_ptr[0]!=0 " : "", (h & 2) ? "row_ptr out of order " : "",
+                     (h & 4) ? "column out of range " : "", (h & 8) ? "columns not increasing" : "");
+            set_error_msg(msg);
+            return MHDC_ERR_BAD_CSR;
+        }
+    }
+    Buf sel_out;
+    if (A->mode == MHDC_MODE_BLOCK) {
+        RC(select_block_mode(A, rp, col, sel_out, st));
+    } else {
+        RC(select_global_mode(A, rp, col, sel_out, st));
+    }
+    const size_t sv = value_size(A->dtype);
+    RC(dalloc_raw((void **)&A->dia_offset, sizeof(int32_t) * (size_t)A->P));
+    RC(dalloc_raw(&A->dia_val, sv * (size_t)A->P * (size_t)A->n_b));
+    const int32_t *base = A->mode == MHDC_MODE_BLOCK ? rp : nullptr;
+    switch (A->dtype) {
+    case MHDC_F64:
+        RC(scatter_all<double>(A, rp, col, val, sel_out.as<int32_t>(), base, st));
+        break;
+    case MHDC_F32:
+        RC(scatter_all<float>(A, rp, col, val, sel_out.as<int32_t>(), base, st));
+        break;
+    default:
+        RC(scatter_all<__nv_bfloat16>(A, rp, col, val, sel_out.as<int32_t>(), base, st));
+        break;
+    }
+    RC(finish_stats(A, st));
+    A->spmv_grid = spmv_grid_for(A);
+    return MHDC_OK;
+}
+
+int build_matrix(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+                 int32_t n_b, double theta, int32_t dtype, int mode, cudaStream_t stream,
+                 mhdc_matrix **out)
+{
+    if (!out || !d_row_ptr || n < 0 || n >= INT32_MAX || n_b < 1 || !std::isfinite(theta) ||
+        theta < 0.0 || dtype < MHDC_F64 || dtype > MHDC_BF16) {
+        set_error_msg("mhdc_build: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    if (n > 0 && (!d_col || !d_val)) {
+        set_error_msg("mhdc_build: null column or value array");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    mhdc_matrix *A = new mhdc_matrix();
+    A->n = n;
+    A->n_b = n_b;
+    A->n_blocks = n == 0 ? 0 : (n + n_b - 1) / n_b;
+    A->theta = theta;
+    A->dtype = dtype;
+    A->mode = mode;
+    cudaGetDevice(&A->device);
+    int rc = build_into(A, d_row_ptr, d_col, d_val, stream);
+    if (rc != MHDC_OK) {
+        cudaStreamSynchronize(stream);
+        free_matrix(A);
+        return rc;
+    }
+    *out = A;
+    return MHDC_OK;
+}
+
+}  // namespace mhdc

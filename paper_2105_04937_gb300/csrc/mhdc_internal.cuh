@@ -1,0 +1,87 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mhdc.h"
+
+// A built matrix: every array is device memory owned by the handle.
+struct mhdc_matrix {
+    int64_t n = 0, nnz = 0, nnz_rem = 0, P = 0, n_blocks = 0;
+    int32_t n_b = 0, dtype = 0, mode = 0;
+    double theta = 0.0;
+    int device = 0;
+    int32_t *dia_ptr = nullptr;      // [n_blocks + 1]
+    int32_t *dia_offset = nullptr;   // [P]
+    void *dia_val = nullptr;         // [P * n_b] of dtype
+    int32_t *csr_row_ptr = nullptr;  // [n + 1]
+    int32_t *csr_col = nullptr;      // [nnz_rem]
+    void *csr_val = nullptr;         // [nnz_rem] of dtype
+    void *x_stage = nullptr;         // host-call staging buffers (lazy)
+    void *y_stage = nullptr;
+    int64_t rem_block_rows = 0;      // rows of blocks whose remainder is nonempty
+    int64_t bytes_model = 0;
+    int64_t bytes_device = 0;
+    int spmv_grid = 0;               // CTAs of the SpMV launch (multiple of the SM count)
+};
+
+namespace mhdc {
+
+inline size_t value_size(int dtype)
+{
+    return dtype == MHDC_F64 ? 8 : dtype == MHDC_F32 ? 4 : 2;
+}
+inline size_t y_size(int dtype) { return dtype == MHDC_F64 ? 8 : 4; }
+
+// Record the details of the last failure of this thread (mhdc_last_error).
+void set_error(const char *where, cudaError_t e);
+void set_error_msg(const char *msg);
+
+inline int cuda_status(cudaError_t e)
+{
+    return e == cudaErrorMemoryAllocation ? MHDC_ERR_OOM : MHDC_ERR_CUDA;
+}
+
+// Build (both selection modes); defined in build.cu.
+int build_matrix(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+                 int32_t n_b, double theta, int32_t dtype, int mode, cudaStream_t stream,
+                 mhdc_matrix **out);
+void free_matrix(mhdc_matrix *A);
+
+// Products; defined in spmv.cu.
+int launch_spmv(const mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream);
+int launch_spmm(const mhdc_matrix *A, int k, const void *d_X, int64_t ldx, void *d_Y,
+                int64_t ldy, cudaStream_t stream);
+int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+               const double *x, double *y, cudaStream_t stream);
+int launch_stream_bench(int64_t N, const double *A, const double *B, const int32_t *I, double *C,
+                        int indirect, cudaStream_t stream);
+int spmv_grid_for(const mhdc_matrix *A);
+
+// Exclusive prefix sum of m int32 values into out[0..m] (out[m] = total);
+// scratch must hold scan_scratch_elems(m) int32.  Defined in scan.cu.
+int64_t scan_scratch_elems(int64_t m);
+int exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t m, int32_t *scratch,
+                       cudaStream_t stream);
+
+}  // namespace mhdc
+
+#define MHDC_CUDA_TRY(expr)                                   \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) {                              \
+            mhdc::set_error(#expr, e_);                       \
+            return mhdc::cuda_status(e_);                     \
+        }                                                     \
+    } while (0)
+
+#define MHDC_LAUNCH_CHECK(name)                               \
+    do {                                                      \
+        cudaError_t e_ = cudaGetLastError();                  \
+        if (e_ != cudaSuccess) {                              \
+            mhdc::set_error(name, e_);                        \
+            return MHDC_ERR_CUDA;                             \
+        }                                                     \
+    } while (0)

@@ -1,0 +1,265 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Conversion (mhdc_build / hdc_build): every array bit-exact.  Products:
+FP64 within 1e-12 * sum_j |a_ij||x_j| per row; FP32/BF16 within the stated
+per-row bound (rounding of the stored values and FP32 accumulation).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import read_golden
+from gpu_util import (build, check_build, check_spmv, dev_csr, torch, x_device, y_empty)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mh():
+    t = torch()
+    assert t.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2105_04937_gb300 as m
+    m.lib()  # raises if the library was not built
+    return m
+
+
+DTYPES = ("f64", "f32", "bf16")
+
+
+# ---------------------------------------------------------------- worked example
+
+def test_example_matches_fig12_on_gpu(mh):
+    g = read_golden("example_mhdc_bl4_theta06.txt")
+    A = synth.example_matrix()
+    h = build(mh, A, 4, 0.6)
+    E = mh.mhdc_export(h)
+    assert E["dia_ptr"].tolist() == g["dia_ptr"]
+    assert E["dia_offset"].tolist() == g["dia_col_offset"]
+    assert E["dia_val"].tolist() == sum((g[f"dia_val{k}"] for k in range(5)), [])
+    assert E["csr_val"].tolist() == g["csr_val"]
+    assert E["csr_col"].tolist() == g["csr_col_ind"]
+    assert E["csr_row_ptr"].tolist() == g["csr_row_ptr"]
+
+
+@pytest.mark.parametrize("mode", ["block", "global"])
+def test_example_every_block_size(mh, mode):
+    A = synth.example_matrix()
+    x = np.arange(1.0, 9.0)
+    for bl in range(1, 11):
+        for theta in (0.0, 0.3, 0.6, 1.0, 1.5):
+            h, M = check_build(mh, A, bl, theta, "f64", mode)
+            y = check_spmv(mh, h, M, A, x, "f64")
+            dense = np.zeros((8, 8))
+            dense[A.rows(), A.col] = A.val
+            assert y.tolist() == (dense @ x).tolist()
+
+
+# ---------------------------------------------------------------- random small
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_small(mh, seed):
+    rng = synth.Rng(seed, 5)
+    n = int(rng.integers(1, 1, 300)[0])
+    A = synth.random_sparse(n, 0.03, seed=seed, diag_bias=0.7)
+    x = synth.uniform_vector(n, seed)
+    for n_b in sorted({1, 3, 8, 64, 100, n, 2 * n + 1}):
+        for theta in (0.0, 0.5, 0.9):
+            for dt in DTYPES:
+                h, M = check_build(mh, A, n_b, theta, dt)
+                check_spmv(mh, h, M, A, x, dt)
+
+
+# ---------------------------------------------------------------- workloads
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_stencil7_32_full(mh, dt):
+    # 7-point FDM on 32^3, n_b = 1024, theta = 0.6 (the small workload)
+    A = synth.config_matrix("stencil7_32")
+    h, M = check_build(mh, A, 1024, 0.6, dt)
+    assert M["nnz_rem"] == 0 and M["P"] == 222
+    check_spmv(mh, h, M, A, synth.uniform_vector(A.n, 0), dt)
+
+
+@pytest.mark.parametrize("n_b", [256, 1000, 4096, 8192, 12345])
+def test_stencil27_scaled(mh, n_b):
+    A = synth.config_matrix("stencil27_128", scale=0.375)   # 48^3 rows, 27-point
+    x = synth.uniform_vector(A.n, 1)
+    for dt in DTYPES:
+        for theta in (0.5, 0.9):
+            h, M = check_build(mh, A, n_b, theta, dt)
+            check_spmv(mh, h, M, A, x, dt)
+    h, M = check_build(mh, A, n_b, 0.6, "f64", "global")
+    check_spmv(mh, h, M, A, x, "f64")
+
+
+@pytest.mark.parametrize("n_b", [2048, 8192])
+def test_scattered_scaled(mh, n_b):
+    # n_b = 8192 has > 12288 distinct offsets per block: the global-table path
+    A = synth.config_matrix("scattered_4m", scale=1 / 64)
+    x = synth.loguniform_vector(A.n, 2)
+    for dt in DTYPES:
+        h, M = check_build(mh, A, n_b, 0.6, dt)
+        check_spmv(mh, h, M, A, x, dt)
+
+
+def test_paper_stencils(mh):
+    for dim in (1, 2, 3):
+        A = synth.paper_stencil(50000, dim)
+        x = synth.uniform_vector(A.n, dim)
+        for n_b in (10, 500, 5000):
+            h, M = check_build(mh, A, n_b, 0.6, "f64")
+            check_spmv(mh, h, M, A, x, "f64")
+
+
+# ---------------------------------------------------------------- full size
+
+def test_stencil27_128_full_size(mh):
+    # the benchmark workload, in the benchmark's configuration
+    A = synth.config_matrix("stencil27_128")
+    h, M = check_build(mh, A, 4096, 0.6, "f64")
+    check_spmv(mh, h, M, A, synth.uniform_vector(A.n, 1), "f64")
+    # HDC over the same matrix (blocked, global selection)
+    h2, M2 = check_build(mh, A, 4096, 0.6, "f64", "global")
+    check_spmv(mh, h2, M2, A, synth.uniform_vector(A.n, 1), "f64")
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_scattered_4m_full_size(mh, dt):
+    A = synth.config_matrix("scattered_4m")
+    h, M = check_build(mh, A, 2048, 0.6, dt)
+    check_spmv(mh, h, M, A, synth.loguniform_vector(A.n, 2), dt)
+
+
+# ---------------------------------------------------------------- CSR baseline
+
+@pytest.mark.parametrize("name,scale", [("stencil7_32", 1.0), ("stencil27_128", 1.0),
+                                        ("scattered_4m", 1.0)])
+def test_csr_spmv(mh, name, scale):
+    A = synth.config_matrix(name, scale)
+    x = synth.uniform_vector(A.n, 3)
+    rp, col, val = dev_csr(A)
+    t = torch()
+    xd = t.from_numpy(x).cuda()
+    y = y_empty(A.n, "f64")
+    mh.csr_spmv(A.n, rp, col, val, xd, y)
+    yg = y.cpu().numpy()
+    ref = oracle.csr_spmv(A, x)
+    assert np.all(np.abs(yg - ref) <= oracle.FP64_ROW_TOL * oracle.csr_absrow(A, x))
+
+
+def test_csr_spmv_row_lengths(mh):
+    # every lanes-per-row choice (mean row length 1 .. 60)
+    t = torch()
+    for density in (0.0005, 0.002, 0.004, 0.008, 0.02, 0.06):
+        A = synth.random_sparse(1000, density, seed=7, diag_bias=0.5)
+        x = synth.uniform_vector(A.n, 3)
+        rp, col, val = dev_csr(A)
+        y = y_empty(A.n, "f64")
+        mh.csr_spmv(A.n, rp, col, val, t.from_numpy(x).cuda(), y)
+        ref = oracle.csr_spmv(A, x)
+        assert np.all(np.abs(y.cpu().numpy() - ref) <= oracle.FP64_ROW_TOL * oracle.csr_absrow(A, x))
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_empty_matrix(mh):
+    A = synth.CSR(0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    t = torch()
+    rp = t.zeros(1, dtype=t.int32, device="cuda")
+    col = t.zeros(1, dtype=t.int32, device="cuda")
+    val = t.zeros(1, dtype=t.float64, device="cuda")
+    h = mh.mhdc_build(0, rp, col, val, 16, 0.6)
+    assert h.info["P"] == 0 and h.info["nnz"] == 0
+    x = t.zeros(1, dtype=t.float64, device="cuda")
+    y = t.zeros(1, dtype=t.float64, device="cuda")
+    mh.mhdc_spmv(h, x[:0], y[:0])
+    del A
+
+
+def test_matrix_without_entries_and_empty_rows(mh):
+    n = 777
+    A = synth.CSR(n, np.zeros(n + 1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    h, M = check_build(mh, A, 64, 0.5)
+    y = check_spmv(mh, h, M, A, synth.uniform_vector(n, 0), "f64")
+    assert np.all(y == 0.0)
+    # only a few rows hold entries
+    d = np.zeros((n, n))
+    d[5, 7] = 1.5
+    d[700, 3] = -2.0
+    d[776, 776] = 3.0
+    B = synth.from_dense(d)
+    for n_b in (1, 64, 777, 1000):
+        h, M = check_build(mh, B, n_b, 0.0)
+        check_spmv(mh, h, M, B, synth.uniform_vector(n, 1), "f64")
+
+
+def test_bad_csr_is_rejected(mh):
+    A = synth.example_matrix()
+    t = torch()
+    cases = []
+    col = A.col.copy(); col[5] = 8; cases.append((A.row_ptr, col))
+    col = A.col.copy(); col[1] = 0; cases.append((A.row_ptr, col))
+    col = A.col.copy(); col[0], col[1] = col[1], col[0]; cases.append((A.row_ptr, col))
+    rp = A.row_ptr.copy(); rp[3], rp[4] = rp[4], rp[3]; cases.append((rp, A.col))
+    rp = A.row_ptr.copy(); rp[0] = 1; cases.append((rp, A.col))
+    for rp, col in cases:
+        with pytest.raises(mh.MhdcError) as e:
+            mh.mhdc_build(8, t.from_numpy(rp.astype(np.int32)).cuda(),
+                          t.from_numpy(col.astype(np.int32)).cuda(),
+                          t.from_numpy(A.val).cuda(), 4, 0.6)
+        assert e.value.code == -2
+    rp_d, col_d, val_d = dev_csr(A)
+    for kw in (dict(n_b=0), dict(theta=-1.0), dict(theta=float("nan")), dict(dtype=7)):
+        args = dict(n_b=4, theta=0.6, dtype="f64")
+        args.update(kw)
+        with pytest.raises(mh.MhdcError) as e:
+            mh.mhdc_build(8, rp_d, col_d, val_d, args["n_b"], args["theta"], args["dtype"])
+        assert e.value.code == -1
+
+
+def test_misaligned_x_gives_identical_result(mh):
+    A = synth.config_matrix("stencil27_128", scale=0.25)
+    t = torch()
+    for dt in DTYPES:
+        h = build(mh, A, 4096, 0.6, dt)
+        xd, _ = x_device(synth.uniform_vector(A.n, 9), dt)
+        buf = t.zeros(A.n + 1, dtype=xd.dtype, device="cuda")
+        buf[1:] = xd
+        y1 = y_empty(A.n, dt)
+        y2 = y_empty(A.n, dt)
+        mh.mhdc_spmv(h, xd, y1)
+        mh.mhdc_spmv(h, buf[1:], y2)
+        assert t.equal(y1, y2)
+
+
+def test_repeatable_and_host_path(mh):
+    A = synth.config_matrix("stencil27_128", scale=0.25)
+    t = torch()
+    for dt in DTYPES:
+        h = build(mh, A, 2048, 0.6, dt)
+        xd, _ = x_device(synth.uniform_vector(A.n, 4), dt)
+        y1 = y_empty(A.n, dt)
+        y2 = y_empty(A.n, dt)
+        mh.mhdc_spmv(h, xd, y1)
+        mh.mhdc_spmv(h, xd, y2)
+        assert t.equal(y1, y2)
+        xh = xd.cpu().pin_memory()
+        yh = t.empty(A.n, dtype=y1.dtype).pin_memory()
+        mh.mhdc_spmv_host(h, xh, yh)
+        assert t.equal(yh, y1.cpu())
+
+
+def test_stream_bench(mh):
+    t = torch()
+    N = 1 << 20
+    Av = t.arange(N, dtype=t.float64, device="cuda")
+    Bv = t.full((N,), 2.0, dtype=t.float64, device="cuda")
+    I = t.arange(N, dtype=t.int32, device="cuda")
+    for ind in (False, True):
+        Cv = t.ones(N, dtype=t.float64, device="cuda")
+        mh.mhdc_stream_bench(Av, Bv, I, Cv, ind)
+        ref = oracle.stream_indirect(Av.cpu().numpy(), Bv.cpu().numpy(), I.cpu().numpy(),
+                                     np.ones(N)) if ind else \
+            oracle.stream_direct(Av.cpu().numpy(), Bv.cpu().numpy(), np.ones(N))
+        assert np.array_equal(Cv.cpu().numpy(), ref)
