@@ -153,10 +153,14 @@ k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
         cap = (int64_t)1 << tab_log2[blockIdx.x];
         limit = 0;
     } else {
+        // distinct offsets <= entries m of the block: a table of 2m slots
+        // (at least 64, at most HCAP) never fills unless m is large
+        const int64_t m = (int64_t)rp[r0 + rows] - rp[r0];
+        cap = 64;
+        while (cap < 2 * m && cap < HCAP) cap <<= 1;
         keys = smem;
         cnt = smem + HCAP;
-        cap = HCAP;
-        limit = HLIMIT;
+        limit = cap == HCAP ? HLIMIT : (int)cap - 1;
     }
     const uint32_t mask = (uint32_t)(cap - 1);
     for (int64_t s = threadIdx.x; s < cap; s += blockDim.x) {
