@@ -79,7 +79,7 @@ typedef struct {
  *   n            rows (= columns), 0 <= n < 2^31 - 1
  *   d_row_ptr    int32[n + 1], row_ptr[0] = 0, nondecreasing, row_ptr[n] = nnz < 2^31
  *   d_col        int32[nnz], columns of each row strictly increasing, in [0, n)
- *   d_val        double[nnz]
+ *   d_val        double[nnz]  (d_col and d_val may be NULL when nnz = 0)
  *   n_b          rows per block, >= 1 (the paper's bl)
  *   theta        density threshold, finite and >= 0: in block ib the partial
  *                diagonal of offset d is kept iff its count N(d, ib) >= 1 and

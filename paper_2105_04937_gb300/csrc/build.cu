@@ -615,6 +615,10 @@ static int build_into(mhdc_matrix *A, const int32_t *rp, const int32_t *col, con
         return MHDC_ERR_BAD_CSR;
     }
     A->nnz = nnz;
+    if (nnz > 0 && (!col || !val)) {
+        set_error_msg("mhdc_build: null column or value array with nnz > 0");
+        return MHDC_ERR_INVALID_ARG;
+    }
     {
         Buf err;
         RC(dalloc(err, sizeof(int)));
@@ -668,10 +672,6 @@ int build_matrix(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, cons
     if (!out || !d_row_ptr || n < 0 || n >= INT32_MAX || n_b < 1 || !std::isfinite(theta) ||
         theta < 0.0 || dtype < MHDC_F64 || dtype > MHDC_BF16) {
         set_error_msg("mhdc_build: invalid argument");
-        return MHDC_ERR_INVALID_ARG;
-    }
-    if (n > 0 && (!d_col || !d_val)) {
-        set_error_msg("mhdc_build: null column or value array");
         return MHDC_ERR_INVALID_ARG;
     }
     mhdc_matrix *A = new mhdc_matrix();
