@@ -284,6 +284,11 @@ def main():
     log(f"built: P={info['P']} nnz_rem={info['nnz_rem']} alpha={info['alpha']:.3f} "
         f"beta={info['beta']:.4f} bytes_model={info['bytes_model']} in {build_ms:.1f} ms")
 
+    # the library's own autotuner picks the tile shape (not timed)
+    best_variant, variant_us = mh.mhdc_tune(H, x, y)
+    log(f"tuned: variant {best_variant}; per-variant us {[round(t, 2) for t in variant_us]}")
+    info = H.info
+
     peak, peak_src = measured_peak()
     vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
     sampler = ClockSampler(vis[local].strip() if local < len(vis) else local)
@@ -385,13 +390,14 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "n_b": N_B, "theta": THETA,
                        "P": info["P"], "nnz_rem": info["nnz_rem"],
+                       "variant": best_variant, "variant_us": [round(t, 2) for t in variant_us],
                        "alpha": round(info["alpha"], 4), "beta": round(info["beta"], 5),
                        "l2": "inputs larger than L2 (M-HDC arrays "
                              f"{info['bytes_model'] / 1e6:.0f} MB > 129 MB L2); no flush",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": None, "kernel": "k_mhdc_spmv<double,2,true>",
+                         "traffic": None, "kernel": f"k_mhdc_spmv<double> variant {best_variant}",
                          "bytes_per_launch": info["bytes_model"],
                          "kernel_us": round(kern_ms * 1e3, 3), "peak_source": peak_src},
             "cpu_baseline": cpu,

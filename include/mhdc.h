@@ -62,7 +62,7 @@ typedef struct {
     int32_t n_b;           /* rows per block */
     int32_t dtype;         /* enum mhdc_dtype */
     int32_t mode;          /* enum mhdc_mode */
-    int32_t reserved;
+    int32_t variant;       /* SpMV tile shape in use (-1: default) */
     double theta;          /* density threshold used */
     double alpha;          /* filling rate: (nnz - nnz_rem) / (P * n_b)   (Sec. 5.3.3) */
     double beta;           /* CSR rate: nnz_rem / nnz                     (Sec. 5.3.1) */
@@ -161,6 +161,23 @@ int mhdc_export(mhdc_handle A, int32_t *h_dia_ptr, int32_t *h_dia_offset, void *
 
 /* mhdc_info -- fill *out with the handle's sizes and statistics. */
 int mhdc_info(mhdc_handle A, mhdc_info_t *out);
+
+/*
+ * Tile shapes of the M-HDC product (no counterpart in the paper, whose kernel
+ * is a CPU loop nest): variant v in [0, MHDC_NUM_VARIANTS) sets how many rows
+ * a warp owns and how many diagonals it loads before accumulating.  All
+ * variants compute the same sums in the same order per row (bit-identical y).
+ *
+ * mhdc_set_variant -- use variant v for this handle (-1: default chosen from n_b).
+ * mhdc_tune        -- time every variant on (d_x, d_y) (overwriting d_y), keep
+ *                     the fastest in the handle, write its id to *best and, if
+ *                     times_us is not NULL, each variant's mean time in
+ *                     microseconds to times_us[MHDC_NUM_VARIANTS].  Synchronous.
+ */
+#define MHDC_NUM_VARIANTS 6
+int mhdc_set_variant(mhdc_handle A, int32_t v);
+int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *best,
+              float *times_us);
 
 /* mhdc_destroy -- free the handle and its device arrays (NULL is a no-op). */
 int mhdc_destroy(mhdc_handle A);

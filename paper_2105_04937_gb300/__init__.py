@@ -23,6 +23,7 @@ __all__ = [
     "MHDC_F64", "MHDC_F32", "MHDC_BF16", "MhdcError", "Matrix", "lib", "mhdc_build",
     "hdc_build", "mhdc_spmv", "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
     "mhdc_info", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
+    "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS",
 ]
 
 MHDC_F64, MHDC_F32, MHDC_BF16 = 0, 1, 2
@@ -42,7 +43,7 @@ class MhdcError(RuntimeError):
 class _Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_rem", C.c_int64), ("P", C.c_int64),
                 ("n_blocks", C.c_int64), ("n_b", C.c_int32), ("dtype", C.c_int32),
-                ("mode", C.c_int32), ("reserved", C.c_int32), ("theta", C.c_double),
+                ("mode", C.c_int32), ("variant", C.c_int32), ("theta", C.c_double),
                 ("alpha", C.c_double), ("beta", C.c_double), ("bytes_model", C.c_int64),
                 ("bytes_device", C.c_int64)]
 
@@ -61,7 +62,11 @@ _SIGS = {
     "mhdc_strerror": [C.c_int],
     "mhdc_last_error": [],
     "mhdc_stream_bench": [_I64, _P, _P, _P, _P, _I32, _P],
+    "mhdc_set_variant": [_P, _I32],
+    "mhdc_tune": [_P, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
 }
+
+MHDC_NUM_VARIANTS = 6
 
 
 def lib(build_if_missing: bool = False):
@@ -234,7 +239,7 @@ def csr_spmv(n, row_ptr, col, val, x, y, stream=None):
 def mhdc_info(A: Matrix) -> dict:
     inf = _Info()
     _check(lib().mhdc_info(C.c_void_p(A.handle), C.byref(inf)), "mhdc_info")
-    return {name: getattr(inf, name) for name, _ in _Info._fields_ if name != "reserved"}
+    return {name: getattr(inf, name) for name, _ in _Info._fields_}
 
 
 def mhdc_export(A: Matrix) -> dict:
@@ -275,3 +280,23 @@ def mhdc_stream_bench(A, B, I, Cv, indirect: bool, stream=None):
     _check(lib().mhdc_stream_bench(N, _ptr(A), _ptr(B), _ptr(I) if indirect else None, _ptr(Cv),
                                    1 if indirect else 0, _stream(stream)), "mhdc_stream_bench")
     return Cv
+
+
+def mhdc_set_variant(A: Matrix, v: int):
+    """Select the SpMV tile shape (-1: default from n_b)."""
+    _check(lib().mhdc_set_variant(C.c_void_p(A.handle), int(v)), "mhdc_set_variant")
+    A._info = None
+
+
+def mhdc_tune(A: Matrix, x, y, stream=None):
+    """Time every tile shape on (x, y); keep the fastest.  Returns
+    (best id, list of mean times in microseconds)."""
+    xt, yt = _xy_types(A)
+    _check_dev(x, xt, A.n, "x")
+    _check_dev(y, yt, A.n, "y")
+    best = C.c_int32(-1)
+    times = (C.c_float * MHDC_NUM_VARIANTS)()
+    _check(lib().mhdc_tune(C.c_void_p(A.handle), _ptr(x), _ptr(y), _stream(stream),
+                           C.byref(best), times), "mhdc_tune")
+    A._info = None
+    return best.value, [float(t) for t in times]

@@ -147,12 +147,33 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out)
     out->n_b = A->n_b;
     out->dtype = A->dtype;
     out->mode = A->mode;
+    out->variant = A->variant;
     out->theta = A->theta;
     out->alpha = A->P ? (double)(A->nnz - A->nnz_rem) / ((double)A->P * (double)A->n_b) : 0.0;
     out->beta = A->nnz ? (double)A->nnz_rem / (double)A->nnz : 0.0;
     out->bytes_model = A->bytes_model;
     out->bytes_device = A->bytes_device;
     return MHDC_OK;
+}
+
+int mhdc_set_variant(mhdc_handle A, int32_t v)
+{
+    if (!A || v < -1 || v >= MHDC_NUM_VARIANTS) {
+        set_error_msg("mhdc_set_variant: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    A->variant = v;
+    return MHDC_OK;
+}
+
+int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *best,
+              float *times_us)
+{
+    if (!A || (A->n > 0 && (!d_x || !d_y))) {
+        set_error_msg("mhdc_tune: null argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    return tune_spmv(A, d_x, d_y, (cudaStream_t)stream, best, times_us);
 }
 
 int mhdc_destroy(mhdc_handle A)

@@ -24,7 +24,8 @@ struct mhdc_matrix {
     int64_t rem_block_rows = 0;      // rows of blocks whose remainder is nonempty
     int64_t bytes_model = 0;
     int64_t bytes_device = 0;
-    int spmv_grid = 0;               // CTAs of the SpMV launch (multiple of the SM count)
+    int spmv_grid = 0;               // CTAs of the SpMV launch
+    int variant = -1;                // SpMV tile shape (-1: chosen from n_b)
 };
 
 namespace mhdc {
@@ -59,6 +60,8 @@ int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *v
 int launch_stream_bench(int64_t N, const double *A, const double *B, const int32_t *I, double *C,
                         int indirect, cudaStream_t stream);
 int spmv_grid_for(const mhdc_matrix *A);
+int tune_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream, int32_t *best,
+              float *times_us);
 
 // Exclusive prefix sum of m int32 values into out[0..m] (out[m] = total);
 // scratch must hold scan_scratch_elems(m) int32.  Defined in scan.cu.

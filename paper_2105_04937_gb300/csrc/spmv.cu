@@ -11,6 +11,7 @@
 // accumulates in registers; y is written once.  A persistent grid of
 // (SMs x resident CTAs) walks the tiles.
 #include <cstring>
+#include <type_traits>
 
 #include "mhdc_internal.cuh"
 
@@ -64,7 +65,27 @@ __device__ __forceinline__ T ldg_elem(const T *p)
 constexpr int SPMV_THREADS = 256;
 constexpr int SPMV_WARPS = SPMV_THREADS / 32;
 
-template <typename VT, int U, bool VEC>
+// x[j .. j+V) into xv: one 16-byte load when j is 16-byte aligned, else V
+// element loads (all in bounds: the caller checked 0 <= j, j + V <= n).
+template <typename X, int V>
+__device__ __forceinline__ void load_x(const X *__restrict__ x, int64_t j, bool aligned, X (&xv)[V])
+{
+    if constexpr (V * sizeof(X) == 16) {
+        if (aligned) {
+            const uint4 r = __ldg(reinterpret_cast<const uint4 *>(x + j));
+            memcpy(xv, &r, 16);
+            return;
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < V; m++) xv[m] = ldg_elem(x + j + m);
+}
+
+// One warp = one tile of RW = 32 * V * U consecutive rows of one row block.
+// The block's diagonals are taken D at a time: the D * U 16-byte value loads
+// of a group are issued first, then the x loads, then the FMAs, so a warp
+// keeps D * U * 512 bytes of dia_val in flight.
+template <typename VT, int U, int D, bool VEC>
 __global__ void __launch_bounds__(SPMV_THREADS)
 k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
             const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
@@ -77,31 +98,36 @@ k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
     constexpr int V = VEC ? Tr<VT>::V : 1;
     constexpr int RW = 32 * V * U;
     const int lane = threadIdx.x & 31;
-    const bool x_vec = VEC && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
-    const int64_t wstride = (int64_t)gridDim.x * SPMV_WARPS;
-    for (int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5); w < n_tiles;
-         w += wstride) {
-        const int64_t ib = w / tpb;
-        const int32_t tw = (int32_t)(w - ib * tpb) * RW;
-        const int64_t r0 = ib * (int64_t)n_b;
-        const int32_t rows = (int32_t)((n - r0 < n_b) ? (n - r0) : n_b);
-        if (tw >= rows) continue;  // warp-uniform
+    const int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5);
+    if (w >= n_tiles) return;
+    const int64_t ib = w / tpb;
+    const int32_t tw = (int32_t)(w - ib * tpb) * RW;
+    const int64_t r0 = ib * (int64_t)n_b;
+    const int32_t rows = (int32_t)((n - r0 < n_b) ? (n - r0) : n_b);
+    if (tw >= rows) return;  // warp-uniform
+    const bool full = tw + RW <= rows;
+    const bool x_al = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
 
-        Acc acc[U][V];
+    int32_t tl[U];
 #pragma unroll
-        for (int u = 0; u < U; u++)
-#pragma unroll
-            for (int m = 0; m < V; m++) acc[u][m] = Acc(0);
+    for (int u = 0; u < U; u++) tl[u] = tw + (u * 32 + lane) * V;
 
-        // CSR remainder rows of the tile (Fig. 13, first loop)
-        const int32_t tend = (tw + RW < rows) ? (tw + RW) : rows;
+    Acc acc[U][V];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+#pragma unroll
+        for (int m = 0; m < V; m++) acc[u][m] = Acc(0);
+
+    // CSR remainder rows of the tile (Fig. 13, first loop)
+    {
+        const int32_t tend = full ? tw + RW : rows;
         const int32_t q0 = csr_row_ptr[r0 + tw], q1 = csr_row_ptr[r0 + tend];
         if (q0 != q1) {
 #pragma unroll
             for (int u = 0; u < U; u++) {
 #pragma unroll
                 for (int m = 0; m < V; m++) {
-                    const int32_t t = tw + (u * 32 + lane) * V + m;
+                    const int32_t t = tl[u] + m;
                     if (t < rows) {
                         const int64_t i = r0 + t;
                         const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
@@ -111,99 +137,106 @@ k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
                 }
             }
         }
+    }
 
-        // the block's partial diagonals (Fig. 13, second loop)
-        const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
-#pragma unroll 2
-        for (int32_t p = p0; p < p1; p++) {
-            const int64_t off = dia_offset[p];
-            const VT *vp = dia_val + (int64_t)p * n_b;
+    // the block's partial diagonals (Fig. 13, second loop)
+    const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
+    const int64_t xrow0 = r0 + tw;  // x index of the tile's first row at offset 0
+    int32_t p = p0;
+    auto group = [&](auto Dc) {
+        constexpr int DD = decltype(Dc)::value;
+        int64_t off[DD];
+#pragma unroll
+        for (int d = 0; d < DD; d++) off[d] = dia_offset[p + d];
+        VT v[DD][U][V];
+#pragma unroll
+        for (int d = 0; d < DD; d++) {
+            const VT *vp = dia_val + (int64_t)(p + d) * n_b;
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                const int32_t t = tw + (u * 32 + lane) * V;
-                if (t < rows) {
-                    VT v[V];
+                if (full || tl[u] < rows) {
                     if constexpr (VEC) {
-                        const uint4 r = ld_stream16(vp + t);
-                        memcpy(v, &r, 16);
+                        const uint4 r = ld_stream16(vp + tl[u]);
+                        memcpy(v[d][u], &r, 16);
                     } else {
-                        v[0] = vp[t];
+                        v[d][u][0] = vp[tl[u]];
                     }
-                    const int64_t j = r0 + t + off;
-                    if (t + V <= rows && j >= 0 && j + V <= n) {
-                        X xv[V];
-                        if constexpr (VEC) {
-                            if (x_vec && (j % V) == 0) {
-                                const uint4 r = __ldg(reinterpret_cast<const uint4 *>(x + j));
-                                memcpy(xv, &r, 16);
-                            } else {
+                } else {
 #pragma unroll
-                                for (int m = 0; m < V; m++) xv[m] = ldg_elem(x + j + m);
-                            }
-                        } else {
-                            xv[0] = ldg_elem(x + j);
-                        }
-#pragma unroll
-                        for (int m = 0; m < V; m++) acc[u][m] += widen(v[m]) * widen(xv[m]);
-                    } else {
-#pragma unroll
-                        for (int m = 0; m < V; m++) {
-                            const int64_t jm = j + m;
-                            if (t + m < rows && jm >= 0 && jm < n)
-                                acc[u][m] += widen(v[m]) * widen(ldg_elem(x + jm));
-                        }
-                    }
+                    for (int m = 0; m < V; m++) v[d][u][m] = VT(0);
                 }
             }
         }
+        X xv[DD][U][V];
+#pragma unroll
+        for (int d = 0; d < DD; d++) {
+            const int64_t jw = xrow0 + off[d];
+            // warp-uniform: the whole tile reads x inside [0, n)
+            if (full && jw >= 0 && jw + RW <= n) {
+                const bool al = x_al && ((jw % V) == 0);
+#pragma unroll
+                for (int u = 0; u < U; u++) load_x<X, V>(x, jw + (tl[u] - tw), al, xv[d][u]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; u++)
+#pragma unroll
+                    for (int m = 0; m < V; m++) {
+                        const int64_t jm = jw + (tl[u] - tw) + m;
+                        xv[d][u][m] = (tl[u] + m < rows && jm >= 0 && jm < n) ? ldg_elem(x + jm)
+                                                                              : X(0);
+                    }
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < DD; d++)
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int m = 0; m < V; m++) acc[u][m] += widen(v[d][u][m]) * widen(xv[d][u][m]);
+        p += DD;
+    };
+    for (; p + D <= p1;) group(std::integral_constant<int, D>{});
+    for (; p < p1;) group(std::integral_constant<int, 1>{});
 
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int32_t t = tw + (u * 32 + lane) * V;
+    for (int u = 0; u < U; u++) {
 #pragma unroll
-            for (int m = 0; m < V; m++)
-                if (t + m < rows) y[r0 + t + m] = acc[u][m];
-        }
+        for (int m = 0; m < V; m++)
+            if (tl[u] + m < rows) y[r0 + tl[u] + m] = acc[u][m];
     }
 }
 
-// Plain CSR (Fig. 2): S lanes per row, lanes stride over the row's entries,
-// butterfly reduction.  All lanes of a warp run the same number of iterations.
-template <int S>
-__device__ __forceinline__ void csr_rows(int64_t n, const int32_t *__restrict__ rp,
-                                         const int32_t *__restrict__ col,
-                                         const double *__restrict__ val,
-                                         const double *__restrict__ x, double *__restrict__ y)
-{
-    constexpr int RPW = 32 / S;
-    const int lane = threadIdx.x & 31, sub = lane & (S - 1);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t wr = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RPW; wr < n;
-         wr += nwarps * RPW) {
-        const int64_t row = wr + lane / S;
-        double s = 0.0;
-        if (row < n) {
-            const int32_t a = rp[row], b = rp[row + 1];
-            for (int32_t k = a + sub; k < b; k += S) s += val[k] * __ldg(x + col[k]);
-        }
-#pragma unroll
-        for (int d = S / 2; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-        if (sub == 0 && row < n) y[row] = s;
-    }
-}
+// Plain CSR (Fig. 2) as a CSR-stream kernel (Greathouse & Daga, SC 2014): a
+// CTA owns CSR_ROWS consecutive rows, whose entries are contiguous in val and
+// col_ind.  They are streamed through shared memory CSR_CHUNK at a time as
+// products val[k] * x[col_ind[k]] (coalesced loads, many in flight), then
+// each thread adds up the products of its own row inside the chunk.
+constexpr int CSR_THREADS = 256;
+constexpr int CSR_ROWS = 256;
+constexpr int CSR_CHUNK = 2048;
 
-// Lanes per row from the mean row length c = nnz / n, decided on the device
-// (every thread reads row_ptr[n]) so the launch needs no host read-back.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(CSR_THREADS)
 k_csr_spmv(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
            const double *__restrict__ val, const double *__restrict__ x, double *__restrict__ y)
 {
-    const double c = (double)__ldg(rp + n) / (double)n;
-    if (c <= 3.0) csr_rows<2>(n, rp, col, val, x, y);
-    else if (c <= 6.0) csr_rows<4>(n, rp, col, val, x, y);
-    else if (c <= 12.0) csr_rows<8>(n, rp, col, val, x, y);
-    else if (c <= 24.0) csr_rows<16>(n, rp, col, val, x, y);
-    else csr_rows<32>(n, rp, col, val, x, y);
+    __shared__ double prod[CSR_CHUNK];
+    const int64_t r0 = (int64_t)blockIdx.x * CSR_ROWS;
+    const int64_t r1 = (r0 + CSR_ROWS < n) ? r0 + CSR_ROWS : n;
+    const int64_t i = r0 + threadIdx.x;
+    const int32_t a = i < r1 ? rp[i] : 0, b = i < r1 ? rp[i + 1] : 0;
+    const int32_t k0 = rp[r0], k1 = rp[r1];
+    double s = 0.0;
+    for (int32_t c0 = k0; c0 < k1; c0 += CSR_CHUNK) {
+        const int32_t c1 = (k1 - c0 < CSR_CHUNK) ? k1 : c0 + CSR_CHUNK;
+#pragma unroll 4
+        for (int32_t k = c0 + threadIdx.x; k < c1; k += CSR_THREADS)
+            prod[k - c0] = val[k] * __ldg(x + col[k]);
+        __syncthreads();
+        const int32_t lo = a > c0 ? a : c0, hi = b < c1 ? b : c1;
+        for (int32_t k = lo; k < hi; k++) s += prod[k - c0];
+        __syncthreads();
+    }
+    if (i < r1) y[i] = s;
 }
 
 __global__ void k_stream(int64_t N, const double *__restrict__ A, const double *__restrict__ B,
@@ -236,26 +269,57 @@ struct Variant {
     int rw;  // rows per warp tile
 };
 
+// Tile shapes of the 16-byte-vector kernel: (U vectors per lane, D diagonals
+// per load group).  Index = the handle's variant id.
 template <typename VT>
-Variant pick_variant(int32_t n_b)
+Variant vec_variant(int id)
 {
     constexpr int V = Tr<VT>::V;
-    const bool vec = (n_b % V) == 0;
-    if (vec) {
-        if (n_b >= 2 * 32 * V * 2) return {(const void *)k_mhdc_spmv<VT, 2, true>, 32 * V * 2};
-        return {(const void *)k_mhdc_spmv<VT, 1, true>, 32 * V};
+    switch (id) {
+    case 0: return {(const void *)k_mhdc_spmv<VT, 1, 4, true>, 32 * V};
+    case 1: return {(const void *)k_mhdc_spmv<VT, 2, 2, true>, 64 * V};
+    case 2: return {(const void *)k_mhdc_spmv<VT, 2, 4, true>, 64 * V};
+    case 3: return {(const void *)k_mhdc_spmv<VT, 1, 8, true>, 32 * V};
+    case 4: return {(const void *)k_mhdc_spmv<VT, 4, 2, true>, 128 * V};
+    default: return {(const void *)k_mhdc_spmv<VT, 1, 2, true>, 32 * V};
     }
-    if (n_b >= 32 * 4) return {(const void *)k_mhdc_spmv<VT, 4, false>, 32 * 4};
-    return {(const void *)k_mhdc_spmv<VT, 1, false>, 32};
 }
 
-Variant variant_for(const mhdc_matrix *A)
+template <typename VT>
+Variant pick_variant(int32_t n_b, int id)
+{
+    constexpr int V = Tr<VT>::V;
+    if ((n_b % V) != 0) {  // dia_val rows not 16-byte aligned: element loads
+        if (n_b >= 32 * 4) return {(const void *)k_mhdc_spmv<VT, 4, 2, false>, 32 * 4};
+        return {(const void *)k_mhdc_spmv<VT, 1, 4, false>, 32};
+    }
+    if (id < 0) id = (n_b >= 64 * V) ? 2 : 0;
+    return vec_variant<VT>(id);
+}
+
+Variant variant_for(const mhdc_matrix *A, int id)
 {
     switch (A->dtype) {
-    case MHDC_F64: return pick_variant<double>(A->n_b);
-    case MHDC_F32: return pick_variant<float>(A->n_b);
-    default: return pick_variant<__nv_bfloat16>(A->n_b);
+    case MHDC_F64: return pick_variant<double>(A->n_b, id);
+    case MHDC_F32: return pick_variant<float>(A->n_b, id);
+    default: return pick_variant<__nv_bfloat16>(A->n_b, id);
     }
+}
+
+int launch_variant(const mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStream_t stream)
+{
+    const Variant v = variant_for(A, id);
+    int32_t tpb = (int32_t)((A->n_b + v.rw - 1) / v.rw);
+    int64_t tiles = (int64_t)tpb * A->n_blocks;
+    const int64_t grid = (tiles + SPMV_WARPS - 1) / SPMV_WARPS;
+    int64_t n = A->n;
+    int32_t n_b = A->n_b;
+    const void *dv = A->dia_val, *cv = A->csr_val;
+    const int32_t *dp = A->dia_ptr, *doff = A->dia_offset, *crp = A->csr_row_ptr, *cc = A->csr_col;
+    void *args[] = {&n, &n_b, &tpb, &tiles, (void *)&dp, (void *)&doff, (void *)&dv, (void *)&crp,
+                    (void *)&cc, (void *)&cv, (void *)&d_x, &d_y};
+    MHDC_CUDA_TRY(cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(SPMV_THREADS), args, 0, stream));
+    return MHDC_OK;
 }
 
 }  // namespace
@@ -263,31 +327,55 @@ Variant variant_for(const mhdc_matrix *A)
 int spmv_grid_for(const mhdc_matrix *A)
 {
     if (A->n == 0) return 0;
-    const Variant v = variant_for(A);
+    const Variant v = variant_for(A, A->variant);
     const int64_t tpb = (A->n_b + v.rw - 1) / v.rw;
-    const int64_t tiles = tpb * A->n_blocks;
-    int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn, SPMV_THREADS, 0);
-    if (occ < 1) occ = 1;
-    const int64_t need = (tiles + SPMV_WARPS - 1) / SPMV_WARPS;
-    const int64_t cap = (int64_t)num_sms() * occ;
-    return (int)(need < cap ? need : cap);
+    return (int)((tpb * A->n_blocks + SPMV_WARPS - 1) / SPMV_WARPS);
 }
 
 int launch_spmv(const mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream)
 {
     if (A->n == 0) return MHDC_OK;
-    const Variant v = variant_for(A);
-    int32_t tpb = (int32_t)((A->n_b + v.rw - 1) / v.rw);
-    int64_t tiles = (int64_t)tpb * A->n_blocks;
-    int grid = A->spmv_grid > 0 ? A->spmv_grid : spmv_grid_for(A);
-    int64_t n = A->n;
-    int32_t n_b = A->n_b;
-    const void *dv = A->dia_val, *cv = A->csr_val;
-    const int32_t *dp = A->dia_ptr, *doff = A->dia_offset, *crp = A->csr_row_ptr, *cc = A->csr_col;
-    void *args[] = {&n, &n_b, &tpb, &tiles, (void *)&dp, (void *)&doff, (void *)&dv, (void *)&crp,
-                    (void *)&cc, (void *)&cv, (void *)&d_x, &d_y};
-    MHDC_CUDA_TRY(cudaLaunchKernel(v.fn, dim3(grid), dim3(SPMV_THREADS), args, 0, stream));
+    return launch_variant(A, A->variant, d_x, d_y, stream);
+}
+
+int tune_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream, int32_t *best,
+              float *times_us)
+{
+    if (A->n == 0) {
+        if (best) *best = -1;
+        return MHDC_OK;
+    }
+    cudaEvent_t e0, e1;
+    MHDC_CUDA_TRY(cudaEventCreate(&e0));
+    MHDC_CUDA_TRY(cudaEventCreate(&e1));
+    int best_id = -1;
+    float best_t = 0.f;
+    const int reps = 20;
+    for (int id = 0; id < MHDC_NUM_VARIANTS; id++) {
+        int rc = MHDC_OK;
+        for (int r = 0; r < 3 && rc == MHDC_OK; r++) rc = launch_variant(A, id, d_x, d_y, stream);
+        cudaEventRecord(e0, stream);
+        for (int r = 0; r < reps && rc == MHDC_OK; r++) rc = launch_variant(A, id, d_x, d_y, stream);
+        cudaEventRecord(e1, stream);
+        if (rc != MHDC_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rc;
+        }
+        MHDC_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const float us = ms * 1e3f / reps;
+        if (times_us) times_us[id] = us;
+        if (best_id < 0 || us < best_t) {
+            best_id = id;
+            best_t = us;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    A->variant = best_id;
+    if (best) *best = best_id;
     return MHDC_OK;
 }
 
@@ -295,10 +383,8 @@ int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *v
                const double *x, double *y, cudaStream_t stream)
 {
     if (n == 0) return MHDC_OK;
-    const int64_t need = (n + 63) / 64;
-    const int64_t cap = (int64_t)num_sms() * 8;
-    const unsigned grid = (unsigned)(need < cap ? need : cap);
-    k_csr_spmv<<<grid, 256, 0, stream>>>(n, rp, col, val, x, y);
+    const int64_t grid = (n + CSR_ROWS - 1) / CSR_ROWS;
+    k_csr_spmv<<<(unsigned)grid, CSR_THREADS, 0, stream>>>(n, rp, col, val, x, y);
     MHDC_LAUNCH_CHECK("k_csr_spmv");
     return MHDC_OK;
 }

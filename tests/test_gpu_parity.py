@@ -263,3 +263,30 @@ def test_stream_bench(mh):
                                      np.ones(N)) if ind else \
             oracle.stream_direct(Av.cpu().numpy(), Bv.cpu().numpy(), np.ones(N))
         assert np.array_equal(Cv.cpu().numpy(), ref)
+
+
+def test_every_variant_is_bit_identical_and_tune_picks_one(mh):
+    t = torch()
+    for name, scale, n_b in (("stencil27_128", 0.375, 4096), ("scattered_4m", 1 / 64, 2048),
+                             ("stencil7_32", 1.0, 1024)):
+        A = synth.config_matrix(name, scale)
+        for dt in DTYPES:
+            h, M = check_build(mh, A, n_b, 0.6, dt)
+            xd, _ = x_device(synth.uniform_vector(A.n, 5), dt)
+            ys = []
+            for v in range(-1, mh.MHDC_NUM_VARIANTS):
+                mh.mhdc_set_variant(h, v)
+                y = y_empty(A.n, dt)
+                mh.mhdc_spmv(h, xd, y)
+                ys.append(y)
+            for y in ys[1:]:
+                assert t.equal(y, ys[0]), (name, dt)
+            check_spmv(mh, h, M, A, synth.uniform_vector(A.n, 5), dt)
+            best, times = mh.mhdc_tune(h, xd, ys[0])
+            assert 0 <= best < mh.MHDC_NUM_VARIANTS and h.info["variant"] == best
+            assert all(tt > 0 for tt in times)
+            y = y_empty(A.n, dt)
+            mh.mhdc_spmv(h, xd, y)
+            assert t.equal(y, ys[1])
+    with pytest.raises(mh.MhdcError):
+        mh.mhdc_set_variant(h, mh.MHDC_NUM_VARIANTS)
