@@ -164,9 +164,12 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
 
 /*
  * Tile shapes of the M-HDC product (no counterpart in the paper, whose kernel
- * is a CPU loop nest): variant v in [0, MHDC_NUM_VARIANTS) sets how many rows
- * a warp owns and how many diagonals it loads before accumulating.  All
- * variants compute the same sums in the same order per row (bit-identical y).
+ * is a CPU loop nest): variants 0-5 load dia_val into registers (a warp owns
+ * 32 x 16 B x U rows and loads D diagonals before accumulating); variants 6-9
+ * stream dia_val through shared memory with TMA bulk copies (one producer
+ * warp, several consumer warps, an mbarrier ring; they need n_b * value size
+ * to be a multiple of 16 bytes, else they run variant -1).  All variants
+ * compute the same sums in the same order per row (bit-identical y).
  *
  * mhdc_set_variant -- use variant v for this handle (-1: default chosen from n_b).
  * mhdc_tune        -- time every variant on (d_x, d_y) (overwriting d_y), keep
@@ -174,10 +177,18 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  *                     times_us is not NULL, each variant's mean time in
  *                     microseconds to times_us[MHDC_NUM_VARIANTS].  Synchronous.
  */
-#define MHDC_NUM_VARIANTS 6
+#define MHDC_NUM_VARIANTS 10
 int mhdc_set_variant(mhdc_handle A, int32_t v);
 int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *best,
               float *times_us);
+
+/*
+ * mhdc_check -- read and clear the handle's device status word: returns
+ * MHDC_ERR_TIMEOUT if a bounded device-side wait of an earlier product on
+ * this handle gave up (its y is then incomplete), else MHDC_OK.
+ * Synchronizes the device.
+ */
+int mhdc_check(mhdc_handle A);
 
 /* mhdc_destroy -- free the handle and its device arrays (NULL is a no-op). */
 int mhdc_destroy(mhdc_handle A);

@@ -23,7 +23,7 @@ __all__ = [
     "MHDC_F64", "MHDC_F32", "MHDC_BF16", "MhdcError", "Matrix", "lib", "mhdc_build",
     "hdc_build", "mhdc_spmv", "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
     "mhdc_info", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
-    "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS",
+    "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "mhdc_check",
 ]
 
 MHDC_F64, MHDC_F32, MHDC_BF16 = 0, 1, 2
@@ -63,10 +63,11 @@ _SIGS = {
     "mhdc_last_error": [],
     "mhdc_stream_bench": [_I64, _P, _P, _P, _P, _I32, _P],
     "mhdc_set_variant": [_P, _I32],
+    "mhdc_check": [_P],
     "mhdc_tune": [_P, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
 }
 
-MHDC_NUM_VARIANTS = 6
+MHDC_NUM_VARIANTS = 10
 
 
 def lib(build_if_missing: bool = False):
@@ -300,3 +301,8 @@ def mhdc_tune(A: Matrix, x, y, stream=None):
                            C.byref(best), times), "mhdc_tune")
     A._info = None
     return best.value, [float(t) for t in times]
+
+
+def mhdc_check(A: Matrix):
+    """Raise MhdcError(MHDC_ERR_TIMEOUT) if a bounded device wait gave up."""
+    _check(lib().mhdc_check(C.c_void_p(A.handle)), "mhdc_check")

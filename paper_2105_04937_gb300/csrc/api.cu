@@ -176,6 +176,23 @@ int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *
     return tune_spmv(A, d_x, d_y, (cudaStream_t)stream, best, times_us);
 }
 
+int mhdc_check(mhdc_handle A)
+{
+    if (!A) {
+        set_error_msg("mhdc_check: null handle");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    int h = 0;
+    MHDC_CUDA_TRY(cudaDeviceSynchronize());
+    MHDC_CUDA_TRY(cudaMemcpy(&h, A->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        MHDC_CUDA_TRY(cudaMemset(A->status, 0, sizeof(int)));
+        set_error_msg("a bounded device-side wait gave up");
+        return MHDC_ERR_TIMEOUT;
+    }
+    return MHDC_OK;
+}
+
 int mhdc_destroy(mhdc_handle A)
 {
     free_matrix(A);

@@ -588,6 +588,7 @@ void free_matrix(mhdc_matrix *A)
     cudaFree(A->csr_val);
     cudaFree(A->x_stage);
     cudaFree(A->y_stage);
+    cudaFree(A->status);
     delete A;
 }
 
@@ -595,6 +596,8 @@ static int build_into(mhdc_matrix *A, const int32_t *rp, const int32_t *col, con
                       cudaStream_t st)
 {
     const int64_t n = A->n;
+    RC(dalloc_raw((void **)&A->status, sizeof(int)));
+    MHDC_CUDA_TRY(cudaMemsetAsync(A->status, 0, sizeof(int), st));
     if (n == 0) {
         RC(dalloc_raw((void **)&A->dia_ptr, sizeof(int32_t)));
         RC(dalloc_raw((void **)&A->csr_row_ptr, sizeof(int32_t)));

@@ -26,6 +26,7 @@ struct mhdc_matrix {
     int64_t bytes_device = 0;
     int spmv_grid = 0;               // CTAs of the SpMV launch
     int variant = -1;                // SpMV tile shape (-1: chosen from n_b)
+    int *status = nullptr;           // device word: bit 0 = a bounded wait gave up
 };
 
 namespace mhdc {
@@ -60,6 +61,10 @@ int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *v
 int launch_stream_bench(int64_t N, const double *A, const double *B, const int32_t *I, double *C,
                         int indirect, cudaStream_t stream);
 int spmv_grid_for(const mhdc_matrix *A);
+bool tma_supported(const mhdc_matrix *A);
+int launch_spmv_tma(const mhdc_matrix *A, int shape, const void *d_x, void *d_y,
+                    cudaStream_t stream);
+constexpr int NUM_REG_VARIANTS = 6;
 int tune_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream, int32_t *best,
               float *times_us);
 

@@ -308,6 +308,10 @@ Variant variant_for(const mhdc_matrix *A, int id)
 
 int launch_variant(const mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStream_t stream)
 {
+    if (id >= NUM_REG_VARIANTS) {
+        if (tma_supported(A)) return launch_spmv_tma(A, id - NUM_REG_VARIANTS, d_x, d_y, stream);
+        id = -1;
+    }
     const Variant v = variant_for(A, id);
     int32_t tpb = (int32_t)((A->n_b + v.rw - 1) / v.rw);
     int64_t tiles = (int64_t)tpb * A->n_blocks;
@@ -327,7 +331,7 @@ int launch_variant(const mhdc_matrix *A, int id, const void *d_x, void *d_y, cud
 int spmv_grid_for(const mhdc_matrix *A)
 {
     if (A->n == 0) return 0;
-    const Variant v = variant_for(A, A->variant);
+    const Variant v = variant_for(A, A->variant < NUM_REG_VARIANTS ? A->variant : -1);
     const int64_t tpb = (A->n_b + v.rw - 1) / v.rw;
     return (int)((tpb * A->n_blocks + SPMV_WARPS - 1) / SPMV_WARPS);
 }

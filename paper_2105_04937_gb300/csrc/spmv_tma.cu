@@ -1,0 +1,405 @@
+// M-HDC y = A x (Fig. 13) with the diagonal values streamed by TMA.
+//
+// A persistent CTA = NCW consumer warps + 1 producer warp.  Work unit = R
+// consecutive rows of one row block (R = NCW * 32 lanes * U vectors * 16 B).
+// For every diagonal of the unit's block, the producer's elected lane issues
+// one 1-D bulk copy (cp.async.bulk) of the unit's R values (contiguous in
+// dia_val) into a ring of STAGES shared-memory buffers, completing on the
+// stage's "full" mbarrier.  Consumers first issue the x loads of the next D
+// diagonals (their addresses depend only on the offsets), then wait for the
+// stages, read their rows' values from shared memory (16 B per lane,
+// conflict-free), accumulate in registers and release the stages on the
+// "empty" mbarriers.  The CSR remainder rows of a unit are added by the
+// consumers from global memory before the diagonals; y is written once.
+//
+// Every mbarrier wait is bounded: a wait that gives up sets bit 0 of
+// *status, the waiting warp stops, and the producer drains the copies it
+// still has in flight (again bounded) before the CTA exits.
+#include <cstring>
+#include <type_traits>
+
+#include "mhdc_internal.cuh"
+
+namespace mhdc {
+namespace {
+
+template <typename VT>
+struct TrT;
+template <>
+struct TrT<double> {
+    using X = double;
+    using Y = double;
+    using Acc = double;
+};
+template <>
+struct TrT<float> {
+    using X = float;
+    using Y = float;
+    using Acc = float;
+};
+template <>
+struct TrT<__nv_bfloat16> {
+    using X = __nv_bfloat16;
+    using Y = float;
+    using Acc = float;
+};
+
+__device__ __forceinline__ double wide(double v) { return v; }
+__device__ __forceinline__ float wide(float v) { return v; }
+__device__ __forceinline__ float wide(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// A wait gives up after WAIT_LIMIT_NS of global-timer time (or SPIN_LIMIT
+// polls, whichever comes first); a correct pipeline never gets near either.
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
+constexpr uint32_t SPIN_LIMIT = 1u << 30;
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `bar` with the given parity to complete; false if
+// the bounded spin gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1; i < SPIN_LIMIT; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 0 && global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    }
+    return false;
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size % 16 == 0),
+// completing `bytes` of transaction count on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+template <typename X, int V>
+__device__ __forceinline__ void load_xv(const X *__restrict__ x, int64_t j, bool aligned, X (&xv)[V])
+{
+    if (aligned) {
+        const uint4 r = __ldg(reinterpret_cast<const uint4 *>(x + j));
+        memcpy(xv, &r, 16);
+        return;
+    }
+#pragma unroll
+    for (int m = 0; m < V; m++) xv[m] = __ldg(x + j + m);
+}
+
+template <typename VT, int NCW, int U, int D, int STAGES>
+struct TmaCfg {
+    static constexpr int V = 16 / sizeof(VT);
+    static constexpr int NT = NCW * 32;          // consumer threads
+    static constexpr int R = NT * U * V;         // rows per unit
+    static constexpr int STAGE_BYTES = R * (int)sizeof(VT);
+    static constexpr int THREADS = NT + 32;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES;
+};
+
+template <typename VT, int NCW, int U, int D, int STAGES>
+__global__ void __launch_bounds__(TmaCfg<VT, NCW, U, D, STAGES>::THREADS)
+k_mhdc_spmv_tma(int64_t n, int32_t n_b, int32_t upb, int64_t n_units,
+                const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
+                const VT *__restrict__ dia_val, const int32_t *__restrict__ csr_row_ptr,
+                const int32_t *__restrict__ csr_col, const VT *__restrict__ csr_val,
+                const typename TrT<VT>::X *__restrict__ x, typename TrT<VT>::Y *__restrict__ y,
+                int *__restrict__ status)
+{
+    using C = TmaCfg<VT, NCW, U, D, STAGES>;
+    using Acc = typename TrT<VT>::Acc;
+    using X = typename TrT<VT>::X;
+    constexpr int V = C::V, NT = C::NT, R = C::R;
+    extern __shared__ __align__(128) uint8_t ring[];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == NCW) {
+        // ---------------- producer (one elected lane)
+        if (lane != 0) return;
+        int stage = 0;
+        uint32_t phase = 0;
+        int64_t issued = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            const int64_t ib = u / upb;
+            const int32_t t0 = (int32_t)(u - ib * upb) * R;
+            const int64_t r0 = ib * (int64_t)n_b;
+            const int32_t rows = (int32_t)((n - r0 < n_b) ? (n - r0) : n_b);
+            if (t0 >= rows) continue;
+            const int32_t ru = (rows - t0 < R) ? rows - t0 : R;
+            const uint32_t bytes = (uint32_t)(((int64_t)ru * sizeof(VT) + 15) & ~(int64_t)15);
+            const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
+            for (int32_t p = p0; p < p1; p++) {
+                if (!mbar_wait(&empty[stage], phase ^ 1)) {
+                    atomicOr(status, 1);
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[stage], bytes);
+                bulk_load(ring + (size_t)stage * C::STAGE_BYTES,
+                          dia_val + (int64_t)p * n_b + t0, bytes, &full[stage]);
+                issued++;
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+            }
+        }
+        if (!ok) {
+            // drain: wait (bounded) for the copies still in flight
+            const int64_t k = issued < STAGES ? issued : STAGES;
+            for (int64_t q = 1; q <= k; q++) {
+                int s = stage - (int)q;
+                uint32_t ph = phase;
+                if (s < 0) {
+                    s += STAGES;
+                    ph ^= 1;
+                }
+                mbar_wait(&full[s], ph);
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumers
+    int stage = 0;
+    uint32_t phase = 0;
+    for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const int64_t ib = u / upb;
+        const int32_t t0 = (int32_t)(u - ib * upb) * R;
+        const int64_t r0 = ib * (int64_t)n_b;
+        const int32_t rows = (int32_t)((n - r0 < n_b) ? (n - r0) : n_b);
+        if (t0 >= rows) continue;
+        const int32_t ru = (rows - t0 < R) ? rows - t0 : R;
+        const bool full_unit = ru == R;
+
+        int32_t tl[U];  // first row (within the unit) of each of this lane's vectors
+#pragma unroll
+        for (int k = 0; k < U; k++) tl[k] = (k * NT + tid) * V;
+
+        Acc acc[U][V];
+#pragma unroll
+        for (int k = 0; k < U; k++)
+#pragma unroll
+            for (int m = 0; m < V; m++) acc[k][m] = Acc(0);
+
+        // CSR remainder rows of the unit (Fig. 13, first loop)
+        if (csr_row_ptr[r0 + t0] != csr_row_ptr[r0 + t0 + ru]) {
+#pragma unroll
+            for (int k = 0; k < U; k++)
+#pragma unroll
+                for (int m = 0; m < V; m++) {
+                    const int32_t t = tl[k] + m;
+                    if (t < ru) {
+                        const int64_t i = r0 + t0 + t;
+                        const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
+                        for (int32_t q = a; q < b; q++)
+                            acc[k][m] += wide(csr_val[q]) * wide(__ldg(x + csr_col[q]));
+                    }
+                }
+        }
+
+        // the block's diagonals, D stages at a time (Fig. 13, second loop)
+        const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
+        const int64_t xw = r0 + t0 + (int64_t)warp * 32 * V;  // this warp's first row, k = 0
+        bool ok = true;
+        int32_t p = p0;
+        auto group = [&](auto Dc) {
+            constexpr int DD = decltype(Dc)::value;
+            X xv[DD][U][V];
+#pragma unroll
+            for (int d = 0; d < DD; d++) {
+                const int64_t off = dia_offset[p + d];
+#pragma unroll
+                for (int k = 0; k < U; k++) {
+                    const int64_t jw = xw + (int64_t)k * NT * V + off;  // warp-uniform
+                    if (full_unit && jw >= 0 && jw + 32 * V <= n) {
+                        const int64_t j = jw + lane * V;
+                        load_xv<X, V>(x, j, ((reinterpret_cast<uintptr_t>(x + jw)) & 15) == 0,
+                                      xv[d][k]);
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < V; m++) {
+                            const int64_t jm = jw + lane * V + m;
+                            xv[d][k][m] = (tl[k] + m < ru && jm >= 0 && jm < n) ? __ldg(x + jm)
+                                                                                 : X(0);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < DD; d++) {
+                int s = stage + d;
+                uint32_t ph = phase;
+                if (s >= STAGES) {
+                    s -= STAGES;
+                    ph ^= 1;
+                }
+                if (!mbar_wait(&full[s], ph)) ok = false;
+            }
+            if (!ok) return;
+#pragma unroll
+            for (int d = 0; d < DD; d++) {
+                int s = stage + d;
+                if (s >= STAGES) s -= STAGES;
+                const VT *sv = reinterpret_cast<const VT *>(ring + (size_t)s * C::STAGE_BYTES);
+#pragma unroll
+                for (int k = 0; k < U; k++) {
+                    VT v[V];
+                    const uint4 r = *reinterpret_cast<const uint4 *>(sv + tl[k]);
+                    memcpy(v, &r, 16);
+#pragma unroll
+                    for (int m = 0; m < V; m++) acc[k][m] += wide(v[m]) * wide(xv[d][k][m]);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int d = 0; d < DD; d++) {
+                int s = stage + d;
+                if (s >= STAGES) s -= STAGES;
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+            stage += DD;
+            if (stage >= STAGES) {
+                stage -= STAGES;
+                phase ^= 1;
+            }
+            p += DD;
+        };
+        while (ok && p + D <= p1) group(std::integral_constant<int, D>{});
+        while (ok && p < p1) group(std::integral_constant<int, 1>{});
+        if (!ok) {
+            if (lane == 0) atomicOr(status, 1);
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < U; k++)
+#pragma unroll
+            for (int m = 0; m < V; m++)
+                if (tl[k] + m < ru) y[r0 + t0 + tl[k] + m] = acc[k][m];
+    }
+}
+
+int num_sms_tma()
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+template <typename VT, int NCW, int U, int D, int STAGES>
+int launch_tma_cfg(const mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t st)
+{
+    using Cf = TmaCfg<VT, NCW, U, D, STAGES>;
+    auto kern = k_mhdc_spmv_tma<VT, NCW, U, D, STAGES>;
+    static int occ = -1;
+    if (occ < 0) {
+        MHDC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)Cf::SMEM));
+        int o = 0;
+        MHDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, Cf::THREADS, Cf::SMEM));
+        occ = o > 0 ? o : 1;
+    }
+    const int32_t upb = (int32_t)((A->n_b + Cf::R - 1) / Cf::R);
+    const int64_t units = (int64_t)upb * A->n_blocks;
+    int64_t grid = (int64_t)num_sms_tma() * occ;
+    if (grid > units) grid = units;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, Cf::THREADS, Cf::SMEM, st>>>(
+        A->n, A->n_b, upb, units, A->dia_ptr, A->dia_offset, static_cast<const VT *>(A->dia_val),
+        A->csr_row_ptr, A->csr_col, static_cast<const VT *>(A->csr_val),
+        static_cast<const typename TrT<VT>::X *>(d_x), static_cast<typename TrT<VT>::Y *>(d_y),
+        A->status);
+    MHDC_LAUNCH_CHECK("k_mhdc_spmv_tma");
+    return MHDC_OK;
+}
+
+template <typename VT>
+int launch_tma_typed(const mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_t st)
+{
+    switch (shape) {
+    case 0: return launch_tma_cfg<VT, 4, 2, 1, 16>(A, d_x, d_y, st);
+    case 1: return launch_tma_cfg<VT, 4, 2, 2, 16>(A, d_x, d_y, st);
+    case 2: return launch_tma_cfg<VT, 8, 1, 2, 16>(A, d_x, d_y, st);
+    default: return launch_tma_cfg<VT, 4, 1, 2, 24>(A, d_x, d_y, st);
+    }
+}
+
+}  // namespace
+
+bool tma_supported(const mhdc_matrix *A)
+{
+    return (A->n_b * (int64_t)value_size(A->dtype)) % 16 == 0;
+}
+
+int launch_spmv_tma(const mhdc_matrix *A, int shape, const void *d_x, void *d_y,
+                    cudaStream_t stream)
+{
+    switch (A->dtype) {
+    case MHDC_F64: return launch_tma_typed<double>(A, shape, d_x, d_y, stream);
+    case MHDC_F32: return launch_tma_typed<float>(A, shape, d_x, d_y, stream);
+    default: return launch_tma_typed<__nv_bfloat16>(A, shape, d_x, d_y, stream);
+    }
+}
+
+}  // namespace mhdc

@@ -74,6 +74,7 @@ def check_spmv(mh, h, M, A, x64, dtype):
     y = y_empty(A.n, dtype)
     mh.mhdc_spmv(h, xd, y)
     torch().cuda.synchronize()
+    mh.mhdc_check(h)
     yg = y.double().cpu().numpy()
     assert np.all(np.isfinite(yg))
     y_st = oracle.mhdc_spmv(M, xs)
