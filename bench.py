@@ -357,6 +357,39 @@ def main():
                              "alpha": round(ih["alpha"], 4), "beta": round(ih["beta"], 4)}
         Hh.destroy()
         extra["mhdc_vs_csr_speedup"] = round(extra["csr_fp64"]["kernel_us"] / (kern_ms * 1e3), 3)
+        # cuSPARSE CSR SpMV through torch.sparse, as a library reference for the CSR baseline
+        try:
+            Acsr = torch.sparse_csr_tensor(rp, col, val, size=(A.n, A.n))
+            xc = x.view(-1, 1)
+
+            def cusp_step():
+                torch.mv(Acsr, x)
+            tot, mean, _ = time_launches(cusp_step, min(args.steps, 1000), args.warmup, stream, torch)
+            extra["csr_cusparse_ref"] = {"gflops": round(gflops(A.nnz, mean / 1e3), 2),
+                                         "gbs": round(csr_bytes / (mean / 1e3) / 1e9, 1),
+                                         "step_us": round(mean * 1e3, 2),
+                                         "note": "torch.mv on a torch.sparse_csr_tensor (library)"}
+            del xc
+        except Exception as e:  # pragma: no cover - depends on the torch build
+            extra["csr_cusparse_ref"] = {"unavailable": str(e)[:120]}
+        # memory benchmarks: the paper's direct / indirect kernels (Sec. 6.2) and a
+        # read-only probe (the ceiling for a read-dominated kernel such as SpMV)
+        Nm = 1 << 26
+        Am = torch.rand(Nm, dtype=torch.float64, device="cuda")
+        Bm = torch.rand(Nm, dtype=torch.float64, device="cuda")
+        Cm = torch.zeros(Nm, dtype=torch.float64, device="cuda")
+        Im = torch.arange(Nm, dtype=torch.int32, device="cuda")
+        wm = {}
+        for nm_, ind, per in (("direct", False, 32), ("indirect", True, 36)):
+            tot, mean, _ = time_launches(lambda: mh.mhdc_stream_bench(Am, Bm, Im, Cm, ind, stream),
+                                         20, 3, stream, torch)
+            wm[nm_] = round(per * Nm / (mean / 1e3) / 1e9, 1)
+        ro = torch.empty(mh.mhdc_read_bench_ctas(), dtype=torch.float64, device="cuda")
+        big = torch.cat([Am, Bm])
+        tot, mean, _ = time_launches(lambda: mh.mhdc_read_bench(big, ro, stream), 20, 3, stream, torch)
+        wm["read_only"] = round(8 * big.numel() / (mean / 1e3) / 1e9, 1)
+        extra["w_mem_gbs"] = wm
+        del Am, Bm, Cm, Im, big
 
     # ---- end to end through the host-buffer entry point (pinned memory)
     xh = torch.from_numpy(x_host).pin_memory()
@@ -382,6 +415,7 @@ def main():
     if rank == 0 and ws == 1 and not args.skip_cpu:
         cpu = cpu_baseline(A, args.cpu_seconds, log)
 
+    read_ceiling = extra.get("w_mem_gbs", {}).get("read_only")
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": ws,
@@ -399,7 +433,10 @@ def main():
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": None, "kernel": f"k_mhdc_spmv<double> variant {best_variant}",
                          "bytes_per_launch": info["bytes_model"],
-                         "kernel_us": round(kern_ms * 1e3, 3), "peak_source": peak_src},
+                         "kernel_us": round(kern_ms * 1e3, 3), "peak_source": peak_src,
+                         "read_only_ceiling_gbs": read_ceiling,
+                         "frac_of_read_only_ceiling": (round(achieved / read_ceiling, 4)
+                                                       if read_ceiling else None)},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,

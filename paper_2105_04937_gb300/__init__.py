@@ -24,6 +24,7 @@ __all__ = [
     "hdc_build", "mhdc_spmv", "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
     "mhdc_info", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
     "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "mhdc_check",
+    "mhdc_read_bench", "mhdc_read_bench_ctas",
 ]
 
 MHDC_F64, MHDC_F32, MHDC_BF16 = 0, 1, 2
@@ -64,6 +65,8 @@ _SIGS = {
     "mhdc_stream_bench": [_I64, _P, _P, _P, _P, _I32, _P],
     "mhdc_set_variant": [_P, _I32],
     "mhdc_check": [_P],
+    "mhdc_read_bench": [_I64, _P, _P, _P],
+    "mhdc_read_bench_ctas": [],
     "mhdc_tune": [_P, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
 }
 
@@ -306,3 +309,16 @@ def mhdc_tune(A: Matrix, x, y, stream=None):
 def mhdc_check(A: Matrix):
     """Raise MhdcError(MHDC_ERR_TIMEOUT) if a bounded device wait gave up."""
     _check(lib().mhdc_check(C.c_void_p(A.handle)), "mhdc_check")
+
+
+def mhdc_read_bench_ctas() -> int:
+    return int(lib().mhdc_read_bench_ctas())
+
+
+def mhdc_read_bench(A, out, stream=None):
+    """Read-only bandwidth probe: out[c] = sum of CTA c's share of A (float64)."""
+    import torch
+    _check_dev(A, torch.float64, None, "A")
+    _check_dev(out, torch.float64, mhdc_read_bench_ctas(), "out")
+    _check(lib().mhdc_read_bench(A.numel(), _ptr(A), _ptr(out), _stream(stream)), "mhdc_read_bench")
+    return out

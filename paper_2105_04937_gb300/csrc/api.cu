@@ -209,4 +209,15 @@ int mhdc_stream_bench(int64_t N, const double *d_A, const double *d_B, const int
     return launch_stream_bench(N, d_A, d_B, d_I, d_C, indirect, (cudaStream_t)stream);
 }
 
+int mhdc_read_bench(int64_t N, const double *d_A, double *d_out, void *stream)
+{
+    if (N < 0 || (N & 1) || (N > 0 && (!d_A || !d_out)) || ((uintptr_t)d_A & 15)) {
+        set_error_msg("mhdc_read_bench: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    return launch_read_bench(N, d_A, d_out, read_bench_grid(), (cudaStream_t)stream);
+}
+
+int mhdc_read_bench_ctas(void) { return read_bench_grid(); }
+
 }  // extern "C"

@@ -61,6 +61,8 @@ int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *v
 int launch_stream_bench(int64_t N, const double *A, const double *B, const int32_t *I, double *C,
                         int indirect, cudaStream_t stream);
 int spmv_grid_for(const mhdc_matrix *A);
+int launch_read_bench(int64_t N, const double *A, double *out, int grid, cudaStream_t stream);
+int read_bench_grid();
 bool tma_supported(const mhdc_matrix *A);
 int launch_spmv_tma(const mhdc_matrix *A, int shape, const void *d_x, void *d_y,
                     cudaStream_t stream);

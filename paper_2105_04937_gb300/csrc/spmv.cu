@@ -206,37 +206,82 @@ k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
     }
 }
 
-// Plain CSR (Fig. 2) as a CSR-stream kernel (Greathouse & Daga, SC 2014): a
-// CTA owns CSR_ROWS consecutive rows, whose entries are contiguous in val and
-// col_ind.  They are streamed through shared memory CSR_CHUNK at a time as
-// products val[k] * x[col_ind[k]] (coalesced loads, many in flight), then
-// each thread adds up the products of its own row inside the chunk.
+// Plain CSR (Fig. 2), warp-streamed: a warp owns 32 consecutive rows, whose
+// entries are contiguous in val and col_ind.  It walks that span CSR_UNR * 32
+// entries at a time: every lane first loads CSR_UNR (val, col) pairs
+// (coalesced, all independent), then their x values, writes the products to
+// the warp's shared-memory slice, and each lane adds the products that fall
+// in its own row, in column order.
 constexpr int CSR_THREADS = 256;
-constexpr int CSR_ROWS = 256;
-constexpr int CSR_CHUNK = 2048;
+constexpr int CSR_UNR = 8;
+constexpr int CSR_SPAN = 32 * CSR_UNR;
 
 __global__ void __launch_bounds__(CSR_THREADS)
 k_csr_spmv(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
            const double *__restrict__ val, const double *__restrict__ x, double *__restrict__ y)
 {
-    __shared__ double prod[CSR_CHUNK];
-    const int64_t r0 = (int64_t)blockIdx.x * CSR_ROWS;
-    const int64_t r1 = (r0 + CSR_ROWS < n) ? r0 + CSR_ROWS : n;
-    const int64_t i = r0 + threadIdx.x;
+    __shared__ double prod[CSR_THREADS / 32][CSR_SPAN];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t r0 = ((int64_t)blockIdx.x * (CSR_THREADS / 32) + wl) * 32;
+    if (r0 >= n) return;
+    const int64_t r1 = (r0 + 32 < n) ? r0 + 32 : n;
+    const int64_t i = r0 + lane;
     const int32_t a = i < r1 ? rp[i] : 0, b = i < r1 ? rp[i + 1] : 0;
     const int32_t k0 = rp[r0], k1 = rp[r1];
+    double *pw = prod[wl];
     double s = 0.0;
-    for (int32_t c0 = k0; c0 < k1; c0 += CSR_CHUNK) {
-        const int32_t c1 = (k1 - c0 < CSR_CHUNK) ? k1 : c0 + CSR_CHUNK;
-#pragma unroll 4
-        for (int32_t k = c0 + threadIdx.x; k < c1; k += CSR_THREADS)
-            prod[k - c0] = val[k] * __ldg(x + col[k]);
-        __syncthreads();
-        const int32_t lo = a > c0 ? a : c0, hi = b < c1 ? b : c1;
-        for (int32_t k = lo; k < hi; k++) s += prod[k - c0];
-        __syncthreads();
+    for (int32_t c0 = k0; c0 < k1; c0 += CSR_SPAN) {
+        double v[CSR_UNR];
+        int32_t c[CSR_UNR];
+#pragma unroll
+        for (int u = 0; u < CSR_UNR; u++) {
+            const int32_t k = c0 + u * 32 + lane;
+            v[u] = k < k1 ? __ldg(val + k) : 0.0;
+            c[u] = k < k1 ? __ldg(col + k) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < CSR_UNR; u++) {
+            const int32_t k = c0 + u * 32 + lane;
+            if (k < k1) pw[u * 32 + lane] = v[u] * __ldg(x + c[u]);
+        }
+        __syncwarp();
+        const int32_t hi0 = c0 + CSR_SPAN;
+        const int32_t lo = a > c0 ? a : c0, hi = b < hi0 ? b : hi0;
+        for (int32_t k = lo; k < hi; k++) s += pw[k - c0];
+        __syncwarp();
     }
     if (i < r1) y[i] = s;
+}
+
+// Read-only member of the memory benchmarks: out[cta] = sum of the CTA's
+// share of A (16-byte loads, 4 in flight per thread).
+__global__ void __launch_bounds__(256) k_read(int64_t N2, const double *__restrict__ A,
+                                              double *__restrict__ out)
+{
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    for (; i + 3 * st < N2; i += 4 * st) {
+        double2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = __ldg(reinterpret_cast<const double2 *>(A) + i + u * st);
+#pragma unroll
+        for (int u = 0; u < 4; u++) s += v[u].x + v[u].y;
+    }
+    for (; i < N2; i += st) {
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(A) + i);
+        s += v.x + v.y;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    __shared__ double ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += ws[w];
+        out[blockIdx.x] = t;
+    }
 }
 
 __global__ void k_stream(int64_t N, const double *__restrict__ A, const double *__restrict__ B,
@@ -387,11 +432,22 @@ int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *v
                const double *x, double *y, cudaStream_t stream)
 {
     if (n == 0) return MHDC_OK;
-    const int64_t grid = (n + CSR_ROWS - 1) / CSR_ROWS;
+    const int64_t rows_per_cta = 32 * (CSR_THREADS / 32);
+    const int64_t grid = (n + rows_per_cta - 1) / rows_per_cta;
     k_csr_spmv<<<(unsigned)grid, CSR_THREADS, 0, stream>>>(n, rp, col, val, x, y);
     MHDC_LAUNCH_CHECK("k_csr_spmv");
     return MHDC_OK;
 }
+
+int launch_read_bench(int64_t N, const double *A, double *out, int grid, cudaStream_t stream)
+{
+    if (N <= 0) return MHDC_OK;
+    k_read<<<grid, 256, 0, stream>>>(N / 2, A, out);
+    MHDC_LAUNCH_CHECK("k_read");
+    return MHDC_OK;
+}
+
+int read_bench_grid() { return num_sms() * 8; }
 
 int launch_spmm(const mhdc_matrix *, int, const void *, int64_t, void *, int64_t, cudaStream_t)
 {

@@ -290,3 +290,13 @@ def test_every_variant_is_bit_identical_and_tune_picks_one(mh):
             assert t.equal(y, ys[1])
     with pytest.raises(mh.MhdcError):
         mh.mhdc_set_variant(h, mh.MHDC_NUM_VARIANTS)
+
+
+def test_read_bench_sums(mh):
+    t = torch()
+    N = (1 << 22) + 6
+    A = t.from_numpy(synth.uniform_vector(N, 8)).cuda()
+    out = t.zeros(mh.mhdc_read_bench_ctas(), dtype=t.float64, device="cuda")
+    mh.mhdc_read_bench(A, out)
+    ref = float(np.sum(A.cpu().numpy()))
+    assert abs(float(out.sum()) - ref) <= 1e-9 * float(np.sum(np.abs(A.cpu().numpy())))
