@@ -206,51 +206,36 @@ k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
     }
 }
 
-// Plain CSR (Fig. 2), warp-streamed: a warp owns 32 consecutive rows, whose
-// entries are contiguous in val and col_ind.  It walks that span CSR_UNR * 32
-// entries at a time: every lane first loads CSR_UNR (val, col) pairs
-// (coalesced, all independent), then their x values, writes the products to
-// the warp's shared-memory slice, and each lane adds the products that fall
-// in its own row, in column order.
+// Plain CSR (Fig. 2), one thread per row: s = fma(val[k], x[col_ind[k]], s)
+// over the row, four entries per step.  One FP64 FMA per nonzero and no
+// cross-lane reduction: on GB300 the FP64 pipe (about 0.6 T FMA/s) rather
+// than HBM bounds an FP64 SpMV, so the baseline must not spend extra FP64
+// adds.  A warp's 32 rows are contiguous in val / col_ind, so the per-thread
+// strided loads are served from L1 lines the warp already fetched.
 constexpr int CSR_THREADS = 256;
-constexpr int CSR_UNR = 8;
-constexpr int CSR_SPAN = 32 * CSR_UNR;
 
 __global__ void __launch_bounds__(CSR_THREADS)
 k_csr_spmv(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
            const double *__restrict__ val, const double *__restrict__ x, double *__restrict__ y)
 {
-    __shared__ double prod[CSR_THREADS / 32][CSR_SPAN];
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int64_t r0 = ((int64_t)blockIdx.x * (CSR_THREADS / 32) + wl) * 32;
-    if (r0 >= n) return;
-    const int64_t r1 = (r0 + 32 < n) ? r0 + 32 : n;
-    const int64_t i = r0 + lane;
-    const int32_t a = i < r1 ? rp[i] : 0, b = i < r1 ? rp[i + 1] : 0;
-    const int32_t k0 = rp[r0], k1 = rp[r1];
-    double *pw = prod[wl];
+    const int64_t i = (int64_t)blockIdx.x * CSR_THREADS + threadIdx.x;
+    if (i >= n) return;
+    const int32_t a = rp[i], b = rp[i + 1];
     double s = 0.0;
-    for (int32_t c0 = k0; c0 < k1; c0 += CSR_SPAN) {
-        double v[CSR_UNR];
-        int32_t c[CSR_UNR];
-#pragma unroll
-        for (int u = 0; u < CSR_UNR; u++) {
-            const int32_t k = c0 + u * 32 + lane;
-            v[u] = k < k1 ? __ldg(val + k) : 0.0;
-            c[u] = k < k1 ? __ldg(col + k) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < CSR_UNR; u++) {
-            const int32_t k = c0 + u * 32 + lane;
-            if (k < k1) pw[u * 32 + lane] = v[u] * __ldg(x + c[u]);
-        }
-        __syncwarp();
-        const int32_t hi0 = c0 + CSR_SPAN;
-        const int32_t lo = a > c0 ? a : c0, hi = b < hi0 ? b : hi0;
-        for (int32_t k = lo; k < hi; k++) s += pw[k - c0];
-        __syncwarp();
+    int32_t k = a;
+    for (; k + 4 <= b; k += 4) {
+        const double v0 = __ldg(val + k), v1 = __ldg(val + k + 1), v2 = __ldg(val + k + 2),
+                     v3 = __ldg(val + k + 3);
+        const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + 1), c2 = __ldg(col + k + 2),
+                      c3 = __ldg(col + k + 3);
+        const double x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+        s = fma(v0, x0, s);
+        s = fma(v1, x1, s);
+        s = fma(v2, x2, s);
+        s = fma(v3, x3, s);
     }
-    if (i < r1) y[i] = s;
+    for (; k < b; k++) s = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
+    y[i] = s;
 }
 
 // Read-only member of the memory benchmarks: out[cta] = sum of the CTA's
@@ -432,8 +417,7 @@ int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *v
                const double *x, double *y, cudaStream_t stream)
 {
     if (n == 0) return MHDC_OK;
-    const int64_t rows_per_cta = 32 * (CSR_THREADS / 32);
-    const int64_t grid = (n + rows_per_cta - 1) / rows_per_cta;
+    const int64_t grid = (n + CSR_THREADS - 1) / CSR_THREADS;
     k_csr_spmv<<<(unsigned)grid, CSR_THREADS, 0, stream>>>(n, rp, col, val, x, y);
     MHDC_LAUNCH_CHECK("k_csr_spmv");
     return MHDC_OK;
