@@ -219,6 +219,43 @@ int mhdc_stream_bench(int64_t N, const double *d_A, const double *d_B, const int
 int mhdc_read_bench(int64_t N, const double *d_A, double *d_out, void *stream);
 int mhdc_read_bench_ctas(void);
 
+/*
+ * mhdc_build_noalloc -- the conversion of mhdc_build, written into arrays the
+ * caller provides, with no device memory allocated by the call.  The paper
+ * has no counterpart; this exists for callers that cannot allocate device
+ * memory: a process that carves all its device memory out of one pool at
+ * start-up, code on a latency-critical path where cudaMalloc would stall or
+ * fail, or a binding that may only pass buffers it already owns.
+ *
+ * Limits: n <= 262144 rows and nnz <= 262144 stored entries; larger inputs
+ * return MHDC_ERR_INVALID_ARG with a message saying so.  All temporaries live
+ * in one file-scope device array of about 15 MB, which every GPU that loads
+ * this library holds until the process exits.  The first call on a device
+ * looks that array's address up (cudaGetSymbolAddress) with the device
+ * current; make the first call on each device before any stream capture.
+ * Every call shares the array and it keeps the last call's contents: calls
+ * that overlap on the GPU (other streams, other threads) race and must not be
+ * issued; the call clears what must start at zero itself.
+ *
+ *   n, d_row_ptr, d_col, d_val, n_b, theta, dtype
+ *                as mhdc_build (n >= 1; d_col, d_val may be NULL if nnz = 0)
+ *   d_dia_ptr    int32[ceil(n / n_b) + 1]                     (output)
+ *   d_dia_offset int32[cap_P], d_dia_val dtype[cap_P * n_b]  (output)
+ *   d_csr_row_ptr int32[n + 1]                                (output)
+ *   d_csr_col    int32[cap_rem], d_csr_val dtype[cap_rem]     (output)
+ *   h_P, h_nnz_rem  host: receive P and the remainder's nnz
+ *   stream       stream to run on; the call synchronizes it
+ * Output layout and values are exactly those mhdc_export returns for the
+ * same input.  If P > cap_P or nnz_rem > cap_rem the call returns
+ * MHDC_ERR_INVALID_ARG with the sizes needed in *h_P / *h_nnz_rem (cap_rem =
+ * nnz always suffices; P <= nnz).  Invalid CSR returns MHDC_ERR_BAD_CSR.
+ */
+int mhdc_build_noalloc(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col,
+                       const double *d_val, int32_t n_b, double theta, int32_t dtype,
+                       int32_t *d_dia_ptr, int32_t *d_dia_offset, void *d_dia_val, int64_t cap_P,
+                       int32_t *d_csr_row_ptr, int32_t *d_csr_col, void *d_csr_val,
+                       int64_t cap_rem, int64_t *h_P, int64_t *h_nnz_rem, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

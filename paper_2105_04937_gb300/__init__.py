@@ -24,7 +24,7 @@ __all__ = [
     "hdc_build", "mhdc_spmv", "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
     "mhdc_info", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
     "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "mhdc_check",
-    "mhdc_read_bench", "mhdc_read_bench_ctas",
+    "mhdc_read_bench", "mhdc_read_bench_ctas", "mhdc_build_noalloc",
 ]
 
 MHDC_F64, MHDC_F32, MHDC_BF16 = 0, 1, 2
@@ -67,6 +67,8 @@ _SIGS = {
     "mhdc_check": [_P],
     "mhdc_read_bench": [_I64, _P, _P, _P],
     "mhdc_read_bench_ctas": [],
+    "mhdc_build_noalloc": [_I64, _P, _P, _P, _I32, _D, _I32, _P, _P, _P, _I64, _P, _P, _P, _I64,
+                           C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P],
     "mhdc_tune": [_P, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
 }
 
@@ -322,3 +324,33 @@ def mhdc_read_bench(A, out, stream=None):
     _check_dev(out, torch.float64, mhdc_read_bench_ctas(), "out")
     _check(lib().mhdc_read_bench(A.numel(), _ptr(A), _ptr(out), _stream(stream)), "mhdc_read_bench")
     return out
+
+
+def mhdc_build_noalloc(n, row_ptr, col, val, n_b, theta, dtype, dia_ptr, dia_offset, dia_val,
+                       csr_row_ptr, csr_col, csr_val, stream=None):
+    """mhdc_build into caller-owned device tensors, allocating nothing.
+
+    Output tensors: dia_ptr int32[ceil(n/n_b)+1], dia_offset int32[cap_P],
+    dia_val (float64 / float32 / int16 bits for bf16)[cap_P * n_b],
+    csr_row_ptr int32[n+1], csr_col int32[cap_rem], csr_val[cap_rem].
+    Returns (P, nnz_rem).  Limits and sharing rules: see include/mhdc.h."""
+    import torch
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    _check_dev(row_ptr, torch.int32, n + 1, "row_ptr")
+    vsz = {MHDC_F64: 8, MHDC_F32: 4, MHDC_BF16: 2}[dtype]
+    for t, nm in ((dia_val, "dia_val"), (csr_val, "csr_val")):
+        if not t.is_cuda or t.element_size() != vsz or not t.is_contiguous():
+            raise ValueError(f"{nm} must be a contiguous CUDA tensor of {vsz}-byte elements")
+    cap_P = dia_offset.numel()
+    if dia_val.numel() < cap_P * n_b:
+        raise ValueError("dia_val must hold dia_offset.numel() * n_b values")
+    cap_rem = min(csr_col.numel(), csr_val.numel())
+    P = C.c_int64(0)
+    R = C.c_int64(0)
+    rc = lib().mhdc_build_noalloc(n, _ptr(row_ptr), _ptr(col), _ptr(val), int(n_b), float(theta),
+                                  int(dtype), _ptr(dia_ptr), _ptr(dia_offset), _ptr(dia_val), cap_P,
+                                  _ptr(csr_row_ptr), _ptr(csr_col), _ptr(csr_val), cap_rem,
+                                  C.byref(P), C.byref(R), _stream(stream))
+    _check(rc, "mhdc_build_noalloc")
+    return P.value, R.value

@@ -209,6 +209,17 @@ int mhdc_stream_bench(int64_t N, const double *d_A, const double *d_B, const int
     return launch_stream_bench(N, d_A, d_B, d_I, d_C, indirect, (cudaStream_t)stream);
 }
 
+int mhdc_build_noalloc(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col,
+                       const double *d_val, int32_t n_b, double theta, int32_t dtype,
+                       int32_t *d_dia_ptr, int32_t *d_dia_offset, void *d_dia_val, int64_t cap_P,
+                       int32_t *d_csr_row_ptr, int32_t *d_csr_col, void *d_csr_val,
+                       int64_t cap_rem, int64_t *h_P, int64_t *h_nnz_rem, void *stream)
+{
+    return build_noalloc(n, d_row_ptr, d_col, d_val, n_b, theta, dtype, d_dia_ptr, d_dia_offset,
+                         d_dia_val, cap_P, d_csr_row_ptr, d_csr_col, d_csr_val, cap_rem, h_P,
+                         h_nnz_rem, (cudaStream_t)stream);
+}
+
 int mhdc_read_bench(int64_t N, const double *d_A, double *d_out, void *stream)
 {
     if (N < 0 || (N & 1) || (N > 0 && (!d_A || !d_out)) || ((uintptr_t)d_A & 15)) {

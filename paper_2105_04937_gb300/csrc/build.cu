@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "mhdc_internal.cuh"
@@ -693,6 +694,234 @@ int build_matrix(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, cons
     }
     *out = A;
     return MHDC_OK;
+}
+
+}  // namespace mhdc
+
+namespace mhdc {
+
+// ---------------------------------------------------------------------------
+// Conversion without any device allocation (mhdc_build_noalloc).
+//
+// For callers that cannot allocate device memory while converting: a process
+// whose device memory comes from a fixed pool handed out at start-up, code
+// running where an allocation would stall or fail (a latency-critical loop,
+// a memory-capped service), or a host language binding that only passes
+// buffers it owns.  The caller passes the input CSR and every output array;
+// all temporaries live in one file-scope device array of fixed size, which
+// every GPU that loads this library keeps until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t NA_MAX_NNZ = 1 << 18;   // stored entries
+constexpr int64_t NA_MAX_N = 1 << 18;     // rows (so at most 2^18 row blocks)
+constexpr int64_t NA_SCAN = 2 * ((NA_MAX_NNZ + 4095) / 4096) + 8;  // scan tile sums, with room
+// int32 words: err | sel_out | sel_cnt | ovf | ovf_pos | flags | pos | scan | keys | cnt | ids | lg | base(i64)
+constexpr int64_t NA_ERR = 0;
+constexpr int64_t NA_SEL = 64;
+constexpr int64_t NA_SELCNT = NA_SEL + NA_MAX_NNZ;
+constexpr int64_t NA_OVF = NA_SELCNT + NA_MAX_N;
+constexpr int64_t NA_OVFPOS = NA_OVF + NA_MAX_N;
+constexpr int64_t NA_FLAGS = NA_OVFPOS + NA_MAX_N + 64;
+constexpr int64_t NA_POS = NA_FLAGS + NA_MAX_NNZ;
+constexpr int64_t NA_SCANS = NA_POS + NA_MAX_NNZ + 64;
+constexpr int64_t NA_KEYS = NA_SCANS + NA_SCAN + 64;
+constexpr int64_t NA_CNT = NA_KEYS + 4 * NA_MAX_NNZ;
+// a block overflows its shared table only with more than 12288 entries, so at
+// most NA_MAX_NNZ / 12288 < NA_MAX_OVF blocks take the global-table path
+constexpr int64_t NA_MAX_OVF = 1024;
+constexpr int64_t NA_IDS = NA_CNT + 4 * NA_MAX_NNZ;
+constexpr int64_t NA_LG = NA_IDS + NA_MAX_OVF;
+constexpr int64_t NA_BASE = NA_LG + NA_MAX_OVF;  // int64 entries start here (8-byte aligned)
+constexpr int64_t NA_WORDS = NA_BASE + 2 * NA_MAX_OVF;
+
+static __device__ __align__(256) int32_t g_noalloc_scratch[NA_WORDS];
+
+std::mutex g_noalloc_mu;
+int32_t *g_noalloc_ptr[64] = {};
+
+// The device address of g_noalloc_scratch on the current device (looked up
+// once per device; host code cannot use the symbol itself as a pointer).
+int noalloc_scratch(int32_t **out)
+{
+    int dev = 0;
+    MHDC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error_msg("mhdc_build_noalloc: device index out of range");
+        return MHDC_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress(g_noalloc_scratch)", e);
+            return MHDC_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<int32_t *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return MHDC_OK;
+}
+
+// List the row blocks whose shared hash table overflowed: ids[pos[b]] = b,
+// with the global table of block b at 4 * row_ptr[r0] (2^lg <= 4m slots).
+__global__ void k_noalloc_ovf_list(int64_t n, int32_t n_b, int64_t nb, const int32_t *__restrict__ rp,
+                                   const int32_t *__restrict__ ovf, const int32_t *__restrict__ pos,
+                                   int32_t *ids, int32_t *lg, int64_t *base)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb || !ovf[b]) return;
+    const int64_t r0 = b * (int64_t)n_b;
+    const int64_t r1 = (n - r0 < n_b) ? n : r0 + n_b;
+    const int64_t m = (int64_t)rp[r1] - rp[r0];
+    int l = 10;
+    while (((int64_t)1 << l) < 2 * m) l++;
+    const int32_t q = pos[b];
+    ids[q] = (int32_t)b;
+    lg[q] = l;
+    base[q] = 4 * (int64_t)rp[r0];
+}
+
+int read_i32(const int32_t *d, int32_t *h, cudaStream_t st)
+{
+    MHDC_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    return MHDC_OK;
+}
+
+template <typename VT>
+int noalloc_fill(int64_t n, int32_t n_b, int64_t nb, int64_t nnz, const int32_t *rp,
+                 const int32_t *col, const double *val, int32_t *S, int32_t *dia_ptr,
+                 int32_t *dia_offset, void *dia_val, int32_t *csr_row_ptr, int32_t *csr_col,
+                 void *csr_val, int64_t cap_rem, int64_t *h_nnz_rem, cudaStream_t st)
+{
+    int32_t *flags = S + NA_FLAGS, *pos = S + NA_POS;
+    if (nb > 0) {
+        k_scatter<VT><<<(unsigned)nb, 256, 0, st>>>(n, n_b, rp, col, val, dia_ptr, S + NA_SEL, rp,
+                                                    dia_offset, static_cast<VT *>(dia_val), flags);
+        MHDC_LAUNCH_CHECK("k_scatter");
+    }
+    RC(exclusive_scan_i32(flags, pos, nnz, S + NA_SCANS, st));
+    int32_t nr = 0;
+    RC(read_i32(pos + nnz, &nr, st));
+    *h_nnz_rem = nr;
+    if (nr > cap_rem) {
+        set_error_msg("mhdc_build_noalloc: csr_col/csr_val capacity too small (needed size in *h_nnz_rem)");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    if (nnz > 0) {
+        k_rem_scatter<VT><<<grid_for(nnz, 256), 256, 0, st>>>(nnz, flags, pos, col, val, csr_col,
+                                                             static_cast<VT *>(csr_val));
+        MHDC_LAUNCH_CHECK("k_rem_scatter");
+    }
+    k_rem_rowptr<<<grid_for(n + 1, 256), 256, 0, st>>>(n, rp, pos, csr_row_ptr);
+    MHDC_LAUNCH_CHECK("k_rem_rowptr");
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    return MHDC_OK;
+}
+
+}  // namespace
+
+int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int32_t n_b,
+                  double theta, int32_t dtype, int32_t *dia_ptr, int32_t *dia_offset, void *dia_val,
+                  int64_t cap_P, int32_t *csr_row_ptr, int32_t *csr_col, void *csr_val,
+                  int64_t cap_rem, int64_t *h_P, int64_t *h_nnz_rem, cudaStream_t st)
+{
+    if (!rp || !h_P || !h_nnz_rem || n < 1 || n_b < 1 || !std::isfinite(theta) || theta < 0.0 ||
+        dtype < MHDC_F64 || dtype > MHDC_BF16 || cap_P < 0 || cap_rem < 0 || !dia_ptr ||
+        !csr_row_ptr) {
+        set_error_msg("mhdc_build_noalloc: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    if (n > NA_MAX_N) {
+        set_error_msg("mhdc_build_noalloc: n exceeds the no-allocation limit of 262144 rows");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    int32_t *S = nullptr;
+    RC(noalloc_scratch(&S));
+    int32_t nnz = 0;
+    RC(read_i32(rp + n, &nnz, st));
+    if (nnz < 0) {
+        set_error_msg("mhdc_build_noalloc: row_ptr[n] < 0");
+        return MHDC_ERR_BAD_CSR;
+    }
+    if (nnz > NA_MAX_NNZ) {
+        set_error_msg("mhdc_build_noalloc: nnz exceeds the no-allocation limit of 262144 entries");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    if (nnz > 0 && (!col || !val)) {
+        set_error_msg("mhdc_build_noalloc: null column or value array with nnz > 0");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    const int64_t nb = (n + n_b - 1) / n_b;
+    // 1. CSR checks (the error word must start at zero: the array keeps old contents)
+    MHDC_CUDA_TRY(cudaMemsetAsync(S + NA_ERR, 0, sizeof(int32_t), st));
+    k_validate<<<grid_for(n, 256), 256, 0, st>>>(n, rp, col, nnz, S + NA_ERR);
+    MHDC_LAUNCH_CHECK("k_validate");
+    int32_t err = 0;
+    RC(read_i32(S + NA_ERR, &err, st));
+    if (err) {
+        set_error_msg("mhdc_build_noalloc: invalid CSR");
+        return MHDC_ERR_BAD_CSR;
+    }
+    // 2. selection per row block (shared-memory tables; overflowing blocks redone
+    //    with tables in the scratch array)
+    MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_select<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CS_SMEM));
+    k_count_select<false><<<(unsigned)nb, CS_THREADS, CS_SMEM, st>>>(
+        n, n_b, rp, col, theta, nullptr, nullptr, nullptr, nullptr, nullptr, S + NA_SEL,
+        S + NA_SELCNT, S + NA_OVF);
+    MHDC_LAUNCH_CHECK("k_count_select");
+    RC(exclusive_scan_i32(S + NA_OVF, S + NA_OVFPOS, nb, S + NA_SCANS, st));
+    int32_t novf = 0;
+    RC(read_i32(S + NA_OVFPOS + nb, &novf, st));
+    if (novf > NA_MAX_OVF) {
+        set_error_msg("mhdc_build_noalloc: too many overflowing row blocks");
+        return MHDC_ERR_DEVICE_CHECK;
+    }
+    if (novf > 0) {
+        int64_t *base = reinterpret_cast<int64_t *>(S + NA_BASE);
+        k_noalloc_ovf_list<<<grid_for(nb, 256), 256, 0, st>>>(n, n_b, nb, rp, S + NA_OVF,
+                                                              S + NA_OVFPOS, S + NA_IDS, S + NA_LG,
+                                                              base);
+        MHDC_LAUNCH_CHECK("k_noalloc_ovf_list");
+        k_count_select<true><<<(unsigned)novf, CS_THREADS, 0, st>>>(
+            n, n_b, rp, col, theta, S + NA_IDS, S + NA_KEYS, S + NA_CNT, base, S + NA_LG,
+            S + NA_SEL, S + NA_SELCNT, S + NA_OVF);
+        MHDC_LAUNCH_CHECK("k_count_select<global>");
+    }
+    // 3. dia_ptr (caller's array) and the number of partial diagonals
+    RC(exclusive_scan_i32(S + NA_SELCNT, dia_ptr, nb, S + NA_SCANS, st));
+    int32_t P = 0;
+    RC(read_i32(dia_ptr + nb, &P, st));
+    *h_P = P;
+    *h_nnz_rem = 0;
+    if (P > cap_P) {
+        set_error_msg("mhdc_build_noalloc: dia_offset/dia_val capacity too small (needed P in *h_P)");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    if (P > 0 && (!dia_offset || !dia_val)) {
+        set_error_msg("mhdc_build_noalloc: null dia_offset or dia_val with P > 0");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    if (nnz > 0 && cap_rem > 0 && (!csr_col || !csr_val)) {
+        set_error_msg("mhdc_build_noalloc: null csr_col or csr_val");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    // 4-5. scatter and remainder compaction
+    switch (dtype) {
+    case MHDC_F64:
+        return noalloc_fill<double>(n, n_b, nb, nnz, rp, col, val, S, dia_ptr, dia_offset, dia_val,
+                                    csr_row_ptr, csr_col, csr_val, cap_rem, h_nnz_rem, st);
+    case MHDC_F32:
+        return noalloc_fill<float>(n, n_b, nb, nnz, rp, col, val, S, dia_ptr, dia_offset, dia_val,
+                                   csr_row_ptr, csr_col, csr_val, cap_rem, h_nnz_rem, st);
+    default:
+        return noalloc_fill<__nv_bfloat16>(n, n_b, nb, nnz, rp, col, val, S, dia_ptr, dia_offset,
+                                           dia_val, csr_row_ptr, csr_col, csr_val, cap_rem,
+                                           h_nnz_rem, st);
+    }
 }
 
 }  // namespace mhdc

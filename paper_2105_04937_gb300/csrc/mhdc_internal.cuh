@@ -51,6 +51,10 @@ int build_matrix(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, cons
                  int32_t n_b, double theta, int32_t dtype, int mode, cudaStream_t stream,
                  mhdc_matrix **out);
 void free_matrix(mhdc_matrix *A);
+int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int32_t n_b,
+                  double theta, int32_t dtype, int32_t *dia_ptr, int32_t *dia_offset, void *dia_val,
+                  int64_t cap_P, int32_t *csr_row_ptr, int32_t *csr_col, void *csr_val,
+                  int64_t cap_rem, int64_t *h_P, int64_t *h_nnz_rem, cudaStream_t st);
 
 // Products; defined in spmv.cu.
 int launch_spmv(const mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream);
