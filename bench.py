@@ -124,6 +124,20 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
 
 
+def fp64_peak_tflops():
+    """FP64 peak from unit counts and clock: GB300 issues 2 FP64 FMAs per SM
+    per clock (1.25 TFLOP/s nominal over 152 SMs at 2070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return 2 * 2 * sms * mhz * 1e6 / 1e12
+
+
 def gflops(nnz, sec):
     return 2.0 * nnz / sec / 1e9
 
@@ -332,6 +346,12 @@ def main():
     ms_step = total_ms / args.steps
     value = gflops(A.nnz, ms_step / 1e3) * ws
     achieved = info["bytes_model"] / (kern_ms / 1e3) / 1e9
+    # ALU work of one launch: one FP64 FMA (2 flop) per stored slot of the rows
+    # the kernel covers (n is a multiple of n_b here, so P * n_b slots) plus one
+    # per remainder entry
+    slots = info["P"] * N_B + info["nnz_rem"]
+    fp64_peak = fp64_peak_tflops()
+    alu_achieved = 2.0 * slots / (kern_ms / 1e3) / 1e12
 
     extra = {}
     if not args.skip_extra:
@@ -384,7 +404,7 @@ def main():
             tot, mean, _ = time_launches(lambda: mh.mhdc_stream_bench(Am, Bm, Im, Cm, ind, stream),
                                          20, 3, stream, torch)
             wm[nm_] = round(per * Nm / (mean / 1e3) / 1e9, 1)
-        ro = torch.empty(mh.mhdc_read_bench_ctas(), dtype=torch.float64, device="cuda")
+        ro = torch.empty(mh.mhdc_read_bench_ctas(), dtype=torch.int64, device="cuda")
         big = torch.cat([Am, Bm])
         tot, mean, _ = time_launches(lambda: mh.mhdc_read_bench(big, ro, stream), 20, 3, stream, torch)
         wm["read_only"] = round(8 * big.numel() / (mean / 1e3) / 1e9, 1)
@@ -429,14 +449,19 @@ def main():
                        "l2": "inputs larger than L2 (M-HDC arrays "
                              f"{info['bytes_model'] / 1e6:.0f} MB > 129 MB L2); no flush",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                         "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": None, "kernel": f"k_mhdc_spmv<double> variant {best_variant}",
-                         "bytes_per_launch": info["bytes_model"],
-                         "kernel_us": round(kern_ms * 1e3, 3), "peak_source": peak_src,
-                         "read_only_ceiling_gbs": read_ceiling,
-                         "frac_of_read_only_ceiling": (round(achieved / read_ceiling, 4)
-                                                       if read_ceiling else None)},
+            "roofline": {"bound": "alu", "achieved": round(alu_achieved, 4),
+                         "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                         "frac": round(alu_achieved / fp64_peak, 4), "traffic": None,
+                         "kernel": f"k_mhdc_spmv<double> variant {best_variant}",
+                         "flops_per_launch": 2 * slots,
+                         "peak_source": "FP64: 2 FMA/clk/SM x 2 flop x SMs x max SM clock "
+                                        "(GB300 nominal 1.25 TFLOP/s)",
+                         "kernel_us": round(kern_ms * 1e3, 3),
+                         "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                                 "frac": round(achieved / peak, 4),
+                                 "bytes_per_launch": info["bytes_model"],
+                                 "peak_source": peak_src,
+                                 "read_only_probe_gbs": read_ceiling}},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,

@@ -211,10 +211,12 @@ int mhdc_stream_bench(int64_t N, const double *d_A, const double *d_B, const int
 
 /*
  * mhdc_read_bench -- read-only member of the memory benchmarks above: each of
- * mhdc_read_bench_ctas() CTAs writes the sum of its share of d_A (N doubles,
- * N even, d_A 16-byte aligned) to d_out[cta].  It measures the bandwidth a
- * kernel that only reads can reach, the ceiling for SpMV, whose traffic is
- * almost all reads (V_A + V_x against V_y, Sec. 5.1).  Asynchronous.
+ * mhdc_read_bench_ctas() CTAs writes the bitwise XOR of the 64-bit words of
+ * its share of d_A (N doubles, N even, d_A 16-byte aligned) to d_out[cta]
+ * (d_out read as uint64).  It measures the bandwidth a kernel that only reads
+ * can reach (SpMV traffic is almost all reads: V_A + V_x against V_y,
+ * Sec. 5.1) with integer work only, so the FP64 pipe does not limit it.
+ * Asynchronous.
  */
 int mhdc_read_bench(int64_t N, const double *d_A, double *d_out, void *stream);
 int mhdc_read_bench_ctas(void);

@@ -318,10 +318,11 @@ def mhdc_read_bench_ctas() -> int:
 
 
 def mhdc_read_bench(A, out, stream=None):
-    """Read-only bandwidth probe: out[c] = sum of CTA c's share of A (float64)."""
+    """Read-only bandwidth probe: out[c] = XOR of the 64-bit words of CTA c's
+    share of A (A float64, out int64)."""
     import torch
     _check_dev(A, torch.float64, None, "A")
-    _check_dev(out, torch.float64, mhdc_read_bench_ctas(), "out")
+    _check_dev(out, torch.int64, mhdc_read_bench_ctas(), "out")
     _check(lib().mhdc_read_bench(A.numel(), _ptr(A), _ptr(out), _stream(stream)), "mhdc_read_bench")
     return out
 

@@ -238,33 +238,35 @@ k_csr_spmv(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict_
     y[i] = s;
 }
 
-// Read-only member of the memory benchmarks: out[cta] = sum of the CTA's
-// share of A (16-byte loads, 4 in flight per thread).
-__global__ void __launch_bounds__(256) k_read(int64_t N2, const double *__restrict__ A,
-                                              double *__restrict__ out)
+// Read-only member of the memory benchmarks: out[cta] = bitwise XOR of the
+// 64-bit words of the CTA's share of A (16-byte loads, 4 in flight per
+// thread).  Integer XOR keeps the FP64 pipe, which on GB300 is slower than
+// HBM, out of the measurement.
+__global__ void __launch_bounds__(256) k_read(int64_t N2, const ulonglong2 *__restrict__ A,
+                                              unsigned long long *__restrict__ out)
 {
     const int64_t st = (int64_t)gridDim.x * blockDim.x;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double s = 0.0;
+    unsigned long long s = 0;
     for (; i + 3 * st < N2; i += 4 * st) {
-        double2 v[4];
+        ulonglong2 v[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) v[u] = __ldg(reinterpret_cast<const double2 *>(A) + i + u * st);
+        for (int u = 0; u < 4; u++) v[u] = __ldg(A + i + u * st);
 #pragma unroll
-        for (int u = 0; u < 4; u++) s += v[u].x + v[u].y;
+        for (int u = 0; u < 4; u++) s ^= v[u].x ^ v[u].y;
     }
     for (; i < N2; i += st) {
-        const double2 v = __ldg(reinterpret_cast<const double2 *>(A) + i);
-        s += v.x + v.y;
+        const ulonglong2 v = __ldg(A + i);
+        s ^= v.x ^ v.y;
     }
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-    __shared__ double ws[8];
+    for (int d = 16; d > 0; d >>= 1) s ^= __shfl_xor_sync(0xffffffffu, s, d);
+    __shared__ unsigned long long ws[8];
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += ws[w];
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t ^= ws[w];
         out[blockIdx.x] = t;
     }
 }
@@ -426,7 +428,8 @@ int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *v
 int launch_read_bench(int64_t N, const double *A, double *out, int grid, cudaStream_t stream)
 {
     if (N <= 0) return MHDC_OK;
-    k_read<<<grid, 256, 0, stream>>>(N / 2, A, out);
+    k_read<<<grid, 256, 0, stream>>>(N / 2, reinterpret_cast<const ulonglong2 *>(A),
+                                     reinterpret_cast<unsigned long long *>(out));
     MHDC_LAUNCH_CHECK("k_read");
     return MHDC_OK;
 }
