@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--skip-extra", action="store_true",
                     help="time only the M-HDC kernel (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--variant", type=int, default=None,
+                    help="use this SpMV tile shape instead of the autotuner's choice")
     return ap.parse_args()
 
 
@@ -299,7 +301,11 @@ def main():
         f"beta={info['beta']:.4f} bytes_model={info['bytes_model']} in {build_ms:.1f} ms")
 
     # the library's own autotuner picks the tile shape (not timed)
-    best_variant, variant_us = mh.mhdc_tune(H, x, y)
+    if args.variant is None:
+        best_variant, variant_us = mh.mhdc_tune(H, x, y)
+    else:
+        mh.mhdc_set_variant(H, args.variant)
+        best_variant, variant_us = args.variant, []
     log(f"tuned: variant {best_variant}; per-variant us {[round(t, 2) for t in variant_us]}")
     info = H.info
 
@@ -410,6 +416,16 @@ def main():
         wm["read_only"] = round(8 * big.numel() / (mean / 1e3) / 1e9, 1)
         extra["w_mem_gbs"] = wm
         del Am, Bm, Cm, Im, big
+        # measured FMA rates (the FP64 one bounds this kernel)
+        ctas = mh.mhdc_read_bench_ctas()
+        fr = {}
+        for fp64, nm_, iters in ((True, "fp64_tflops", 512), (False, "fp32_tflops", 8192)):
+            ob = torch.empty(ctas * 256, dtype=torch.float64 if fp64 else torch.float32,
+                             device="cuda")
+            tot, mean, _ = time_launches(lambda: mh.mhdc_fma_bench(fp64, iters, ob, stream),
+                                         5, 2, stream, torch)
+            fr[nm_] = round(2.0 * ctas * 256 * 8 * iters / (mean / 1e3) / 1e12, 4)
+        extra["fma_measured"] = fr
 
     # ---- end to end through the host-buffer entry point (pinned memory)
     xh = torch.from_numpy(x_host).pin_memory()
@@ -457,6 +473,7 @@ def main():
                          "peak_source": "FP64: 2 FMA/clk/SM x 2 flop x SMs x max SM clock "
                                         "(GB300 nominal 1.25 TFLOP/s)",
                          "kernel_us": round(kern_ms * 1e3, 3),
+                         "fp64_measured_tflops": extra.get("fma_measured", {}).get("fp64_tflops"),
                          "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                                  "frac": round(achieved / peak, 4),
                                  "bytes_per_launch": info["bytes_model"],

@@ -222,6 +222,16 @@ int mhdc_read_bench(int64_t N, const double *d_A, double *d_out, void *stream);
 int mhdc_read_bench_ctas(void);
 
 /*
+ * mhdc_fma_bench -- arithmetic-throughput probe (no counterpart in the paper):
+ * mhdc_read_bench_ctas() CTAs of 256 threads each run iters rounds of 8
+ * independent FMA chains, in FP64 if fp64 != 0 else FP32, and write one
+ * value per thread to d_out (double or float, ctas * 256 entries).  Timing it
+ * gives the measured FMA rate: total FMAs = ctas * 256 * 8 * iters.  On GB300
+ * the FP64 rate, not HBM, bounds an FP64 SpMV.  Asynchronous.
+ */
+int mhdc_fma_bench(int32_t fp64, int32_t iters, void *d_out, void *stream);
+
+/*
  * mhdc_build_noalloc -- the conversion of mhdc_build, written into arrays the
  * caller provides, with no device memory allocated by the call.  The paper
  * has no counterpart; this exists for callers that cannot allocate device

@@ -25,6 +25,7 @@ __all__ = [
     "mhdc_info", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
     "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "mhdc_check",
     "mhdc_read_bench", "mhdc_read_bench_ctas", "mhdc_build_noalloc",
+    "mhdc_fma_bench",
 ]
 
 MHDC_F64, MHDC_F32, MHDC_BF16 = 0, 1, 2
@@ -67,6 +68,7 @@ _SIGS = {
     "mhdc_check": [_P],
     "mhdc_read_bench": [_I64, _P, _P, _P],
     "mhdc_read_bench_ctas": [],
+    "mhdc_fma_bench": [_I32, _I32, _P, _P],
     "mhdc_build_noalloc": [_I64, _P, _P, _P, _I32, _D, _I32, _P, _P, _P, _I64, _P, _P, _P, _I64,
                            C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P],
     "mhdc_tune": [_P, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
@@ -355,3 +357,13 @@ def mhdc_build_noalloc(n, row_ptr, col, val, n_b, theta, dtype, dia_ptr, dia_off
                                   C.byref(P), C.byref(R), _stream(stream))
     _check(rc, "mhdc_build_noalloc")
     return P.value, R.value
+
+
+def mhdc_fma_bench(fp64: bool, iters: int, out, stream=None):
+    """FMA-throughput probe; out: float64 (fp64) or float32 tensor of
+    mhdc_read_bench_ctas() * 256 elements.  FMAs = that count * 8 * iters."""
+    import torch
+    _check_dev(out, torch.float64 if fp64 else torch.float32, mhdc_read_bench_ctas() * 256, "out")
+    _check(lib().mhdc_fma_bench(1 if fp64 else 0, int(iters), _ptr(out), _stream(stream)),
+           "mhdc_fma_bench")
+    return out

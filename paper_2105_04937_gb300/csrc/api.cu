@@ -231,4 +231,13 @@ int mhdc_read_bench(int64_t N, const double *d_A, double *d_out, void *stream)
 
 int mhdc_read_bench_ctas(void) { return read_bench_grid(); }
 
+int mhdc_fma_bench(int32_t fp64, int32_t iters, void *d_out, void *stream)
+{
+    if (iters < 1 || !d_out) {
+        set_error_msg("mhdc_fma_bench: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    return launch_fma_probe(fp64, iters, d_out, (cudaStream_t)stream);
+}
+
 }  // extern "C"

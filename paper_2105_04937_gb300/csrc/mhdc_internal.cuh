@@ -67,6 +67,7 @@ int launch_stream_bench(int64_t N, const double *A, const double *B, const int32
 int spmv_grid_for(const mhdc_matrix *A);
 int launch_read_bench(int64_t N, const double *A, double *out, int grid, cudaStream_t stream);
 int read_bench_grid();
+int launch_fma_probe(int fp64, int iters, void *out, cudaStream_t stream);
 bool tma_supported(const mhdc_matrix *A);
 int launch_spmv_tma(const mhdc_matrix *A, int shape, const void *d_x, void *d_y,
                     cudaStream_t stream);

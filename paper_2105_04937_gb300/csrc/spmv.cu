@@ -271,6 +271,24 @@ __global__ void __launch_bounds__(256) k_read(int64_t N2, const ulonglong2 *__re
     }
 }
 
+// FMA-throughput probe: each thread runs `iters` rounds of 8 independent FMA
+// chains in FP64 (fp64 != 0) or FP32 and stores a value that depends on them.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, T seed, T *__restrict__ out)
+{
+    T a = seed + (T)threadIdx.x, b = seed * (T)0.5, c[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) c[k] = (T)k * (T)0.125 + (T)threadIdx.x;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) c[k] = fma(a, b, c[k]);
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += c[k];
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 __global__ void k_stream(int64_t N, const double *__restrict__ A, const double *__restrict__ B,
                          const int32_t *__restrict__ I, double *__restrict__ C, int indirect)
 {
@@ -435,6 +453,14 @@ int launch_read_bench(int64_t N, const double *A, double *out, int grid, cudaStr
 }
 
 int read_bench_grid() { return num_sms() * 8; }
+
+int launch_fma_probe(int fp64, int iters, void *out, cudaStream_t stream)
+{
+    if (fp64) k_fma_probe<double><<<num_sms() * 8, 256, 0, stream>>>(iters, 1.0, (double *)out);
+    else k_fma_probe<float><<<num_sms() * 8, 256, 0, stream>>>(iters, 1.0f, (float *)out);
+    MHDC_LAUNCH_CHECK("k_fma_probe");
+    return MHDC_OK;
+}
 
 int launch_spmm(const mhdc_matrix *, int, const void *, int64_t, void *, int64_t, cudaStream_t)
 {

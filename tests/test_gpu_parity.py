@@ -301,3 +301,15 @@ def test_read_bench_xor(mh):
     got = np.bitwise_xor.reduce(out.cpu().numpy().view(np.uint64))
     ref = np.bitwise_xor.reduce(A.cpu().numpy().view(np.uint64))
     assert got == ref
+
+
+def test_fma_probe_values(mh):
+    t = torch()
+    ctas = mh.mhdc_read_bench_ctas()
+    for fp64 in (True, False):
+        out = t.zeros(ctas * 256, dtype=t.float64 if fp64 else t.float32, device="cuda")
+        mh.mhdc_fma_bench(fp64, 3, out)
+        tid = np.tile(np.arange(256), ctas).astype(np.float64)
+        # c_k = k/8 + tid + 3 * (1 + tid) * 0.5; out = sum_k c_k
+        ref = sum(k * 0.125 + tid + 3 * (1.0 + tid) * 0.5 for k in range(8))
+        assert np.allclose(out.cpu().numpy(), ref, rtol=1e-6)
