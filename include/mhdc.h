@@ -63,6 +63,8 @@ typedef struct {
     int32_t dtype;         /* enum mhdc_dtype */
     int32_t mode;          /* enum mhdc_mode */
     int32_t variant;       /* SpMV tile shape in use (-1: default) */
+    int32_t emulated_ok;   /* FP64 handle whose values allow variants 10-12 */
+    int32_t reserved;
     double theta;          /* density threshold used */
     double alpha;          /* filling rate: (nnz - nnz_rem) / (P * n_b)   (Sec. 5.3.3) */
     double beta;           /* CSR rate: nnz_rem / nnz                     (Sec. 5.3.1) */
@@ -168,8 +170,18 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  * 32 x 16 B x U rows and loads D diagonals before accumulating); variants 6-9
  * stream dia_val through shared memory with TMA bulk copies (one producer
  * warp, several consumer warps, an mbarrier ring; they need n_b * value size
- * to be a multiple of 16 bytes, else they run variant -1).  All variants
+ * to be a multiple of 16 bytes, else they run variant -1).  Variants 0-9
  * compute the same sums in the same order per row (bit-identical y).
+ * Variants 10-12 (FP64 handles only; others run variant -1) emulate the FP64
+ * product with pairs of FP32 numbers (values and x split into hi + lo, about
+ * 49 significant bits; products and sums by error-free transformations): on
+ * GB300 the FP64 pipe is about 64x slower than FP32, and this keeps the
+ * product bound by memory.  Their per-row error stays below
+ * 7e-13 * sum_j |a_ij||x_j| (inside the FP64 tolerance 1e-12) as long as every
+ * nonzero |a_ij| and |x_j| lies in [2^-51, 2^60] and a row has at most 64
+ * terms; the handle checks its values at build and each product checks x on
+ * the device, and outside that window the product runs the native FP64 path
+ * (variant -1's arithmetic) instead.
  *
  * mhdc_set_variant -- use variant v for this handle (-1: default chosen from n_b).
  * mhdc_tune        -- time every variant on (d_x, d_y) (overwriting d_y), keep
@@ -177,7 +189,7 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  *                     times_us is not NULL, each variant's mean time in
  *                     microseconds to times_us[MHDC_NUM_VARIANTS].  Synchronous.
  */
-#define MHDC_NUM_VARIANTS 10
+#define MHDC_NUM_VARIANTS 13
 int mhdc_set_variant(mhdc_handle A, int32_t v);
 int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *best,
               float *times_us);

@@ -45,7 +45,8 @@ class MhdcError(RuntimeError):
 class _Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_rem", C.c_int64), ("P", C.c_int64),
                 ("n_blocks", C.c_int64), ("n_b", C.c_int32), ("dtype", C.c_int32),
-                ("mode", C.c_int32), ("variant", C.c_int32), ("theta", C.c_double),
+                ("mode", C.c_int32), ("variant", C.c_int32), ("emulated_ok", C.c_int32),
+                ("reserved", C.c_int32), ("theta", C.c_double),
                 ("alpha", C.c_double), ("beta", C.c_double), ("bytes_model", C.c_int64),
                 ("bytes_device", C.c_int64)]
 
@@ -74,7 +75,8 @@ _SIGS = {
     "mhdc_tune": [_P, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
 }
 
-MHDC_NUM_VARIANTS = 10
+MHDC_NUM_VARIANTS = 13
+FIRST_EMULATED_VARIANT = 10
 
 
 def lib(build_if_missing: bool = False):
@@ -247,7 +249,7 @@ def csr_spmv(n, row_ptr, col, val, x, y, stream=None):
 def mhdc_info(A: Matrix) -> dict:
     inf = _Info()
     _check(lib().mhdc_info(C.c_void_p(A.handle), C.byref(inf)), "mhdc_info")
-    return {name: getattr(inf, name) for name, _ in _Info._fields_}
+    return {name: getattr(inf, name) for name, _ in _Info._fields_ if name != "reserved"}
 
 
 def mhdc_export(A: Matrix) -> dict:

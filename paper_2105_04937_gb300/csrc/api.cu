@@ -148,6 +148,7 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out)
     out->dtype = A->dtype;
     out->mode = A->mode;
     out->variant = A->variant;
+    out->emulated_ok = A->dw_ok ? 1 : 0;
     out->theta = A->theta;
     out->alpha = A->P ? (double)(A->nnz - A->nnz_rem) / ((double)A->P * (double)A->n_b) : 0.0;
     out->beta = A->nnz ? (double)A->nnz_rem / (double)A->nnz : 0.0;

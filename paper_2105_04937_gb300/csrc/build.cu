@@ -590,7 +590,93 @@ void free_matrix(mhdc_matrix *A)
     cudaFree(A->x_stage);
     cudaFree(A->y_stage);
     cudaFree(A->status);
+    cudaFree(A->dia_dw);
+    cudaFree(A->csr_dw);
+    cudaFree(A->x_dw);
+    cudaFree(A->dw_flag);
     delete A;
+}
+
+namespace {
+
+// (hi, lo) = (RN32(v), RN32(v - hi)): the FP32 pair of an FP64 value (build time).
+__global__ void k_split_dw(int64_t m, const double *__restrict__ v, float2 *__restrict__ out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const double d = v[k];
+    const float h = __double2float_rn(d);
+    out[k] = make_float2(h, __double2float_rn(d - (double)h));
+}
+
+// flag |= 1 if a nonzero value lies outside [2^DW_EMIN, 2^DW_EMAX] or is not finite.
+__global__ void k_value_window(int64_t m, const double *__restrict__ v, int *flag)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const double a = fabs(v[k]);
+    if (a != 0.0 && !(a >= ldexp(1.0, DW_EMIN) && a <= ldexp(1.0, DW_EMAX))) atomicOr(flag, 1);
+}
+
+// out = max over i of ptr[i + 1] - ptr[i], i < m.
+__global__ void k_max_diff(int64_t m, const int32_t *__restrict__ ptr, int *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    atomicMax(out, ptr[i + 1] - ptr[i]);
+}
+
+}  // namespace
+
+// Split an FP64 handle's values into FP32 pairs and decide whether the
+// emulated product may be used.  Lack of memory only disables emulation.
+int prepare_dw(mhdc_matrix *A, cudaStream_t st)
+{
+    A->dw_ok = false;
+    if (A->dtype != MHDC_F64 || A->n == 0) return MHDC_OK;
+    const int64_t nd = A->P * (int64_t)A->n_b;
+    if (cudaMalloc((void **)&A->dia_dw, sizeof(float2) * (size_t)(nd ? nd : 1)) != cudaSuccess ||
+        cudaMalloc((void **)&A->csr_dw, sizeof(float2) * (size_t)(A->nnz_rem ? A->nnz_rem : 1)) !=
+            cudaSuccess ||
+        cudaMalloc((void **)&A->x_dw, sizeof(float2) * (size_t)A->n) != cudaSuccess ||
+        cudaMalloc((void **)&A->dw_flag, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(A->dia_dw);
+        cudaFree(A->csr_dw);
+        cudaFree(A->x_dw);
+        cudaFree(A->dw_flag);
+        A->dia_dw = A->csr_dw = A->x_dw = nullptr;
+        A->dw_flag = nullptr;
+        return MHDC_OK;
+    }
+    MHDC_CUDA_TRY(cudaMemsetAsync(A->dw_flag, 0, sizeof(unsigned long long), st));
+    Buf w;
+    RC(dalloc(w, 2 * sizeof(int)));
+    MHDC_CUDA_TRY(cudaMemsetAsync(w.p, 0, 2 * sizeof(int), st));
+    if (nd > 0) {
+        k_split_dw<<<grid_for(nd, 256), 256, 0, st>>>(nd, (const double *)A->dia_val, A->dia_dw);
+        k_value_window<<<grid_for(nd, 256), 256, 0, st>>>(nd, (const double *)A->dia_val, w.as<int>());
+    }
+    if (A->nnz_rem > 0) {
+        k_split_dw<<<grid_for(A->nnz_rem, 256), 256, 0, st>>>(A->nnz_rem, (const double *)A->csr_val,
+                                                              A->csr_dw);
+        k_value_window<<<grid_for(A->nnz_rem, 256), 256, 0, st>>>(
+            A->nnz_rem, (const double *)A->csr_val, w.as<int>());
+    }
+    MHDC_LAUNCH_CHECK("k_split_dw");
+    int h[3] = {0, 0, 0};
+    Buf mx;
+    RC(dalloc(mx, 2 * sizeof(int)));
+    MHDC_CUDA_TRY(cudaMemsetAsync(mx.p, 0, 2 * sizeof(int), st));
+    k_max_diff<<<grid_for(A->n_blocks, 256), 256, 0, st>>>(A->n_blocks, A->dia_ptr, mx.as<int>());
+    k_max_diff<<<grid_for(A->n, 256), 256, 0, st>>>(A->n, A->csr_row_ptr, mx.as<int>() + 1);
+    MHDC_LAUNCH_CHECK("k_max_diff");
+    MHDC_CUDA_TRY(cudaMemcpyAsync(h, w.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaMemcpyAsync(h + 1, mx.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    A->dw_ok = h[0] == 0 && (h[1] + h[2]) <= DW_MAX_TERMS;
+    A->bytes_device += (int64_t)sizeof(float2) * (nd + A->nnz_rem + A->n);
+    return MHDC_OK;
 }
 
 static int build_into(mhdc_matrix *A, const int32_t *rp, const int32_t *col, const double *val,
@@ -665,6 +751,7 @@ static int build_into(mhdc_matrix *A, const int32_t *rp, const int32_t *col, con
         break;
     }
     RC(finish_stats(A, st));
+    RC(prepare_dw(A, st));
     A->spmv_grid = spmv_grid_for(A);
     return MHDC_OK;
 }

@@ -27,6 +27,13 @@ struct mhdc_matrix {
     int spmv_grid = 0;               // CTAs of the SpMV launch
     int variant = -1;                // SpMV tile shape (-1: chosen from n_b)
     int *status = nullptr;           // device word: bit 0 = a bounded wait gave up
+    // FP64 handles: values split into FP32 (hi, lo) pairs for the emulated product
+    float2 *dia_dw = nullptr;        // [P * n_b]
+    float2 *csr_dw = nullptr;        // [nnz_rem]
+    float2 *x_dw = nullptr;          // [n]: x split by each emulated product
+    unsigned long long *dw_flag = nullptr;  // (epoch << 1) | (x outside the window)
+    unsigned long long dw_epoch = 0;
+    bool dw_ok = false;              // values inside the window, <= DW_MAX_TERMS terms per row
 };
 
 namespace mhdc {
@@ -57,7 +64,7 @@ int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double
                   int64_t cap_rem, int64_t *h_P, int64_t *h_nnz_rem, cudaStream_t st);
 
 // Products; defined in spmv.cu.
-int launch_spmv(const mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream);
+int launch_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream);
 int launch_spmm(const mhdc_matrix *A, int k, const void *d_X, int64_t ldx, void *d_Y,
                 int64_t ldy, cudaStream_t stream);
 int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
@@ -72,6 +79,13 @@ bool tma_supported(const mhdc_matrix *A);
 int launch_spmv_tma(const mhdc_matrix *A, int shape, const void *d_x, void *d_y,
                     cudaStream_t stream);
 constexpr int NUM_REG_VARIANTS = 6;
+constexpr int FIRST_DW_VARIANT = 10;
+// Emulated FP64 (FP32 pairs): nonzero |a|, |x| must lie in [2^DW_EMIN, 2^DW_EMAX]
+// and a row may have at most DW_MAX_TERMS terms (error bound, see spmv.cu).
+constexpr int DW_EMIN = -51;
+constexpr int DW_EMAX = 60;
+constexpr int DW_MAX_TERMS = 64;
+int prepare_dw(mhdc_matrix *A, cudaStream_t st);
 int tune_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream, int32_t *best,
               float *times_us);
 

