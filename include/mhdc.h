@@ -172,8 +172,9 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  * warp, several consumer warps, an mbarrier ring; they need n_b * value size
  * to be a multiple of 16 bytes, else they run variant -1).  Variants 0-9
  * compute the same sums in the same order per row (bit-identical y).
- * Variants 10-12 (FP64 handles only; others run variant -1) emulate the FP64
- * product with pairs of FP32 numbers (values and x split into hi + lo, about
+ * Variants 10-15 (FP64 handles only; others run variant -1) emulate the FP64
+ * product (10-12 in registers, 13-15 streamed by TMA like 6-9) with pairs of
+ * FP32 numbers (values and x split into hi + lo, about
  * 49 significant bits; products and sums by error-free transformations): on
  * GB300 the FP64 pipe is about 64x slower than FP32, and this keeps the
  * product bound by memory.  Their per-row error stays below
@@ -189,7 +190,7 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  *                     times_us is not NULL, each variant's mean time in
  *                     microseconds to times_us[MHDC_NUM_VARIANTS].  Synchronous.
  */
-#define MHDC_NUM_VARIANTS 13
+#define MHDC_NUM_VARIANTS 16
 int mhdc_set_variant(mhdc_handle A, int32_t v);
 int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *best,
               float *times_us);

@@ -75,7 +75,7 @@ _SIGS = {
     "mhdc_tune": [_P, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
 }
 
-MHDC_NUM_VARIANTS = 13
+MHDC_NUM_VARIANTS = 16
 FIRST_EMULATED_VARIANT = 10
 
 

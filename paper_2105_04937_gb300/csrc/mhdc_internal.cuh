@@ -80,6 +80,10 @@ int launch_spmv_tma(const mhdc_matrix *A, int shape, const void *d_x, void *d_y,
                     cudaStream_t stream);
 constexpr int NUM_REG_VARIANTS = 6;
 constexpr int FIRST_DW_VARIANT = 10;
+constexpr int FIRST_TMA_DW_VARIANT = 13;
+int launch_spmv_tma_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y,
+                       unsigned long long epoch, cudaStream_t stream);
+int launch_split_x(mhdc_matrix *A, const void *d_x, unsigned long long epoch, cudaStream_t stream);
 // Emulated FP64 (FP32 pairs): nonzero |a|, |x| must lie in [2^DW_EMIN, 2^DW_EMAX]
 // and a row may have at most DW_MAX_TERMS terms (error bound, see spmv.cu).
 constexpr int DW_EMIN = -51;

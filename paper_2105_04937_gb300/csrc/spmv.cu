@@ -13,6 +13,7 @@
 #include <cstring>
 #include <type_traits>
 
+#include "dw_arith.cuh"
 #include "mhdc_internal.cuh"
 
 namespace mhdc {
@@ -238,51 +239,6 @@ k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
 // rounding to FP64: at most (5 + 3k) * 2^-48 + 2^-53 < 7e-13 for k <= 64.
 // Outside the window the same launch runs the native FP64 tile instead.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
-}
-
-// (sh, sl) += (a.x + a.y) * (x.x + x.y)
-__device__ __forceinline__ void dw_fma(float &sh, float &sl, float2 a, float2 x)
-{
-    float ph = __fmul_rn(a.x, x.x);
-    float pe = __fmaf_rn(a.x, x.x, -ph);
-    pe = __fmaf_rn(a.x, x.y, pe);
-    pe = __fmaf_rn(a.y, x.x, pe);
-    fast_two_sum(ph, pe, ph, pe);
-    float s, t, u, v;
-    two_sum(sh, ph, s, t);
-    two_sum(sl, pe, u, v);
-    t = __fadd_rn(t, u);
-    fast_two_sum(s, t, s, t);
-    t = __fadd_rn(t, v);
-    fast_two_sum(s, t, sh, sl);
-}
-
-// An FP32 number as FP64 without the FP64 pipe for normal numbers and zeros.
-__device__ __forceinline__ double f32_to_f64(float f)
-{
-    const uint32_t b = __float_as_uint(f);
-    const uint32_t e = (b >> 23) & 0xFF;
-    if (e == 0 || e == 0xFF) {
-        if ((b & 0x7FFFFFFFu) == 0) return __longlong_as_double((long long)(b & 0x80000000u) << 32);
-        return (double)f;  // subnormal, inf, nan: rare
-    }
-    const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
-                                 ((unsigned long long)(e - 127 + 1023) << 52) |
-                                 ((unsigned long long)(b & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)d);
-}
-
 // x_dw[i] = FP32 pair of x[i] (integer operations only): hi = x rounded to 24
 // significant bits (half-up on the magnitude), lo = x - hi (exact, at most 29
 // bits) rounded to FP32.  Any nonzero |x| outside [2^DW_EMIN, 2^DW_EMAX] or
@@ -366,7 +322,7 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
                         const int64_t i = r0 + t;
                         const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
                         for (int32_t k = a; k < b; k++)
-                            dw_fma(sh[u][m], sl[u][m], __ldg(csr_dw + k),
+                            dw::dw_fma(sh[u][m], sl[u][m], __ldg(csr_dw + k),
                                    __ldg(x_dw + __ldg(csr_col + k)));
                     }
                 }
@@ -429,7 +385,7 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
 #pragma unroll
             for (int u = 0; u < U; u++)
 #pragma unroll
-                for (int m = 0; m < V; m++) dw_fma(sh[u][m], sl[u][m], v[d][u][m], xv[d][u][m]);
+                for (int m = 0; m < V; m++) dw::dw_fma(sh[u][m], sl[u][m], v[d][u][m], xv[d][u][m]);
         p += DD;
     };
     for (; p + D <= p1;) group(std::integral_constant<int, D>{});
@@ -439,7 +395,7 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
     for (int u = 0; u < U; u++)
 #pragma unroll
         for (int m = 0; m < V; m++)
-            if (tl[u] + m < rows) y[r0 + tl[u] + m] = f32_to_f64(sh[u][m]) + f32_to_f64(sl[u][m]);
+            if (tl[u] + m < rows) y[r0 + tl[u] + m] = dw::f32_to_f64(sh[u][m]) + dw::f32_to_f64(sl[u][m]);
 }
 
 // Plain CSR (Fig. 2), one thread per row: s = fma(val[k], x[col_ind[k]], s)
@@ -621,8 +577,14 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
 int launch_variant(mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStream_t stream)
 {
     if (id >= FIRST_DW_VARIANT) {
-        if (A->dw_ok && A->dtype == MHDC_F64 && (A->n_b % 2) == 0)
-            return launch_dw(A, id - FIRST_DW_VARIANT, d_x, d_y, stream);
+        if (A->dw_ok && A->dtype == MHDC_F64 && (A->n_b % 2) == 0) {
+            if (id < FIRST_TMA_DW_VARIANT) return launch_dw(A, id - FIRST_DW_VARIANT, d_x, d_y, stream);
+            const unsigned long long epoch = ++A->dw_epoch;
+            k_split_x<<<(unsigned)((A->n + 255) / 256), 256, 0, stream>>>(
+                A->n, (const double *)d_x, A->x_dw, A->dw_flag, epoch);
+            MHDC_LAUNCH_CHECK("k_split_x");
+            return launch_spmv_tma_dw(A, id - FIRST_TMA_DW_VARIANT, d_x, d_y, epoch, stream);
+        }
         id = -1;
     }
     if (id >= NUM_REG_VARIANTS) {

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <type_traits>
 
+#include "dw_arith.cuh"
 #include "mhdc_internal.cuh"
 
 namespace mhdc {
@@ -335,6 +336,276 @@ k_mhdc_spmv_tma(int64_t n, int32_t n_b, int32_t upb, int64_t n_units,
     }
 }
 
+int num_sms_tma();
+
+// ---------------------------------------------------------------------------
+// FP64 handles, emulated product (variants 13-15): the same pipeline over
+// 8-byte slots.  If the launch's x passed the window check (flag ==
+// epoch << 1) the producer streams the FP32 pairs dia_dw and consumers run the
+// double-word arithmetic of dw_arith.cuh on x_dw; otherwise it streams the
+// FP64 dia_val and consumers run native FP64 FMAs on x.
+// ---------------------------------------------------------------------------
+template <bool EMU, int NCW, int U, int D, int STAGES>
+__device__ __forceinline__ void tma_dw_consumer(
+    int64_t n, int32_t n_b, int32_t upb, int64_t n_units, const int32_t *__restrict__ dia_ptr,
+    const int32_t *__restrict__ dia_offset, const int32_t *__restrict__ csr_row_ptr,
+    const int32_t *__restrict__ csr_col, const double *__restrict__ csr_val,
+    const float2 *__restrict__ csr_dw, const double *__restrict__ x,
+    const float2 *__restrict__ x_dw, double *__restrict__ y, uint8_t *ring, uint64_t *full,
+    uint64_t *empty, int *__restrict__ status)
+{
+    constexpr int V = 2, NT = NCW * 32, R = NT * U * V, STAGE_BYTES = R * 8;
+    using XT = typename std::conditional<EMU, float2, double>::type;
+    const XT *xs = reinterpret_cast<const XT *>(EMU ? (const void *)x_dw : (const void *)x);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int stage = 0;
+    uint32_t phase = 0;
+    for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const int64_t ib = u / upb;
+        const int32_t t0 = (int32_t)(u - ib * upb) * R;
+        const int64_t r0 = ib * (int64_t)n_b;
+        const int32_t rows = (int32_t)((n - r0 < n_b) ? (n - r0) : n_b);
+        if (t0 >= rows) continue;
+        const int32_t ru = (rows - t0 < R) ? rows - t0 : R;
+        const bool full_unit = ru == R;
+        int32_t tl[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) tl[k] = (k * NT + tid) * V;
+        double acc[U][V];
+        float sh[U][V], sl[U][V];
+#pragma unroll
+        for (int k = 0; k < U; k++)
+#pragma unroll
+            for (int m = 0; m < V; m++) {
+                acc[k][m] = 0.0;
+                sh[k][m] = sl[k][m] = 0.f;
+            }
+        if (csr_row_ptr[r0 + t0] != csr_row_ptr[r0 + t0 + ru]) {
+#pragma unroll
+            for (int k = 0; k < U; k++)
+#pragma unroll
+                for (int m = 0; m < V; m++) {
+                    const int32_t t = tl[k] + m;
+                    if (t < ru) {
+                        const int64_t i = r0 + t0 + t;
+                        const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
+                        for (int32_t q = a; q < b; q++) {
+                            if constexpr (EMU)
+                                dw::dw_fma(sh[k][m], sl[k][m], __ldg(csr_dw + q),
+                                           __ldg(x_dw + __ldg(csr_col + q)));
+                            else
+                                acc[k][m] = fma(__ldg(csr_val + q), __ldg(x + __ldg(csr_col + q)),
+                                                acc[k][m]);
+                        }
+                    }
+                }
+        }
+        const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
+        const int64_t xw = r0 + t0 + (int64_t)warp * 32 * V;
+        bool ok = true;
+        int32_t p = p0;
+        auto group = [&](auto Dc) {
+            constexpr int DD = decltype(Dc)::value;
+            XT xv[DD][U][V];
+#pragma unroll
+            for (int d = 0; d < DD; d++) {
+                const int64_t off = dia_offset[p + d];
+#pragma unroll
+                for (int k = 0; k < U; k++) {
+                    const int64_t jw = xw + (int64_t)k * NT * V + off;
+                    if (full_unit && jw >= 0 && jw + 32 * V <= n) {
+                        const int64_t j = jw + lane * V;
+                        if ((reinterpret_cast<uintptr_t>(xs + jw) & 15) == 0) {
+                            const uint4 r = __ldg(reinterpret_cast<const uint4 *>(xs + j));
+                            memcpy(xv[d][k], &r, 16);
+                        } else {
+                            xv[d][k][0] = __ldg(xs + j);
+                            xv[d][k][1] = __ldg(xs + j + 1);
+                        }
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < V; m++) {
+                            const int64_t jm = jw + lane * V + m;
+                            if (tl[k] + m < ru && jm >= 0 && jm < n) xv[d][k][m] = __ldg(xs + jm);
+                            else memset(&xv[d][k][m], 0, sizeof(XT));
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < DD; d++) {
+                int st = stage + d;
+                uint32_t ph = phase;
+                if (st >= STAGES) {
+                    st -= STAGES;
+                    ph ^= 1;
+                }
+                if (!mbar_wait(&full[st], ph)) ok = false;
+            }
+            if (!ok) return;
+#pragma unroll
+            for (int d = 0; d < DD; d++) {
+                int st = stage + d;
+                if (st >= STAGES) st -= STAGES;
+                const uint8_t *sv = ring + (size_t)st * STAGE_BYTES;
+#pragma unroll
+                for (int k = 0; k < U; k++) {
+                    const uint4 r = *reinterpret_cast<const uint4 *>(sv + (size_t)tl[k] * 8);
+                    if constexpr (EMU) {
+                        float2 v[V];
+                        memcpy(v, &r, 16);
+#pragma unroll
+                        for (int m = 0; m < V; m++) dw::dw_fma(sh[k][m], sl[k][m], v[m], xv[d][k][m]);
+                    } else {
+                        double v[V];
+                        memcpy(v, &r, 16);
+#pragma unroll
+                        for (int m = 0; m < V; m++) acc[k][m] = fma(v[m], xv[d][k][m], acc[k][m]);
+                    }
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int d = 0; d < DD; d++) {
+                int st = stage + d;
+                if (st >= STAGES) st -= STAGES;
+                if (lane == 0) mbar_arrive(&empty[st]);
+            }
+            stage += DD;
+            if (stage >= STAGES) {
+                stage -= STAGES;
+                phase ^= 1;
+            }
+            p += DD;
+        };
+        while (ok && p + D <= p1) group(std::integral_constant<int, D>{});
+        while (ok && p < p1) group(std::integral_constant<int, 1>{});
+        if (!ok) {
+            if (lane == 0) atomicOr(status, 1);
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < U; k++)
+#pragma unroll
+            for (int m = 0; m < V; m++)
+                if (tl[k] + m < ru) {
+                    if constexpr (EMU)
+                        y[r0 + t0 + tl[k] + m] = dw::f32_to_f64(sh[k][m]) + dw::f32_to_f64(sl[k][m]);
+                    else
+                        y[r0 + t0 + tl[k] + m] = acc[k][m];
+                }
+    }
+}
+
+template <int NCW, int U, int D, int STAGES>
+__global__ void __launch_bounds__(NCW * 32 + 32)
+k_mhdc_spmv_tma_dw(int64_t n, int32_t n_b, int32_t upb, int64_t n_units,
+                   const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
+                   const double *__restrict__ dia_val, const float2 *__restrict__ dia_dw,
+                   const int32_t *__restrict__ csr_row_ptr, const int32_t *__restrict__ csr_col,
+                   const double *__restrict__ csr_val, const float2 *__restrict__ csr_dw,
+                   const double *__restrict__ x, const float2 *__restrict__ x_dw,
+                   double *__restrict__ y, const unsigned long long *__restrict__ flag,
+                   unsigned long long epoch, int *__restrict__ status)
+{
+    constexpr int V = 2, NT = NCW * 32, R = NT * U * V, STAGE_BYTES = R * 8;
+    extern __shared__ __align__(128) uint8_t ring[];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+    const bool emu = *flag == (epoch << 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == NCW) {
+        if (lane != 0) return;
+        const uint8_t *src = emu ? reinterpret_cast<const uint8_t *>(dia_dw)
+                                 : reinterpret_cast<const uint8_t *>(dia_val);
+        int stage = 0;
+        uint32_t phase = 0;
+        int64_t issued = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+            const int64_t ib = u / upb;
+            const int32_t t0 = (int32_t)(u - ib * upb) * R;
+            const int64_t r0 = ib * (int64_t)n_b;
+            const int32_t rows = (int32_t)((n - r0 < n_b) ? (n - r0) : n_b);
+            if (t0 >= rows) continue;
+            const int32_t ru = (rows - t0 < R) ? rows - t0 : R;
+            const uint32_t bytes = (uint32_t)(((int64_t)ru * 8 + 15) & ~(int64_t)15);
+            const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
+            for (int32_t p = p0; p < p1; p++) {
+                if (!mbar_wait(&empty[stage], phase ^ 1)) {
+                    atomicOr(status, 1);
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[stage], bytes);
+                bulk_load(ring + (size_t)stage * STAGE_BYTES,
+                          src + ((int64_t)p * n_b + t0) * 8, bytes, &full[stage]);
+                issued++;
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+            }
+        }
+        if (!ok) {
+            const int64_t k = issued < STAGES ? issued : STAGES;
+            for (int64_t q = 1; q <= k; q++) {
+                int st = stage - (int)q;
+                uint32_t ph = phase;
+                if (st < 0) {
+                    st += STAGES;
+                    ph ^= 1;
+                }
+                mbar_wait(&full[st], ph);
+            }
+        }
+        return;
+    }
+    if (emu)
+        tma_dw_consumer<true, NCW, U, D, STAGES>(n, n_b, upb, n_units, dia_ptr, dia_offset,
+                                                 csr_row_ptr, csr_col, csr_val, csr_dw, x, x_dw,
+                                                 y, ring, full, empty, status);
+    else
+        tma_dw_consumer<false, NCW, U, D, STAGES>(n, n_b, upb, n_units, dia_ptr, dia_offset,
+                                                  csr_row_ptr, csr_col, csr_val, csr_dw, x, x_dw,
+                                                  y, ring, full, empty, status);
+}
+
+template <int NCW, int U, int D, int STAGES>
+int launch_tma_dw_cfg(mhdc_matrix *A, const void *d_x, void *d_y, unsigned long long epoch,
+                      cudaStream_t st)
+{
+    constexpr int R = NCW * 32 * U * 2, THREADS = NCW * 32 + 32;
+    constexpr size_t SMEM = (size_t)STAGES * R * 8;
+    auto kern = k_mhdc_spmv_tma_dw<NCW, U, D, STAGES>;
+    static int occ = -1;
+    if (occ < 0) {
+        MHDC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)SMEM));
+        int o = 0;
+        MHDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, THREADS, SMEM));
+        occ = o > 0 ? o : 1;
+    }
+    const int32_t upb = (int32_t)((A->n_b + R - 1) / R);
+    const int64_t units = (int64_t)upb * A->n_blocks;
+    int64_t grid = (int64_t)num_sms_tma() * occ;
+    if (grid > units) grid = units;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, THREADS, SMEM, st>>>(
+        A->n, A->n_b, upb, units, A->dia_ptr, A->dia_offset, (const double *)A->dia_val,
+        A->dia_dw, A->csr_row_ptr, A->csr_col, (const double *)A->csr_val, A->csr_dw,
+        (const double *)d_x, A->x_dw, (double *)d_y, A->dw_flag, epoch, A->status);
+    MHDC_LAUNCH_CHECK("k_mhdc_spmv_tma_dw");
+    return MHDC_OK;
+}
+
 int num_sms_tma()
 {
     static int sms = 0;
@@ -386,6 +657,16 @@ int launch_tma_typed(const mhdc_matrix *A, int shape, const void *d_x, void *d_y
 }
 
 }  // namespace
+
+int launch_spmv_tma_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y,
+                       unsigned long long epoch, cudaStream_t stream)
+{
+    switch (shape) {
+    case 0: return launch_tma_dw_cfg<8, 1, 2, 16>(A, d_x, d_y, epoch, stream);
+    case 1: return launch_tma_dw_cfg<4, 2, 2, 16>(A, d_x, d_y, epoch, stream);
+    default: return launch_tma_dw_cfg<8, 1, 1, 24>(A, d_x, d_y, epoch, stream);
+    }
+}
 
 bool tma_supported(const mhdc_matrix *A)
 {

@@ -226,11 +226,26 @@ def test_misaligned_x_gives_identical_result(mh):
         xd, _ = x_device(synth.uniform_vector(A.n, 9), dt)
         buf = t.zeros(A.n + 1, dtype=xd.dtype, device="cuda")
         buf[1:] = xd
-        y1 = y_empty(A.n, dt)
-        y2 = y_empty(A.n, dt)
-        mh.mhdc_spmv(h, xd, y1)
-        mh.mhdc_spmv(h, buf[1:], y2)
-        assert t.equal(y1, y2)
+        for v in range(-1, mh.MHDC_NUM_VARIANTS):
+            mh.mhdc_set_variant(h, v)
+            y1 = y_empty(A.n, dt)
+            y2 = y_empty(A.n, dt)
+            mh.mhdc_spmv(h, xd, y1)
+            mh.mhdc_spmv(h, buf[1:], y2)
+            assert t.equal(y1, y2), (dt, v)
+        # an x far outside the emulation window sends FP64 variants down the
+        # native path, which also reads the unaligned x
+        if dt == "f64":
+            buf[1 + A.n // 2] = 1e300
+            for v in range(mh.FIRST_EMULATED_VARIANT, mh.MHDC_NUM_VARIANTS):
+                mh.mhdc_set_variant(h, v)
+                y1 = y_empty(A.n, dt)
+                mh.mhdc_spmv(h, buf[1:], y1)
+                mh.mhdc_set_variant(h, -1)
+                y2 = y_empty(A.n, dt)
+                mh.mhdc_spmv(h, buf[1:], y2)
+                assert t.equal(y1, y2), v
+        mh.mhdc_check(h)
 
 
 def test_repeatable_and_host_path(mh):
