@@ -140,6 +140,25 @@ def fp64_peak_tflops():
     return 2 * 2 * sms * mhz * 1e6 / 1e12
 
 
+def profiled_traffic(variant):
+    """DRAM bytes per launch from the committed ncu summary of the tuned
+    kernel, if that summary covers this variant and spmv.cu is unchanged
+    since the capture; else None."""
+    import hashlib
+    try:
+        md = open(os.path.join(ROOT, "profiles", "mhdc_spmv_f64_stencil27_128.md")).read()
+        src = open(os.path.join(ROOT, "paper_2105_04937_gb300", "csrc", "spmv.cu"), "rb").read()
+    except OSError:
+        return None
+    fields = dict(line.split(": ", 1) for line in md.splitlines()
+                  if line.startswith(("traffic_bytes:", "kernel:", "source_sha1_16:")))
+    if fields.get("kernel") != f"k_mhdc_spmv<double> variant {variant}":
+        return None
+    if fields.get("source_sha1_16") != hashlib.sha1(src).hexdigest()[:16]:
+        return None
+    return int(fields["traffic_bytes"])
+
+
 def gflops(nnz, sec):
     return 2.0 * nnz / sec / 1e9
 
@@ -467,7 +486,8 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": round(alu_achieved, 4),
                          "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                         "frac": round(alu_achieved / fp64_peak, 4), "traffic": None,
+                         "frac": round(alu_achieved / fp64_peak, 4),
+                         "traffic": profiled_traffic(best_variant),
                          "kernel": f"k_mhdc_spmv<double> variant {best_variant}",
                          "flops_per_launch": 2 * slots,
                          "peak_source": "FP64: 2 FMA/clk/SM x 2 flop x SMs x max SM clock "
