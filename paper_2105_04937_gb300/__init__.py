@@ -225,10 +225,13 @@ def mhdc_spmv_host(A: Matrix, x, y, stream=None):
 def mhdc_spmm(A: Matrix, X, Y, stream=None):
     """Y = A X for row-major n x k device tensors X and Y."""
     xt, yt = _xy_types(A)
-    _check_dev(X, xt, None, "X")
-    _check_dev(Y, yt, None, "Y")
-    if X.dim() != 2 or Y.dim() != 2 or X.shape[0] < A.n or Y.shape[0] < A.n or X.shape[1] != Y.shape[1]:
-        raise ValueError("X and Y must be n x k")
+    for t, dt, nm in ((X, xt, "X"), (Y, yt, "Y")):
+        if not t.is_cuda or t.dtype != dt:
+            raise TypeError(f"{nm} must be a CUDA tensor of {dt}")
+        if t.dim() != 2 or t.stride(1) != 1 or t.shape[0] < A.n:
+            raise ValueError(f"{nm} must be n x k with unit column stride")
+    if X.shape[1] != Y.shape[1]:
+        raise ValueError("X and Y must have the same number of columns")
     k = X.shape[1]
     _check(lib().mhdc_spmm(C.c_void_p(A.handle), k, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0),
                            _stream(stream)), "mhdc_spmm")

@@ -398,6 +398,111 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
             if (tl[u] + m < rows) y[r0 + tl[u] + m] = dw::f32_to_f64(sh[u][m]) + dw::f32_to_f64(sl[u][m]);
 }
 
+// ---------------------------------------------------------------------------
+// SpMM: Y = A X for k right-hand sides (row-major X, Y), the M-HDC kernel of
+// Fig. 13 with each scalar x_j replaced by row j of X.  A lane owns U rows
+// (r, r + 32, ...) of a warp tile and KC columns [c0, c0 + KC) of Y; per
+// diagonal it loads one value per row (coalesced across the warp) and the KC
+// contiguous entries of X's row j = i + off (16-byte vectors when aligned),
+// so a warp reads 32 consecutive rows of X per diagonal.
+// ---------------------------------------------------------------------------
+template <typename X, int KC>
+__device__ __forceinline__ void load_row(const X *__restrict__ p, bool vec, X (&v)[KC])
+{
+    if constexpr ((KC * sizeof(X)) % 16 == 0) {
+        if (vec) {
+#pragma unroll
+            for (int q = 0; q < (int)(KC * sizeof(X) / 16); q++) {
+                const uint4 r = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+                memcpy(reinterpret_cast<char *>(v) + 16 * q, &r, 16);
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < KC; c++) v[c] = __ldg(p + c);
+}
+
+template <typename VT, int KC, int U>
+__global__ void __launch_bounds__(SPMV_THREADS)
+k_mhdc_spmm(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles, int32_t c0, int32_t k,
+            const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
+            const VT *__restrict__ dia_val, const int32_t *__restrict__ csr_row_ptr,
+            const int32_t *__restrict__ csr_col, const VT *__restrict__ csr_val,
+            const typename Tr<VT>::X *__restrict__ Xm, int64_t ldx,
+            typename Tr<VT>::Y *__restrict__ Ym, int64_t ldy)
+{
+    using Acc = typename Tr<VT>::Acc;
+    using X = typename Tr<VT>::X;
+    constexpr int RW = 32 * U;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5);
+    if (w >= n_tiles) return;
+    const int64_t ib = w / tpb;
+    const int32_t tw = (int32_t)(w - ib * tpb) * RW;
+    const int64_t r0 = ib * (int64_t)n_b;
+    const int32_t rows = (int32_t)((n - r0 < n_b) ? (n - r0) : n_b);
+    if (tw >= rows) return;
+    const int kc = (k - c0 < KC) ? k - c0 : KC;  // columns of this pass (ragged last pass)
+    const bool vec = kc == KC && (reinterpret_cast<uintptr_t>(Xm + c0) & 15) == 0 &&
+                     ((ldx * (int64_t)sizeof(X)) & 15) == 0;
+    Acc acc[U][KC];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+#pragma unroll
+        for (int c = 0; c < KC; c++) acc[u][c] = Acc(0);
+    auto add_row = [&](int u, Acc a, int64_t j) {
+        X xv[KC];
+        const X *xp = Xm + j * ldx + c0;
+        if (kc == KC) {
+            load_row<X, KC>(xp, vec, xv);
+        } else {
+#pragma unroll
+            for (int c = 0; c < KC; c++) xv[c] = c < kc ? __ldg(xp + c) : X(0);
+        }
+#pragma unroll
+        for (int c = 0; c < KC; c++) acc[u][c] += a * widen(xv[c]);
+    };
+    // CSR remainder rows (Fig. 13, first loop)
+    {
+        const int32_t tend = (tw + RW < rows) ? tw + RW : rows;
+        if (csr_row_ptr[r0 + tw] != csr_row_ptr[r0 + tend]) {
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int32_t t = tw + u * 32 + lane;
+                if (t < rows) {
+                    const int64_t i = r0 + t;
+                    const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
+                    for (int32_t q = a; q < b; q++) add_row(u, widen(csr_val[q]), csr_col[q]);
+                }
+            }
+        }
+    }
+    // diagonals (Fig. 13, second loop)
+    const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
+#pragma unroll 2
+    for (int32_t p = p0; p < p1; p++) {
+        const int64_t off = dia_offset[p];
+        const VT *vp = dia_val + (int64_t)p * n_b;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int32_t t = tw + u * 32 + lane;
+            const int64_t j = r0 + t + off;
+            if (t < rows && j >= 0 && j < n) add_row(u, widen(vp[t]), j);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int32_t t = tw + u * 32 + lane;
+        if (t < rows) {
+            typename Tr<VT>::Y *yp = Ym + (r0 + t) * ldy + c0;
+#pragma unroll
+            for (int c = 0; c < KC; c++)
+                if (c < kc) yp[c] = acc[u][c];
+        }
+    }
+}
+
 // Plain CSR (Fig. 2), one thread per row: s = fma(val[k], x[col_ind[k]], s)
 // over the row, four entries per step.  One FP64 FMA per nonzero and no
 // cross-lane reduction: on GB300 the FP64 pipe (about 0.6 T FMA/s) rather
@@ -691,10 +796,51 @@ int launch_fma_probe(int fp64, int iters, void *out, cudaStream_t stream)
     return MHDC_OK;
 }
 
-int launch_spmm(const mhdc_matrix *, int, const void *, int64_t, void *, int64_t, cudaStream_t)
+template <typename VT, int KC>
+int spmm_pass(const mhdc_matrix *A, int32_t c0, int32_t k, const void *X, int64_t ldx, void *Y,
+              int64_t ldy, cudaStream_t st)
 {
-    set_error_msg("mhdc_spmm: not available in this build");
-    return MHDC_ERR_UNSUPPORTED;
+    constexpr int U = KC >= 8 ? 1 : 2;
+    constexpr int RW = 32 * U;
+    const int32_t tpb = (int32_t)((A->n_b + RW - 1) / RW);
+    const int64_t tiles = (int64_t)tpb * A->n_blocks;
+    const int64_t grid = (tiles + SPMV_WARPS - 1) / SPMV_WARPS;
+    k_mhdc_spmm<VT, KC, U><<<(unsigned)grid, SPMV_THREADS, 0, st>>>(
+        A->n, A->n_b, tpb, tiles, c0, k, A->dia_ptr, A->dia_offset,
+        static_cast<const VT *>(A->dia_val), A->csr_row_ptr, A->csr_col,
+        static_cast<const VT *>(A->csr_val), static_cast<const typename Tr<VT>::X *>(X), ldx,
+        static_cast<typename Tr<VT>::Y *>(Y), ldy);
+    MHDC_LAUNCH_CHECK("k_mhdc_spmm");
+    return MHDC_OK;
+}
+
+template <typename VT>
+int spmm_typed(const mhdc_matrix *A, int k, const void *X, int64_t ldx, void *Y, int64_t ldy,
+               cudaStream_t st)
+{
+    // column passes of at most 16; the pass width follows k
+    for (int32_t c0 = 0; c0 < k; c0 += 16) {
+        const int kc = (k - c0 < 16) ? k - c0 : 16;
+        int rc;
+        if (kc > 8) rc = spmm_pass<VT, 16>(A, c0, k, X, ldx, Y, ldy, st);
+        else if (kc > 4) rc = spmm_pass<VT, 8>(A, c0, k, X, ldx, Y, ldy, st);
+        else if (kc > 2) rc = spmm_pass<VT, 4>(A, c0, k, X, ldx, Y, ldy, st);
+        else rc = spmm_pass<VT, 2>(A, c0, k, X, ldx, Y, ldy, st);
+        if (rc != MHDC_OK) return rc;
+    }
+    return MHDC_OK;
+}
+
+int launch_spmm(mhdc_matrix *A, int k, const void *d_X, int64_t ldx, void *d_Y, int64_t ldy,
+                cudaStream_t stream)
+{
+    if (A->n == 0) return MHDC_OK;
+    if (k == 1 && ldx == 1 && ldy == 1) return launch_spmv(A, d_X, d_Y, stream);
+    switch (A->dtype) {
+    case MHDC_F64: return spmm_typed<double>(A, k, d_X, ldx, d_Y, ldy, stream);
+    case MHDC_F32: return spmm_typed<float>(A, k, d_X, ldx, d_Y, ldy, stream);
+    default: return spmm_typed<__nv_bfloat16>(A, k, d_X, ldx, d_Y, ldy, stream);
+    }
 }
 
 int launch_stream_bench(int64_t N, const double *A, const double *B, const int32_t *I, double *C,

@@ -90,3 +90,38 @@ def check_spmv(mh, h, M, A, x64, dtype):
     bad = np.nonzero(err > bnd)[0]
     assert bad.size == 0, ("vs exact", dtype, bad[:5], err[bad[:5]], bnd[bad[:5]])
     return yg
+
+
+def check_spmm(mh, h, M, A, X64, dtype, pad=0):
+    """mhdc_spmm against the oracle column by column (same bounds as SpMV).
+    X64: n x k float64; pad > 0 stores X and Y with leading dimension k + pad."""
+    t = torch()
+    n, k = X64.shape
+    Xs = oracle.store(X64.ravel(), dtype).reshape(n, k)
+    Xw = oracle.widen(Xs.ravel(), dtype).reshape(n, k)
+    ld = k + pad
+    if dtype == "bf16":
+        base = t.zeros((n, ld), dtype=t.int16)
+        base[:, :k] = t.from_numpy(Xs.view(np.int16))
+        Xd = base.cuda().view(t.bfloat16)
+    else:
+        base = t.zeros((n, ld), dtype=t.float64 if dtype == "f64" else t.float32)
+        base[:, :k] = t.from_numpy(Xs)
+        Xd = base.cuda()
+    yt = t.float64 if dtype == "f64" else t.float32
+    Yfull = t.full((n, ld), float("nan"), dtype=yt, device="cuda")
+    Yd = Yfull[:, :k]
+    Xv = Xd[:, :k]
+    mh.mhdc_spmm(h, Xv, Yd)
+    t.cuda.synchronize()
+    Y = Yfull.double().cpu().numpy()
+    if pad:
+        assert np.all(np.isnan(Y[:, k:])), "mhdc_spmm wrote outside the k columns"
+    for c in range(k):
+        yg = Y[:, c]
+        y_st = oracle.mhdc_spmv(M, Xw[:, c])
+        abs_st, terms = oracle.mhdc_absrow(M, Xw[:, c])
+        assert np.all(np.abs(yg - y_st) <= oracle.bound_vs_stored(abs_st, terms, dtype)), (dtype, k, c)
+        x64 = np.ascontiguousarray(X64[:, c])
+        bnd = oracle.bound_vs_exact(oracle.csr_absrow(A, x64), terms, dtype)
+        assert np.all(np.abs(yg - oracle.csr_spmv(A, x64)) <= bnd), (dtype, k, c)

@@ -10,7 +10,8 @@ import pytest
 import oracle
 import synth
 from conftest import read_golden
-from gpu_util import (build, check_build, check_spmv, dev_csr, torch, x_device, y_empty)
+from gpu_util import (build, check_build, check_spmm, check_spmv, dev_csr, torch, x_device,
+                      y_empty)
 
 pytestmark = pytest.mark.gpu
 
@@ -424,3 +425,40 @@ def test_emulated_fp64_disabled_by_values_or_row_length(mh):
         y0, ys = _native_and_emulated(mh, h, xd)
         for y in ys:
             assert t.equal(y, y0)
+
+
+# ---------------------------------------------------------------- SpMM
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_spmm_matches_columnwise_oracle(mh, dt):
+    cases = [(synth.config_matrix("stencil27_128", scale=0.25), 4096),
+             (synth.config_matrix("scattered_4m", scale=1 / 256), 2048),
+             (synth.random_sparse(123, 0.05, seed=4, diag_bias=0.5), 10),
+             (synth.config_matrix("stencil7_32", scale=0.5), 999)]
+    for A, n_b in cases:
+        h, M = check_build(mh, A, n_b, 0.6, dt)
+        for k in (1, 2, 3, 4, 5, 8, 13, 16, 17, 33):
+            X = synth.uniform_vector(A.n * k, 40 + k).reshape(A.n, k)
+            check_spmm(mh, h, M, A, X, dt)
+        X = synth.uniform_vector(A.n * 6, 77).reshape(A.n, 6)
+        check_spmm(mh, h, M, A, X, dt, pad=3)
+
+
+def test_spmm_full_size_fp32_k16(mh):
+    # the 128^3 27-point matrix with 16 right-hand sides in FP32
+    A = synth.config_matrix("stencil27_128")
+    h, M = check_build(mh, A, 4096, 0.6, "f32")
+    X = synth.uniform_vector(A.n * 16, 5).reshape(A.n, 16)
+    check_spmm(mh, h, M, A, X, "f32")
+
+
+def test_spmm_k64_and_bad_args(mh):
+    t = torch()
+    A = synth.config_matrix("stencil7_32", scale=0.25)
+    h, M = check_build(mh, A, 64, 0.6, "f64")
+    X = synth.uniform_vector(A.n * 64, 9).reshape(A.n, 64)
+    check_spmm(mh, h, M, A, X, "f64")
+    Xd = t.zeros((A.n, 65), dtype=t.float64, device="cuda")
+    Yd = t.zeros((A.n, 65), dtype=t.float64, device="cuda")
+    with pytest.raises(mh.MhdcError):
+        mh.mhdc_spmm(h, Xd, Yd)
