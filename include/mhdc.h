@@ -203,6 +203,33 @@ int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *
  */
 int mhdc_check(mhdc_handle A);
 
+/*
+ * Batched product: y_i = A_i x_i for m handles in one persistent launch (no
+ * counterpart in the paper; it serves many small systems, where one launch
+ * per matrix leaves the GPU idle).  Warps take chunks of row tiles of all
+ * matrices from a global counter, so uneven sizes balance.
+ *
+ * mhdc_batch_create  -- batch of m >= 1 handles of one dtype (host array
+ *                       `mats`); the handles must outlive the batch, which
+ *                       only references them.  Synchronous.
+ * mhdc_batch_spmv    -- one launch on `stream`: d_xs and d_ys are DEVICE arrays
+ *                       of m device pointers (x_i: n_i values of the x dtype,
+ *                       y_i: n_i values of the y dtype).  Launches of one batch
+ *                       must not overlap on the GPU (they share a counter).
+ * mhdc_batch_spmv_graph -- the same launch captured once in a CUDA graph (on a
+ *                       stream owned by the batch) and replayed on `stream`;
+ *                       recaptured when d_xs or d_ys change.  The pointer
+ *                       arrays are read at run time, so their contents (and the
+ *                       vectors) may change between replays.
+ * mhdc_batch_destroy -- free the batch (not the handles).
+ */
+typedef struct mhdc_batch *mhdc_batch_handle;
+int mhdc_batch_create(int32_t m, const mhdc_handle *mats, mhdc_batch_handle *out);
+int mhdc_batch_spmv(mhdc_batch_handle B, const void *const *d_xs, void *const *d_ys, void *stream);
+int mhdc_batch_spmv_graph(mhdc_batch_handle B, const void *const *d_xs, void *const *d_ys,
+                          void *stream);
+int mhdc_batch_destroy(mhdc_batch_handle B);
+
 /* mhdc_destroy -- free the handle and its device arrays (NULL is a no-op). */
 int mhdc_destroy(mhdc_handle A);
 

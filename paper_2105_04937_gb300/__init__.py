@@ -25,7 +25,8 @@ __all__ = [
     "mhdc_info", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
     "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "mhdc_check",
     "mhdc_read_bench", "mhdc_read_bench_ctas", "mhdc_build_noalloc",
-    "mhdc_fma_bench",
+    "mhdc_fma_bench", "Batch", "mhdc_batch_create", "mhdc_batch_spmv", "mhdc_batch_spmv_graph",
+    "mhdc_batch_destroy", "pointer_array",
 ]
 
 MHDC_F64, MHDC_F32, MHDC_BF16 = 0, 1, 2
@@ -70,6 +71,10 @@ _SIGS = {
     "mhdc_read_bench": [_I64, _P, _P, _P],
     "mhdc_read_bench_ctas": [],
     "mhdc_fma_bench": [_I32, _I32, _P, _P],
+    "mhdc_batch_create": [_I32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)],
+    "mhdc_batch_spmv": [_P, _P, _P, _P],
+    "mhdc_batch_spmv_graph": [_P, _P, _P, _P],
+    "mhdc_batch_destroy": [_P],
     "mhdc_build_noalloc": [_I64, _P, _P, _P, _I32, _D, _I32, _P, _P, _P, _I64, _P, _P, _P, _I64,
                            C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P],
     "mhdc_tune": [_P, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
@@ -372,3 +377,59 @@ def mhdc_fma_bench(fp64: bool, iters: int, out, stream=None):
     _check(lib().mhdc_fma_bench(1 if fp64 else 0, int(iters), _ptr(out), _stream(stream)),
            "mhdc_fma_bench")
     return out
+
+
+class Batch:
+    """Owner of an mhdc_batch_handle; keeps its matrices alive."""
+
+    def __init__(self, handle: int, mats):
+        self.handle = handle
+        self.mats = list(mats)
+
+    def destroy(self):
+        if self.handle:
+            lib().mhdc_batch_destroy(C.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def mhdc_batch_create(mats) -> Batch:
+    """Batch of Matrix handles of one dtype for one-launch products."""
+    arr = (C.c_void_p * len(mats))(*[m.handle for m in mats])
+    h = C.c_void_p()
+    _check(lib().mhdc_batch_create(len(mats), arr, C.byref(h)), "mhdc_batch_create")
+    return Batch(h.value, mats)
+
+
+def pointer_array(tensors):
+    """Device int64 tensor holding the data pointers of CUDA tensors."""
+    import torch
+    return torch.tensor([t.data_ptr() for t in tensors], dtype=torch.int64, device="cuda")
+
+
+def _batch_args(B, xs, ys):
+    import torch
+    for a, nm in ((xs, "xs"), (ys, "ys")):
+        if not a.is_cuda or a.dtype != torch.int64 or a.numel() < len(B.mats):
+            raise ValueError(f"{nm} must be a CUDA int64 tensor of {len(B.mats)} device pointers")
+    return C.c_void_p(B.handle), _ptr(xs), _ptr(ys)
+
+
+def mhdc_batch_spmv(B: Batch, xs, ys, stream=None):
+    """y_i = A_i x_i for every matrix of B in one launch; xs, ys from pointer_array()."""
+    _check(lib().mhdc_batch_spmv(*_batch_args(B, xs, ys), _stream(stream)), "mhdc_batch_spmv")
+
+
+def mhdc_batch_spmv_graph(B: Batch, xs, ys, stream=None):
+    """mhdc_batch_spmv replayed from a CUDA graph captured on first use."""
+    _check(lib().mhdc_batch_spmv_graph(*_batch_args(B, xs, ys), _stream(stream)),
+           "mhdc_batch_spmv_graph")
+
+
+def mhdc_batch_destroy(B: Batch):
+    B.destroy()

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "mhdc_internal.cuh"
 
@@ -191,6 +192,120 @@ int mhdc_check(mhdc_handle A)
         set_error_msg("a bounded device-side wait gave up");
         return MHDC_ERR_TIMEOUT;
     }
+    return MHDC_OK;
+}
+
+int mhdc_batch_create(int32_t m, const mhdc_handle *mats, mhdc_batch_handle *out)
+{
+    if (m < 1 || !mats || !out) {
+        set_error_msg("mhdc_batch_create: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    for (int32_t i = 0; i < m; i++) {
+        if (!mats[i] || mats[i]->dtype != mats[0]->dtype) {
+            set_error_msg("mhdc_batch_create: null handle or mixed dtypes");
+            return MHDC_ERR_INVALID_ARG;
+        }
+    }
+    std::vector<BatchMat> h((size_t)m);
+    int64_t tiles = 0, nnz = 0;
+    for (int32_t i = 0; i < m; i++) {
+        const mhdc_matrix *A = mats[i];
+        int vec = 0;
+        const int rw = batch_tile_rows(A->dtype, A->n_b, &vec);
+        BatchMat &b = h[(size_t)i];
+        b.n = A->n;
+        b.n_b = A->n_b;
+        b.tpb = (int32_t)((A->n_b + rw - 1) / rw);
+        b.vec = vec;
+        b.pad = 0;
+        b.tile0 = tiles;
+        b.dia_ptr = A->dia_ptr;
+        b.dia_offset = A->dia_offset;
+        b.dia_val = A->dia_val;
+        b.csr_row_ptr = A->csr_row_ptr;
+        b.csr_col = A->csr_col;
+        b.csr_val = A->csr_val;
+        tiles += (int64_t)b.tpb * A->n_blocks;
+        nnz += A->nnz;
+    }
+    mhdc_batch *B = new mhdc_batch();
+    B->m = m;
+    B->dtype = mats[0]->dtype;
+    B->total_tiles = tiles;
+    B->total_nnz = nnz;
+    cudaGetDevice(&B->device);
+    cudaError_t e = cudaMalloc((void **)&B->d_mats, sizeof(BatchMat) * (size_t)m);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&B->d_ctr, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(B->d_mats, h.data(), sizeof(BatchMat) * (size_t)m, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(B->d_ctr, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking);
+    int rc = e == cudaSuccess ? batch_prepare(B) : MHDC_ERR_CUDA;
+    if (e != cudaSuccess) set_error("mhdc_batch_create", e);
+    if (rc != MHDC_OK) {
+        mhdc_batch_destroy(B);
+        return e == cudaErrorMemoryAllocation ? MHDC_ERR_OOM : rc;
+    }
+    *out = B;
+    return MHDC_OK;
+}
+
+int mhdc_batch_spmv(mhdc_batch_handle B, const void *const *d_xs, void *const *d_ys, void *stream)
+{
+    if (!B || !d_xs || !d_ys) {
+        set_error_msg("mhdc_batch_spmv: null argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    return launch_batch(B, d_xs, d_ys, (cudaStream_t)stream);
+}
+
+int mhdc_batch_spmv_graph(mhdc_batch_handle B, const void *const *d_xs, void *const *d_ys,
+                          void *stream)
+{
+    if (!B || !d_xs || !d_ys) {
+        set_error_msg("mhdc_batch_spmv_graph: null argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    if (!B->graph || B->g_xs != d_xs || B->g_ys != d_ys) {
+        if (B->graph) {
+            cudaGraphExecDestroy(B->graph);
+            B->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        MHDC_CUDA_TRY(cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = launch_batch(B, d_xs, d_ys, B->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(B->cap_stream, &g);
+        if (rc != MHDC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) {
+            set_error("cudaStreamEndCapture", e);
+            return MHDC_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&B->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            B->graph = nullptr;
+            set_error("cudaGraphInstantiate", e);
+            return MHDC_ERR_CUDA;
+        }
+        B->g_xs = d_xs;
+        B->g_ys = d_ys;
+    }
+    MHDC_CUDA_TRY(cudaGraphLaunch(B->graph, (cudaStream_t)stream));
+    return MHDC_OK;
+}
+
+int mhdc_batch_destroy(mhdc_batch_handle B)
+{
+    if (!B) return MHDC_OK;
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+    cudaFree(B->d_mats);
+    cudaFree(B->d_ctr);
+    delete B;
     return MHDC_OK;
 }
 

@@ -36,6 +36,33 @@ struct mhdc_matrix {
     bool dw_ok = false;              // values inside the window, <= DW_MAX_TERMS terms per row
 };
 
+// One matrix of a batch, as the batched kernel reads it (device memory).
+struct BatchMat {
+    int64_t n;
+    int64_t tile0;      // first warp tile of this matrix in the batch's tile list
+    int32_t n_b, tpb;   // rows per block, warp tiles per block
+    int32_t vec, pad;   // 16-byte value loads possible (n_b % V == 0)
+    const int32_t *dia_ptr, *dia_offset;
+    const void *dia_val;
+    const int32_t *csr_row_ptr, *csr_col;
+    const void *csr_val;
+};
+
+// A batch of handles (same dtype) for mhdc_batch_spmv; it does not own them.
+struct mhdc_batch {
+    int32_t m = 0, dtype = 0;
+    int device = 0;
+    BatchMat *d_mats = nullptr;
+    unsigned long long *d_ctr = nullptr;  // [next tile, finished CTAs]
+    int64_t total_tiles = 0;
+    int64_t total_nnz = 0;
+    int grid = 0;
+    cudaStream_t cap_stream = nullptr;    // stream the graph is captured on
+    cudaGraphExec_t graph = nullptr;
+    const void *const *g_xs = nullptr;    // pointer arrays baked into the graph
+    void *const *g_ys = nullptr;
+};
+
 namespace mhdc {
 
 inline size_t value_size(int dtype)
@@ -72,6 +99,9 @@ int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *v
 int launch_stream_bench(int64_t N, const double *A, const double *B, const int32_t *I, double *C,
                         int indirect, cudaStream_t stream);
 int spmv_grid_for(const mhdc_matrix *A);
+int batch_prepare(mhdc_batch *B);
+int batch_tile_rows(int dtype, int n_b, int *vec);
+int launch_batch(mhdc_batch *B, const void *const *d_xs, void *const *d_ys, cudaStream_t st);
 int launch_read_bench(int64_t N, const double *A, double *out, int grid, cudaStream_t stream);
 int read_bench_grid();
 int launch_fma_probe(int fp64, int iters, void *out, cudaStream_t stream);

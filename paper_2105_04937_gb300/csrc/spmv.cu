@@ -855,3 +855,106 @@ int launch_stream_bench(int64_t N, const double *A, const double *B, const int32
 }
 
 }  // namespace mhdc
+
+// ---------------------------------------------------------------------------
+// Batched product: y_i = A_i x_i for m matrices in one persistent launch.
+// The warp tiles of all matrices form one list (matrix i's tiles start at
+// tile0[i]); warps take chunks of BATCH_CHUNK tiles from a global counter, so
+// matrices of uneven size share the GPU without a launch per matrix.  Each
+// tile runs the register kernel's code (reg_tile, U = 1, D = 2).  The last CTA
+// to finish resets the counters for the next launch (no waits between CTAs).
+// ---------------------------------------------------------------------------
+namespace mhdc {
+namespace {
+
+constexpr int BATCH_CHUNK = 4;
+
+template <typename VT>
+__global__ void __launch_bounds__(SPMV_THREADS)
+k_batch_spmv(int32_t m, const BatchMat *__restrict__ mats, int64_t total_tiles,
+             const void *const *__restrict__ xs, void *const *__restrict__ ys,
+             unsigned long long *__restrict__ ctr)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctr[0], (unsigned long long)BATCH_CHUNK);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= (unsigned long long)total_tiles) break;
+        for (int c = 0; c < BATCH_CHUNK; c++) {
+            const int64_t g = (int64_t)base + c;
+            if (g >= total_tiles) break;
+            int lo = 0, hi = m - 1;  // last matrix with tile0 <= g
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (mats[mid].tile0 <= g) lo = mid;
+                else hi = mid - 1;
+            }
+            const BatchMat &M = mats[lo];
+            const int64_t w = g - M.tile0;
+            using X = typename Tr<VT>::X;
+            using Y = typename Tr<VT>::Y;
+            if (M.vec)
+                reg_tile<VT, 1, 2, true>(w, M.n, M.n_b, M.tpb, M.dia_ptr, M.dia_offset,
+                                         static_cast<const VT *>(M.dia_val), M.csr_row_ptr,
+                                         M.csr_col, static_cast<const VT *>(M.csr_val),
+                                         static_cast<const X *>(xs[lo]), static_cast<Y *>(ys[lo]));
+            else
+                reg_tile<VT, 1, 2, false>(w, M.n, M.n_b, M.tpb, M.dia_ptr, M.dia_offset,
+                                          static_cast<const VT *>(M.dia_val), M.csr_row_ptr,
+                                          M.csr_col, static_cast<const VT *>(M.csr_val),
+                                          static_cast<const X *>(xs[lo]), static_cast<Y *>(ys[lo]));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctr[1], 1ull) == (unsigned long long)gridDim.x - 1) {
+            ctr[0] = 0;
+            ctr[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <typename VT>
+const void *batch_kernel() { return (const void *)k_batch_spmv<VT>; }
+
+}  // namespace
+
+int batch_prepare(mhdc_batch *B)
+{
+    const void *fn = B->dtype == MHDC_F64 ? batch_kernel<double>()
+                     : B->dtype == MHDC_F32 ? batch_kernel<float>() : batch_kernel<__nv_bfloat16>();
+    int occ = 0;
+    MHDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, SPMV_THREADS, 0));
+    if (occ < 1) occ = 1;
+    const int64_t need = (B->total_tiles + (int64_t)SPMV_WARPS * BATCH_CHUNK - 1) /
+                         ((int64_t)SPMV_WARPS * BATCH_CHUNK);
+    const int64_t cap = (int64_t)num_sms() * occ;
+    B->grid = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+    return MHDC_OK;
+}
+
+int batch_tile_rows(int dtype, int n_b, int *vec)
+{
+    const int V = dtype == MHDC_F64 ? 2 : dtype == MHDC_F32 ? 4 : 8;
+    *vec = (n_b % V) == 0;
+    return *vec ? 32 * V : 32;
+}
+
+int launch_batch(mhdc_batch *B, const void *const *d_xs, void *const *d_ys, cudaStream_t st)
+{
+    if (B->total_tiles == 0) return MHDC_OK;
+    const void *fn = B->dtype == MHDC_F64 ? batch_kernel<double>()
+                     : B->dtype == MHDC_F32 ? batch_kernel<float>() : batch_kernel<__nv_bfloat16>();
+    int32_t m = B->m;
+    const BatchMat *mats = B->d_mats;
+    int64_t tiles = B->total_tiles;
+    unsigned long long *ctr = B->d_ctr;
+    void *args[] = {&m, (void *)&mats, &tiles, (void *)&d_xs, (void *)&d_ys, (void *)&ctr};
+    MHDC_CUDA_TRY(cudaLaunchKernel(fn, dim3(B->grid), dim3(SPMV_THREADS), args, 0, st));
+    return MHDC_OK;
+}
+
+}  // namespace mhdc

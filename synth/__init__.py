@@ -432,7 +432,10 @@ def batch_matrices(count: int = 64, lo: int = 16, hi: int = 96, *, seed: int = 3
     mats = []
     for m in range(count):
         nx, ny, nz = (int(v) for v in edges[m])
-        mats.append(stencil_3d(nx, ny, nz, 27 if kind[m] else 7, seed=seed * 1000 + m))
+        pts = 27 if kind[m] else 7
+        mats.append(_cached(f"b:{nx}:{ny}:{nz}:{pts}:{seed * 1000 + m}",
+                            lambda nx=nx, ny=ny, nz=nz, pts=pts, sd=seed * 1000 + m:
+                            stencil_3d(nx, ny, nz, pts, seed=sd)))
     return mats
 
 

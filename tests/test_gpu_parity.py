@@ -462,3 +462,84 @@ def test_spmm_k64_and_bad_args(mh):
     Yd = t.zeros((A.n, 65), dtype=t.float64, device="cuda")
     with pytest.raises(mh.MhdcError):
         mh.mhdc_spmm(h, Xd, Yd)
+
+
+# ---------------------------------------------------------------- batched
+
+def _batch_case(mh, dt, seed):
+    rng = synth.Rng(seed, 17)
+    mats, hs, Ms, xs = [], [], [], []
+    for q in range(10):
+        e = [int(v) for v in rng.integers(3, 6, 20)]
+        if q % 3 == 2:
+            A = synth.random_sparse(200 + 17 * q, 0.04, seed=seed * 100 + q, diag_bias=0.6)
+            n_b = 37 if q % 2 else 64        # odd n_b: element loads
+        else:
+            A = synth.stencil_3d(*e, 27 if q % 2 else 7, seed=seed * 100 + q, drop_rate=0.2,
+                                 drop_block=256)
+            n_b = (256, 1024, 100)[q % 3]
+        h, M = check_build(mh, A, n_b, 0.6, dt)
+        mats.append(A); hs.append(h); Ms.append(M)
+        xs.append(synth.uniform_vector(A.n, seed * 100 + q))
+    return mats, hs, Ms, xs
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_batch_matches_oracle_and_graph_replays(mh, dt):
+    t = torch()
+    mats, hs, Ms, xs = _batch_case(mh, dt, 1)
+    B = mh.mhdc_batch_create(hs)
+    xd = [x_device(x, dt)[0] for x in xs]
+    ys = [y_empty(A.n, dt) for A in mats]
+    XP, YP = mh.pointer_array(xd), mh.pointer_array(ys)
+    for rep in range(2):     # the counter is reset by each launch
+        mh.mhdc_batch_spmv(B, XP, YP)
+        t.cuda.synchronize()
+        for A, M, x, y in zip(mats, Ms, xs, ys):
+            xs_w = oracle.widen(oracle.store(x, dt), dt)
+            ref = oracle.mhdc_spmv(M, xs_w)
+            a, terms = oracle.mhdc_absrow(M, xs_w)
+            assert np.all(np.abs(y.double().cpu().numpy() - ref) <= oracle.bound_vs_stored(a, terms, dt))
+    direct = [y.clone() for y in ys]
+    for rep in range(3):
+        for y in ys:
+            y.fill_(float("nan"))
+        mh.mhdc_batch_spmv_graph(B, XP, YP)
+        t.cuda.synchronize()
+        for y, d in zip(ys, direct):
+            assert t.equal(y, d)
+    # new x contents, same pointer arrays: the graph reads them at run time
+    for x in xd:
+        x.mul_(2)
+    mh.mhdc_batch_spmv_graph(B, XP, YP)
+    t.cuda.synchronize()
+    for y, d in zip(ys, direct):
+        assert t.allclose(y.double(), 2 * d.double(), rtol=1e-6 if dt != "f64" else 1e-15, atol=0)
+    # one handle at a time gives the same bits
+    for h, x, y in zip(hs, xd, ys):
+        yy = y_empty(h.n, dt)
+        mh.mhdc_set_variant(h, 5)
+        mh.mhdc_spmv(h, x, yy)
+        if h.info["n_b"] % {"f64": 2, "f32": 4, "bf16": 8}[dt] == 0:
+            assert t.equal(yy, y)
+    B.destroy()
+
+
+def test_batch_64_stencils_full_size(mh):
+    # 64 seeded 7-/27-point stencils, grid edges uniform in [16, 96], FP64
+    t = torch()
+    mats = synth.batch_matrices(64, 16, 96, seed=3)
+    hs, xd, ys, xs = [], [], [], []
+    for i, A in enumerate(mats):
+        rp, col, val = dev_csr(A)
+        hs.append(mh.mhdc_build(A.n, rp, col, val, 4096, 0.6, "f64"))
+        xs.append(synth.uniform_vector(A.n, 500 + i))
+        xd.append(t.from_numpy(xs[-1]).cuda())
+        ys.append(y_empty(A.n, "f64"))
+    B = mh.mhdc_batch_create(hs)
+    mh.mhdc_batch_spmv_graph(B, mh.pointer_array(xd), mh.pointer_array(ys))
+    t.cuda.synchronize()
+    for A, x, y in zip(mats, xs, ys):
+        ref = oracle.csr_spmv(A, x)
+        assert np.all(np.abs(y.cpu().numpy() - ref) <= oracle.FP64_ROW_TOL * oracle.csr_absrow(A, x))
+    B.destroy()
