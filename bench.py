@@ -280,6 +280,107 @@ def run_reference(args):
         dist.destroy_process_group()
 
 
+def _mean_launch_us(fn, steps, warmup, stream, torch):
+    tot, mean, _ = time_launches(fn, steps, warmup, stream, torch)
+    return mean * 1e3
+
+
+def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
+    """Measurements of the other rows of the hot path beside the headline:
+    reduced precision (scattered 4M-row matrix), SpMM (the 128^3 matrix,
+    FP32, k right-hand sides) and the batched product (64 stencils)."""
+    import oracle
+    import synth
+    out = {}
+    steps = max(10, min(args.steps, 400))
+    # -- reduced precision: FP64 / FP32 / BF16 storage, n_b = 2048, theta = 0.6
+    S = synth.config_matrix("scattered_4m")
+    srp = torch.from_numpy(S.row_ptr).cuda()
+    scol = torch.from_numpy(S.col).cuda()
+    sval = torch.from_numpy(S.val).cuda()
+    x64 = synth.loguniform_vector(S.n, 2)
+    y_ex = oracle.csr_spmv(S, x64)
+    abs_ex = oracle.csr_absrow(S, x64)
+    prec = {"workload": "scattered_4m: 4,194,304 rows, 19 offsets in [-20000, 20000] in 60% of "
+                        "2048-row blocks, Poisson(3) random entries per row, |values| "
+                        "log-uniform in [1e-3, 1e3]; n_b=2048, theta=0.6",
+            "nnz": S.nnz}
+    for dt in ("f64", "f32", "bf16"):
+        Hs = mh.mhdc_build(S.n, srp, scol, sval, 2048, 0.6, dt)
+        inf = Hs.info
+        xs = oracle.store(x64, dt)
+        xd = (torch.from_numpy(xs.view(np.int16)).cuda().view(torch.bfloat16) if dt == "bf16"
+              else torch.from_numpy(xs).cuda())
+        yd = torch.empty(S.n, dtype=torch.float64 if dt == "f64" else torch.float32, device="cuda")
+        best, _ = mh.mhdc_tune(Hs, xd, yd)
+        us = _mean_launch_us(lambda: mh.mhdc_spmv(Hs, xd, yd, stream), steps, 5, stream, torch)
+        mh.mhdc_spmv(Hs, xd, yd, stream)
+        torch.cuda.synchronize()
+        err = np.abs(yd.double().cpu().numpy() - y_ex)
+        terms = np.diff(S.row_ptr).astype(np.float64) + 19
+        bnd = oracle.bound_vs_exact(abs_ex, terms, dt)
+        prec[dt] = {"kernel_us": round(us, 2), "gflops": round(gflops(S.nnz, us / 1e6), 1),
+                    "gbs": round(inf["bytes_model"] / us / 1e3, 1), "bytes": inf["bytes_model"],
+                    "variant": best, "P": inf["P"], "beta": round(inf["beta"], 4),
+                    "max_rel_err": float(np.max(err / np.maximum(abs_ex, 1e-300))),
+                    "max_err_over_bound": float(np.max(err / np.maximum(bnd, 1e-300)))}
+        Hs.destroy()
+        del xd, yd
+    us = _mean_launch_us(lambda: mh.csr_spmv(S.n, srp, scol, sval, torch.from_numpy(x64).cuda(),
+                                             torch.empty(S.n, dtype=torch.float64, device="cuda"),
+                                             stream), 20, 3, stream, torch)
+    prec["csr_fp64"] = {"step_us": round(us, 2), "gflops": round(gflops(S.nnz, us / 1e6), 1)}
+    out["a7_reduced_precision"] = prec
+    log(f"reduced precision: {json.dumps(prec)[:300]}")
+    del srp, scol, sval
+    # -- SpMM on the headline matrix in FP32
+    H32 = mh.mhdc_build(A.n, rp, col, val, 4096, 0.6, "f32")
+    mm = {"workload": "stencil27_128, FP32 values and X, Y row-major n x k"}
+    for k in (1, 4, 8, 16):
+        X = torch.rand((A.n, k), dtype=torch.float32, device="cuda")
+        Y = torch.empty((A.n, k), dtype=torch.float32, device="cuda")
+        us = _mean_launch_us(lambda: mh.mhdc_spmm(H32, X, Y, stream), min(steps, 200), 3,
+                             stream, torch)
+        bytes_ = H32.info["bytes_model"] + (k - 1) * A.n * 8
+        mm[f"k{k}"] = {"kernel_us": round(us, 2), "gflops": round(gflops(A.nnz * k, us / 1e6), 1),
+                       "gbs": round(bytes_ / us / 1e3, 1)}
+        del X, Y
+    H32.destroy()
+    out["a8_spmm_fp32"] = mm
+    log(f"spmm: {json.dumps(mm)}")
+    # -- batched: 64 stencils, edges in [16, 96], FP64
+    mats = synth.batch_matrices(64, 16, 96, seed=3)
+    hs, xs, ys = [], [], []
+    for i, Am in enumerate(mats):
+        r_, c_, v_ = (torch.from_numpy(Am.row_ptr).cuda(), torch.from_numpy(Am.col).cuda(),
+                      torch.from_numpy(Am.val).cuda())
+        hs.append(mh.mhdc_build(Am.n, r_, c_, v_, 4096, 0.6, "f64"))
+        mh.mhdc_set_variant(hs[-1], 5)
+        xs.append(torch.rand(Am.n, dtype=torch.float64, device="cuda"))
+        ys.append(torch.empty(Am.n, dtype=torch.float64, device="cuda"))
+    B = mh.mhdc_batch_create(hs)
+    XP, YP = mh.pointer_array(xs), mh.pointer_array(ys)
+    nnz_b = sum(Am.nnz for Am in mats)
+
+    def separate():
+        for h, x, y in zip(hs, xs, ys):
+            mh.mhdc_spmv(h, x, y, stream)
+    bt = {"workload": "64 seeded 7-/27-point stencils, grid edges uniform in [16, 96], FP64, "
+                      "n_b=4096, theta=0.6", "matrices": 64, "rows": sum(Am.n for Am in mats),
+          "nnz": nnz_b}
+    for nm_, fn in (("separate_launches", separate),
+                    ("persistent_launch", lambda: mh.mhdc_batch_spmv(B, XP, YP, stream)),
+                    ("graph_replay", lambda: mh.mhdc_batch_spmv_graph(B, XP, YP, stream))):
+        tot, mean, _ = time_launches(fn, 30, 3, stream, torch)
+        bt[nm_] = {"us": round(mean * 1e3, 1), "gflops": round(gflops(nnz_b, mean / 1e3), 1)}
+    B.destroy()
+    for h in hs:
+        h.destroy()
+    out["a9_batched_fp64"] = bt
+    log(f"batched: {json.dumps(bt)}")
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -446,6 +547,10 @@ def main():
             fr[nm_] = round(2.0 * ctas * 256 * 8 * iters / (mean / 1e3) / 1e12, 4)
         extra["fma_measured"] = fr
 
+    rows = {}
+    if not args.skip_extra and ws == 1:
+        rows = measure_rows(mh, torch, stream, args, H, A, rp, col, val, log)
+
     # ---- end to end through the host-buffer entry point (pinned memory)
     xh = torch.from_numpy(x_host).pin_memory()
     yh = torch.empty(A.n, dtype=torch.float64).pin_memory()
@@ -505,6 +610,7 @@ def main():
             "clocks": clocks,
             "build_ms": round(build_ms, 1),
             "baselines": extra,
+            "rows": rows,
         }
         print(json.dumps(line), flush=True)
     H.destroy()
