@@ -230,6 +230,82 @@ int mhdc_batch_spmv_graph(mhdc_batch_handle B, const void *const *d_xs, void *co
                           void *stream);
 int mhdc_batch_destroy(mhdc_batch_handle B);
 
+/*
+ * Parameter selection (an extension of Sec. 6.4.3 and Sec. 7: the
+ * paper fixes theta = 0.6 and a swept block width, and leaves the choice of
+ * format as future work).  A candidate is (n_b, theta, dtype) from a fixed
+ * grid of MHDC_NUM_CANDIDATES: dtype in {F64, F32, BF16} (index / 15),
+ * n_b in {512, 1024, 2048, 4096, 8192} ((index % 15) / 3), theta in
+ * {0.5, 0.7, 0.9} (index % 3).
+ *
+ * mhdc_candidate   -- candidate idx as an mhdc_params.
+ * mhdc_features    -- MHDC_NUM_FEATURES floats to host h_features: for block
+ *                     sizes 256, 1024, 4096, the fraction of stored entries
+ *                     on partial diagonals whose filling rate N(d,ib)/rows(ib)
+ *                     falls in each of 10 bins, then log1p(diagonals per
+ *                     block in each bin) / 8; then log2(1 + nnz/n) / 6,
+ *                     log2(n) / 24, log2(1 + nnz) / 32 and 1.  Computed on the
+ *                     device from a valid CSR (see mhdc_build).  Synchronous.
+ * mhdc_autotune    -- the exhaustive autotuner: builds every candidate and
+ *                     times `reps` products of each (default tile shape);
+ *                     h_times_us[MHDC_NUM_CANDIDATES] receives the mean time
+ *                     in microseconds, or -1 for a candidate that could not
+ *                     be built for lack of memory.  Synchronous.
+ * mhdc_select      -- choose parameters for a CSR matrix and a tolerance tol
+ *                     on the per-row error relative to sum_j |a_ij||x_j|: a
+ *                     dtype is allowed if its worst-case bound for rows of
+ *                     nnz/n terms is <= tol (F64 always).  flags:
+ *                     MHDC_SELECT_PAPER (0): theta 0.6, n_b 4096, cheapest
+ *                       allowed dtype (the paper's fixed policy);
+ *                     MHDC_SELECT_MLP: the candidate the MLP `mlp` predicts
+ *                       fastest (mlp maps MHDC_NUM_FEATURES to
+ *                       MHDC_NUM_CANDIDATES predicted log relative times);
+ *                     MHDC_SELECT_AUTOTUNE: the fastest measured candidate;
+ *                     MHDC_SELECT_MODEL: the fewest bytes by the paper's
+ *                       model (Sec. 5.3.3) evaluated on the features.
+ *                     Synchronous.
+ *
+ * The MLP (no counterpart in the paper): n_in -> n_hidden -> n_hidden ->
+ * n_out, ReLU after the hidden layers, FP32 parameters W1 [h x in], b1 [h],
+ * W2 [h x h], b2 [h], W3 [out x h], b3 [out] (contiguous in that order),
+ * He-uniform initialisation from `seed`.  Batches are row-major device
+ * arrays: X [batch x n_in], Y / T / M [batch x n_out].  The loss is the
+ * masked mean squared error sum M (Y - T)^2 / sum M; mhdc_mlp_grad returns
+ * its gradient (host array of mhdc_mlp_num_params floats) and value;
+ * mhdc_mlp_train_step applies one Adam step (b1 0.9, b2 0.999, eps 1e-8).
+ */
+#define MHDC_NUM_FEATURES 64
+#define MHDC_NUM_CANDIDATES 45
+enum { MHDC_SELECT_PAPER = 0, MHDC_SELECT_MLP = 1, MHDC_SELECT_AUTOTUNE = 2, MHDC_SELECT_MODEL = 4 };
+typedef struct {
+    int32_t n_b;
+    int32_t dtype;
+    double theta;
+    int32_t variant;
+    int32_t reserved;
+} mhdc_params;
+typedef struct mhdc_mlp *mhdc_mlp_handle;
+
+int mhdc_num_candidates(void);
+int mhdc_candidate(int32_t idx, mhdc_params *out);
+int mhdc_features(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, void *stream,
+                  float *h_features);
+int mhdc_autotune(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+                  int32_t reps, void *stream, float *h_times_us);
+int mhdc_select(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+                double tol, int32_t flags, mhdc_mlp_handle mlp, void *stream, mhdc_params *out);
+int mhdc_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed,
+                    mhdc_mlp_handle *out);
+int64_t mhdc_mlp_num_params(mhdc_mlp_handle M);
+int mhdc_mlp_get_params(mhdc_mlp_handle M, float *h_params);
+int mhdc_mlp_set_params(mhdc_mlp_handle M, const float *h_params);
+int mhdc_mlp_forward(mhdc_mlp_handle M, int32_t batch, const float *d_X, float *d_Y, void *stream);
+int mhdc_mlp_grad(mhdc_mlp_handle M, int32_t batch, const float *d_X, const float *d_T,
+                  const float *d_M, float *h_grads, float *h_loss, void *stream);
+int mhdc_mlp_train_step(mhdc_mlp_handle M, int32_t batch, const float *d_X, const float *d_T,
+                        const float *d_M, float lr, void *stream, float *h_loss);
+int mhdc_mlp_destroy(mhdc_mlp_handle M);
+
 /* mhdc_destroy -- free the handle and its device arrays (NULL is a no-op). */
 int mhdc_destroy(mhdc_handle A);
 

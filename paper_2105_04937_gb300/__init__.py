@@ -26,7 +26,12 @@ __all__ = [
     "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "mhdc_check",
     "mhdc_read_bench", "mhdc_read_bench_ctas", "mhdc_build_noalloc",
     "mhdc_fma_bench", "Batch", "mhdc_batch_create", "mhdc_batch_spmv", "mhdc_batch_spmv_graph",
-    "mhdc_batch_destroy", "pointer_array",
+    "mhdc_batch_destroy", "pointer_array", "MHDC_NUM_FEATURES", "MHDC_NUM_CANDIDATES",
+    "MHDC_SELECT_PAPER", "MHDC_SELECT_MLP", "MHDC_SELECT_AUTOTUNE", "MHDC_SELECT_MODEL",
+    "mhdc_candidate", "mhdc_features", "mhdc_autotune", "mhdc_select", "Mlp",
+    "mhdc_mlp_create", "mhdc_mlp_forward", "mhdc_mlp_grad", "mhdc_mlp_train_step",
+    "mhdc_mlp_get_params", "mhdc_mlp_set_params", "mhdc_mlp_destroy", "mhdc_num_candidates",
+    "mhdc_mlp_num_params",
 ]
 
 MHDC_F64, MHDC_F32, MHDC_BF16 = 0, 1, 2
@@ -75,12 +80,28 @@ _SIGS = {
     "mhdc_batch_spmv": [_P, _P, _P, _P],
     "mhdc_batch_spmv_graph": [_P, _P, _P, _P],
     "mhdc_batch_destroy": [_P],
+    "mhdc_num_candidates": [],
+    "mhdc_candidate": [_I32, _P],
+    "mhdc_features": [_I64, _P, _P, _P, _P],
+    "mhdc_autotune": [_I64, _P, _P, _P, _I32, _P, _P],
+    "mhdc_select": [_I64, _P, _P, _P, _D, _I32, _P, _P, _P],
+    "mhdc_mlp_create": [_I32, _I32, _I32, C.c_uint64, C.POINTER(C.c_void_p)],
+    "mhdc_mlp_num_params": [_P],
+    "mhdc_mlp_get_params": [_P, _P],
+    "mhdc_mlp_set_params": [_P, _P],
+    "mhdc_mlp_forward": [_P, _I32, _P, _P, _P],
+    "mhdc_mlp_grad": [_P, _I32, _P, _P, _P, _P, _P, _P],
+    "mhdc_mlp_train_step": [_P, _I32, _P, _P, _P, C.c_float, _P, _P],
+    "mhdc_mlp_destroy": [_P],
     "mhdc_build_noalloc": [_I64, _P, _P, _P, _I32, _D, _I32, _P, _P, _P, _I64, _P, _P, _P, _I64,
                            C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P],
     "mhdc_tune": [_P, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
 }
 
 MHDC_NUM_VARIANTS = 16
+MHDC_NUM_FEATURES = 64
+MHDC_NUM_CANDIDATES = 45
+MHDC_SELECT_PAPER, MHDC_SELECT_MLP, MHDC_SELECT_AUTOTUNE, MHDC_SELECT_MODEL = 0, 1, 2, 4
 FIRST_EMULATED_VARIANT = 10
 
 
@@ -99,7 +120,8 @@ def lib(build_if_missing: bool = False):
             for name, args in _SIGS.items():
                 f = getattr(L, name)
                 f.argtypes = args
-                f.restype = C.c_char_p if name in ("mhdc_strerror", "mhdc_last_error") else C.c_int
+                f.restype = (C.c_char_p if name in ("mhdc_strerror", "mhdc_last_error") else
+                             C.c_int64 if name == "mhdc_mlp_num_params" else C.c_int)
             _lib = L
     return _lib
 
@@ -433,3 +455,148 @@ def mhdc_batch_spmv_graph(B: Batch, xs, ys, stream=None):
 
 def mhdc_batch_destroy(B: Batch):
     B.destroy()
+
+
+class _Params(C.Structure):
+    _fields_ = [("n_b", C.c_int32), ("dtype", C.c_int32), ("theta", C.c_double),
+                ("variant", C.c_int32), ("reserved", C.c_int32)]
+
+
+_DT_NAME = {MHDC_F64: "f64", MHDC_F32: "f32", MHDC_BF16: "bf16"}
+
+
+def _params_dict(p: _Params) -> dict:
+    return {"n_b": p.n_b, "theta": p.theta, "dtype": _DT_NAME[p.dtype], "variant": p.variant}
+
+
+def mhdc_num_candidates() -> int:
+    return int(lib().mhdc_num_candidates())
+
+
+def mhdc_candidate(idx: int) -> dict:
+    p = _Params()
+    _check(lib().mhdc_candidate(int(idx), C.byref(p)), "mhdc_candidate")
+    return _params_dict(p)
+
+
+def mhdc_features(n, row_ptr, col, stream=None) -> np.ndarray:
+    """The selector's feature vector (MHDC_NUM_FEATURES floats) of a CSR matrix."""
+    import torch
+    _check_dev(row_ptr, torch.int32, n + 1, "row_ptr")
+    f = np.zeros(MHDC_NUM_FEATURES, dtype=np.float32)
+    _check(lib().mhdc_features(n, _ptr(row_ptr), _ptr(col), _stream(stream),
+                               f.ctypes.data_as(C.c_void_p)), "mhdc_features")
+    return f
+
+
+def mhdc_autotune(n, row_ptr, col, val, reps=10, stream=None) -> np.ndarray:
+    """Mean time (us) of every candidate, -1 where it could not be built."""
+    import torch
+    _check_dev(row_ptr, torch.int32, n + 1, "row_ptr")
+    t = np.zeros(MHDC_NUM_CANDIDATES, dtype=np.float32)
+    _check(lib().mhdc_autotune(n, _ptr(row_ptr), _ptr(col), _ptr(val), int(reps), _stream(stream),
+                               t.ctypes.data_as(C.c_void_p)), "mhdc_autotune")
+    return t
+
+
+def mhdc_select(n, row_ptr, col, val, tol, flags=MHDC_SELECT_PAPER, mlp=None, stream=None) -> dict:
+    import torch
+    _check_dev(row_ptr, torch.int32, n + 1, "row_ptr")
+    p = _Params()
+    _check(lib().mhdc_select(n, _ptr(row_ptr), _ptr(col), _ptr(val), float(tol), int(flags),
+                             C.c_void_p(mlp.handle if mlp is not None else 0), _stream(stream),
+                             C.byref(p)), "mhdc_select")
+    return _params_dict(p)
+
+
+class Mlp:
+    """Owner of an mhdc_mlp_handle (the selector network)."""
+
+    def __init__(self, handle: int, n_in: int, n_hidden: int, n_out: int):
+        self.handle, self.n_in, self.n_hidden, self.n_out = handle, n_in, n_hidden, n_out
+
+    @property
+    def num_params(self) -> int:
+        return mhdc_mlp_num_params(self)
+
+    def destroy(self):
+        if self.handle:
+            lib().mhdc_mlp_destroy(C.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def mhdc_mlp_create(n_in, n_hidden, n_out, seed=0) -> Mlp:
+    h = C.c_void_p()
+    _check(lib().mhdc_mlp_create(int(n_in), int(n_hidden), int(n_out), int(seed), C.byref(h)),
+           "mhdc_mlp_create")
+    return Mlp(h.value, n_in, n_hidden, n_out)
+
+
+def mhdc_mlp_num_params(M: Mlp) -> int:
+    return int(lib().mhdc_mlp_num_params(C.c_void_p(M.handle)))
+
+
+def mhdc_mlp_get_params(M: Mlp) -> np.ndarray:
+    p = np.zeros(M.num_params, dtype=np.float32)
+    _check(lib().mhdc_mlp_get_params(C.c_void_p(M.handle), p.ctypes.data_as(C.c_void_p)),
+           "mhdc_mlp_get_params")
+    return p
+
+
+def mhdc_mlp_set_params(M: Mlp, p):
+    p = np.ascontiguousarray(p, dtype=np.float32)
+    if p.size != M.num_params:
+        raise ValueError("wrong parameter count")
+    _check(lib().mhdc_mlp_set_params(C.c_void_p(M.handle), p.ctypes.data_as(C.c_void_p)),
+           "mhdc_mlp_set_params")
+
+
+def _mlp_batch(M, X, T=None, Mask=None):
+    import torch
+    _check_dev(X, torch.float32, None, "X")
+    B = X.shape[0]
+    if X.dim() != 2 or X.shape[1] != M.n_in:
+        raise ValueError("X must be batch x n_in")
+    for t, nm in ((T, "T"), (Mask, "M")):
+        if t is not None:
+            _check_dev(t, torch.float32, B * M.n_out, nm)
+    return B
+
+
+def mhdc_mlp_forward(M: Mlp, X, stream=None):
+    import torch
+    B = _mlp_batch(M, X)
+    Y = torch.empty((B, M.n_out), dtype=torch.float32, device=X.device)
+    _check(lib().mhdc_mlp_forward(C.c_void_p(M.handle), B, _ptr(X), _ptr(Y), _stream(stream)),
+           "mhdc_mlp_forward")
+    return Y
+
+
+def mhdc_mlp_grad(M: Mlp, X, T, Mask, stream=None):
+    """(gradient of the masked MSE as a float32 numpy array, loss)."""
+    B = _mlp_batch(M, X, T, Mask)
+    g = np.zeros(M.num_params, dtype=np.float32)
+    loss = C.c_float(0)
+    _check(lib().mhdc_mlp_grad(C.c_void_p(M.handle), B, _ptr(X), _ptr(T), _ptr(Mask),
+                               g.ctypes.data_as(C.c_void_p), C.byref(loss), _stream(stream)),
+           "mhdc_mlp_grad")
+    return g, float(loss.value)
+
+
+def mhdc_mlp_train_step(M: Mlp, X, T, Mask, lr, stream=None, want_loss=True):
+    B = _mlp_batch(M, X, T, Mask)
+    loss = C.c_float(0)
+    _check(lib().mhdc_mlp_train_step(C.c_void_p(M.handle), B, _ptr(X), _ptr(T), _ptr(Mask),
+                                     float(lr), _stream(stream),
+                                     C.byref(loss) if want_loss else None), "mhdc_mlp_train_step")
+    return float(loss.value) if want_loss else None
+
+
+def mhdc_mlp_destroy(M: Mlp):
+    M.destroy()

@@ -225,6 +225,66 @@ k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
     }
 }
 
+// Selector features: for one block size, histogram the partial diagonals by
+// filling rate f = N(d, ib) / rows(ib) in 10 bins ([0, 0.1), ..., [0.9, 1]):
+// ent[bin] += N (stored entries) and dia[bin] += 1.  A block whose distinct
+// offsets overflow the shared table counts the entries it could not insert
+// as single-entry diagonals (bin 0): such offsets are almost all singletons.
+__global__ void __launch_bounds__(CS_THREADS)
+k_count_hist(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
+             const int32_t *__restrict__ col, unsigned long long *ent, unsigned long long *dia)
+{
+    extern __shared__ int32_t smem[];
+    __shared__ int used;
+    __shared__ unsigned long long lost;
+    __shared__ unsigned long long h_ent[10], h_dia[10];
+    const int64_t ib = blockIdx.x;
+    const int64_t r0 = ib * (int64_t)n_b;
+    const int64_t rows = (n - r0 < n_b) ? (n - r0) : n_b;
+    const int64_t m = (int64_t)rp[r0 + rows] - rp[r0];
+    int64_t cap = 64;
+    while (cap < 2 * m && cap < HCAP) cap <<= 1;
+    const int limit = cap == HCAP ? HLIMIT : (int)cap - 1;
+    int32_t *keys = smem, *cnt = smem + HCAP;
+    const uint32_t mask = (uint32_t)(cap - 1);
+    for (int64_t s = threadIdx.x; s < cap; s += blockDim.x) {
+        keys[s] = EMPTY_KEY;
+        cnt[s] = 0;
+    }
+    if (threadIdx.x < 10) h_ent[threadIdx.x] = h_dia[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        used = 0;
+        lost = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t i = r0 + warp; i < r0 + rows; i += CS_WARPS) {
+        const int32_t a = rp[i], b = rp[i + 1];
+        for (int32_t k = a + lane; k < b; k += 32)
+            if (!table_insert(keys, cnt, mask, col[k] - (int32_t)i, &used, limit))
+                atomicAdd(&lost, 1ull);
+    }
+    __syncthreads();
+    for (int64_t s = threadIdx.x; s < cap; s += blockDim.x) {
+        if (((volatile int32_t *)keys)[s] == EMPTY_KEY) continue;
+        const int32_t c = ((volatile int32_t *)cnt)[s];
+        int bin = (int)(10.0 * (double)c / (double)rows);
+        bin = bin > 9 ? 9 : bin;
+        atomicAdd(&h_ent[bin], (unsigned long long)c);
+        atomicAdd(&h_dia[bin], 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        unsigned long long e = h_ent[threadIdx.x], d = h_dia[threadIdx.x];
+        if (threadIdx.x == 0) {
+            e += lost;
+            d += lost;
+        }
+        if (e) atomicAdd(&ent[threadIdx.x], e);
+        if (d) atomicAdd(&dia[threadIdx.x], d);
+    }
+}
+
 // HDC: N(d) for d in [-(n-1), n-1] at cnt[d + n - 1].
 __global__ void k_count_all(int64_t n, const int32_t *__restrict__ rp,
                             const int32_t *__restrict__ col, int32_t *cnt)
@@ -577,6 +637,28 @@ int finish_stats(mhdc_matrix *A, cudaStream_t st)
 }
 
 }  // namespace
+
+int feature_hist(int64_t n, const int32_t *rp, const int32_t *col, int32_t n_b,
+                 cudaStream_t st, unsigned long long *h_ent, unsigned long long *h_dia)
+{
+    const int64_t nb = (n + n_b - 1) / n_b;
+    Buf d;
+    RC(dalloc(d, 20 * sizeof(unsigned long long)));
+    MHDC_CUDA_TRY(cudaMemsetAsync(d.p, 0, 20 * sizeof(unsigned long long), st));
+    if (nb > 0) {
+        MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(2 * HCAP * sizeof(int32_t))));
+        k_count_hist<<<(unsigned)nb, CS_THREADS, 2 * HCAP * sizeof(int32_t), st>>>(
+            n, n_b, rp, col, d.as<unsigned long long>(), d.as<unsigned long long>() + 10);
+        MHDC_LAUNCH_CHECK("k_count_hist");
+    }
+    unsigned long long h[20];
+    MHDC_CUDA_TRY(cudaMemcpyAsync(h, d.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    memcpy(h_ent, h, 10 * sizeof(unsigned long long));
+    memcpy(h_dia, h + 10, 10 * sizeof(unsigned long long));
+    return MHDC_OK;
+}
 
 void free_matrix(mhdc_matrix *A)
 {

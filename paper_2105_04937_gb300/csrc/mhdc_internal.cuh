@@ -85,6 +85,8 @@ int build_matrix(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, cons
                  int32_t n_b, double theta, int32_t dtype, int mode, cudaStream_t stream,
                  mhdc_matrix **out);
 void free_matrix(mhdc_matrix *A);
+int feature_hist(int64_t n, const int32_t *rp, const int32_t *col, int32_t n_b,
+                 cudaStream_t st, unsigned long long *h_ent, unsigned long long *h_dia);
 int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int32_t n_b,
                   double theta, int32_t dtype, int32_t *dia_ptr, int32_t *dia_offset, void *dia_val,
                   int64_t cap_P, int32_t *csr_row_ptr, int32_t *csr_col, void *csr_val,

@@ -1,0 +1,130 @@
+"""GPU tests of the parameter selector: features, the MLP kernels against the
+FP64 numpy oracle (forward, gradient, Adam), the autotuner and mhdc_select."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import check_build, dev_csr, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mh():
+    t = torch()
+    assert t.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2105_04937_gb300 as m
+    m.lib()
+    return m
+
+
+def reference_features(A):
+    """The feature vector re-derived on the host with numpy (no table overflow)."""
+    rows = A.rows()
+    off = A.col.astype(np.int64) - rows
+    f = []
+    for n_b in (256, 1024, 4096):
+        ib = rows // n_b
+        nblocks = -(-A.n // n_b)
+        key = ib * (4 * A.n) + (off + 2 * A.n)
+        uk, cnt = np.unique(key, return_counts=True)
+        blk = uk // (4 * A.n)
+        nrows = np.minimum(n_b, A.n - blk * n_b)
+        bins = np.minimum(9, (10.0 * cnt / nrows).astype(np.int64))
+        ent = np.bincount(bins, weights=cnt, minlength=10) / A.nnz
+        dia = np.bincount(bins, minlength=10)
+        f += list(ent) + list(np.log1p(dia / nblocks) / 8.0)
+    c = A.nnz / A.n
+    f += [np.log2(1 + c) / 6, np.log2(A.n) / 24, np.log2(1 + A.nnz) / 32, 1.0]
+    return np.array(f, dtype=np.float32)
+
+
+def test_features_match_host_derivation(mh):
+    for A in (synth.config_matrix("stencil7_32"), synth.config_matrix("stencil27_128", scale=0.25),
+              synth.random_sparse(700, 0.01, seed=3, diag_bias=0.6),
+              synth.stencil_3d(20, 17, 13, 13, seed=5, drop_rate=0.4, drop_block=256,
+                               offband_poisson=1.0)):
+        rp, col, _ = dev_csr(A)
+        f = mh.mhdc_features(A.n, rp, col)
+        ref = reference_features(A)
+        assert f.shape == (mh.MHDC_NUM_FEATURES,)
+        assert np.allclose(f, ref, rtol=1e-6, atol=1e-7), np.nonzero(~np.isclose(f, ref))
+    # the 7-point 32^3 stencil at 1024-row blocks: every diagonal at least 31/32 full
+    A = synth.config_matrix("stencil7_32")
+    f = mh.mhdc_features(A.n, *dev_csr(A)[:2])
+    assert abs(f[20 + 9] - 1.0) < 1e-6
+
+
+def _mlp_case(seed, F, H, O, B):
+    rng = synth.Rng(seed, 3)
+    X = rng.uniform(B * F, -1, 1).reshape(B, F).astype(np.float32)
+    T = rng.uniform(B * O, -1, 1).reshape(B, O).astype(np.float32)
+    M = (rng.unit(B * O) < 0.8).astype(np.float32).reshape(B, O)
+    return X, T, M
+
+
+@pytest.mark.parametrize("F,H,O,B", [(5, 7, 4, 3), (64, 128, 45, 256), (64, 96, 45, 1)])
+def test_mlp_kernels_match_oracle(mh, F, H, O, B):
+    from oracle import mlp as omlp
+    t = torch()
+    M_ = mh.mhdc_mlp_create(F, H, O, seed=11)
+    p = mh.mhdc_mlp_get_params(M_).astype(np.float64)
+    X, T, Mk = _mlp_case(1, F, H, O, B)
+    Xd, Td, Md = (t.from_numpy(a).cuda() for a in (X, T, Mk))
+    Y = mh.mhdc_mlp_forward(M_, Xd).cpu().numpy()
+    Yref, _ = omlp.forward(p, F, H, O, X)
+    assert np.allclose(Y, Yref, rtol=1e-5, atol=1e-5 * np.abs(Yref).max())
+    g, loss = mh.mhdc_mlp_grad(M_, Xd, Td, Md)
+    gref = omlp.gradient(p, F, H, O, X, T, Mk)
+    assert abs(loss - omlp.loss(p, F, H, O, X, T, Mk)) <= 1e-5 * max(1.0, loss)
+    assert np.max(np.abs(g - gref)) <= 1e-5 * np.max(np.abs(gref)) + 1e-7
+    # one Adam step
+    lr = 1e-3
+    mh.mhdc_mlp_train_step(M_, Xd, Td, Md, lr)
+    p1 = mh.mhdc_mlp_get_params(M_).astype(np.float64)
+    p1ref, _, _ = omlp.adam_step(p, gref, np.zeros_like(p), np.zeros_like(p), 1, lr)
+    assert np.max(np.abs(p1 - p1ref)) <= 1e-6 + 1e-4 * lr
+    M_.destroy()
+
+
+def test_mlp_training_reduces_loss(mh):
+    t = torch()
+    F, H, O, B = 16, 32, 6, 128
+    rng = synth.Rng(5, 1)
+    X = rng.uniform(B * F, -1, 1).reshape(B, F).astype(np.float32)
+    Wt = rng.uniform(O * F, -1, 1).reshape(O, F)
+    T = np.tanh(X @ Wt.T).astype(np.float32)
+    Mk = np.ones((B, O), dtype=np.float32)
+    M_ = mh.mhdc_mlp_create(F, H, O, seed=2)
+    Xd, Td, Md = (t.from_numpy(a).cuda() for a in (X, T, Mk))
+    first = mh.mhdc_mlp_train_step(M_, Xd, Td, Md, 3e-3)
+    for _ in range(400):
+        last = mh.mhdc_mlp_train_step(M_, Xd, Td, Md, 3e-3, want_loss=False)
+    last = mh.mhdc_mlp_train_step(M_, Xd, Td, Md, 3e-3)
+    assert last < 0.1 * first
+
+
+def test_autotune_and_select(mh):
+    A = synth.stencil_3d(24, 24, 24, 27, seed=9, drop_rate=0.3, drop_block=1024,
+                         offband_poisson=0.5)
+    rp, col, val = dev_csr(A)
+    times = mh.mhdc_autotune(A.n, rp, col, val, reps=5)
+    assert times.shape == (45,) and np.all(times > 0)
+    cands = [mh.mhdc_candidate(k) for k in range(45)]
+    assert {c["dtype"] for c in cands} == {"f64", "f32", "bf16"}
+    # FP64 only (tight tolerance): the autotuner's choice is the fastest FP64 candidate
+    got = mh.mhdc_select(A.n, rp, col, val, 1e-12, mh.MHDC_SELECT_AUTOTUNE)
+    assert got["dtype"] == "f64"
+    assert got["n_b"] in (512, 1024, 2048, 4096, 8192) and got["theta"] in (0.5, 0.7, 0.9)
+    # loose tolerance admits BF16 in the paper policy
+    assert mh.mhdc_select(A.n, rp, col, val, 1e-1)["dtype"] == "bf16"
+    assert mh.mhdc_select(A.n, rp, col, val, 1e-12) == {"n_b": 4096, "theta": 0.6,
+                                                         "dtype": "f64", "variant": -1}
+    m = mh.mhdc_select(A.n, rp, col, val, 1e-5, mh.MHDC_SELECT_MODEL)
+    assert m["dtype"] in ("f64", "f32")
+    net = mh.mhdc_mlp_create(mh.MHDC_NUM_FEATURES, 32, mh.MHDC_NUM_CANDIDATES, seed=1)
+    s = mh.mhdc_select(A.n, rp, col, val, 1e-3, mh.MHDC_SELECT_MLP, mlp=net)
+    assert s["dtype"] in ("f64", "f32")
+    bad = mh.mhdc_mlp_create(3, 4, 5)
+    with pytest.raises(mh.MhdcError):
+        mh.mhdc_select(A.n, rp, col, val, 1e-3, mh.MHDC_SELECT_MLP, mlp=bad)

@@ -388,3 +388,35 @@ def test_spmv_reads_no_x_outside_the_vector():
     for bl, theta in ((1024, 0.6), (100, 0.3), (4096, 0.6)):
         M = oracle.convert(A, bl, theta)
         assert np.all(np.isfinite(oracle.mhdc_spmv(M, x)))
+
+
+# ---------------------------------------------------------------- selector network
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    from oracle import mlp
+    F, H, O = 5, 7, 4
+    rng = synth.Rng(21, 1)
+    P = H * F + H + H * H + H + O * H + O
+    p = rng.uniform(P, -0.6, 0.6)
+    X = rng.uniform(6 * F, -1, 1).reshape(6, F)
+    T = rng.uniform(6 * O, -1, 1).reshape(6, O)
+    M = (rng.unit(6 * O) < 0.7).astype(float).reshape(6, O)
+    g = mlp.gradient(p, F, H, O, X, T, M)
+    fd = mlp.fd_gradient(p, F, H, O, X, T, M)
+    for k, v in fd.items():
+        assert abs(g[k] - v) <= 1e-6 * max(1.0, abs(v)), k
+
+
+def test_mlp_oracle_closed_form_linear_case():
+    # with ReLU units all active and a single output, the loss of a one-sample
+    # batch is (w3 . relu(W2 relu(W1 x + b1) + b2) + b3 - t)^2
+    from oracle import mlp
+    F, H, O = 2, 2, 1
+    W1 = np.array([[1.0, 0.0], [0.0, 2.0]]); b1 = np.array([0.5, 0.5])
+    W2 = np.eye(2); b2 = np.zeros(2)
+    W3 = np.array([[1.0, -1.0]]); b3 = np.array([0.25])
+    p = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3])
+    x = np.array([[1.0, 1.0]])
+    Y, _ = mlp.forward(p, F, H, O, x)
+    assert Y[0, 0] == 1.5 - 2.5 + 0.25
+    assert mlp.loss(p, F, H, O, x, np.array([[0.0]]), np.ones((1, 1))) == (-0.75) ** 2
