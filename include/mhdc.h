@@ -236,7 +236,7 @@ int mhdc_batch_destroy(mhdc_batch_handle B);
  * format as future work).  A candidate is (n_b, theta, dtype) from a fixed
  * grid of MHDC_NUM_CANDIDATES: dtype in {F64, F32, BF16} (index / 15),
  * n_b in {512, 1024, 2048, 4096, 8192} ((index % 15) / 3), theta in
- * {0.5, 0.7, 0.9} (index % 3).
+ * {0.5, 0.6, 0.8} (index % 3).
  *
  * mhdc_candidate   -- candidate idx as an mhdc_params.
  * mhdc_features    -- MHDC_NUM_FEATURES floats to host h_features: for block

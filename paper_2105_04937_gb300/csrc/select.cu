@@ -19,7 +19,7 @@ namespace {
 
 constexpr int FEAT_NB[3] = {256, 1024, 4096};
 constexpr int CAND_NB[5] = {512, 1024, 2048, 4096, 8192};
-constexpr double CAND_THETA[3] = {0.5, 0.7, 0.9};
+constexpr double CAND_THETA[3] = {0.5, 0.6, 0.8};
 constexpr int CAND_DT[3] = {MHDC_F64, MHDC_F32, MHDC_BF16};
 
 // ---------------------------------------------------------------- MLP kernels
