@@ -82,6 +82,25 @@ __device__ __forceinline__ void load_x(const X *__restrict__ x, int64_t j, bool 
     for (int m = 0; m < V; m++) xv[m] = ldg_elem(x + j + m);
 }
 
+// The 16 bytes starting `sh` bytes (sh < 16, a multiple of the element size)
+// into the 32-byte window (lo, hi): two aligned loads replace V element loads
+// when x[j .. j+V) is not 16-byte aligned.  `sh` is warp-uniform.
+__device__ __forceinline__ uint4 window16(const uint4 &lo, const uint4 &hi, int sh)
+{
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    const int bs = (sh & 3) * 8;
+    uint32_t o[5];
+    switch (sh >> 2) {
+    case 0: o[0] = w[0]; o[1] = w[1]; o[2] = w[2]; o[3] = w[3]; o[4] = w[4]; break;
+    case 1: o[0] = w[1]; o[1] = w[2]; o[2] = w[3]; o[3] = w[4]; o[4] = w[5]; break;
+    case 2: o[0] = w[2]; o[1] = w[3]; o[2] = w[4]; o[3] = w[5]; o[4] = w[6]; break;
+    default: o[0] = w[3]; o[1] = w[4]; o[2] = w[5]; o[3] = w[6]; o[4] = w[7]; break;
+    }
+    if (bs == 0) return make_uint4(o[0], o[1], o[2], o[3]);
+    return make_uint4(__funnelshift_r(o[0], o[1], bs), __funnelshift_r(o[1], o[2], bs),
+                      __funnelshift_r(o[2], o[3], bs), __funnelshift_r(o[3], o[4], bs));
+}
+
 // One warp = one tile of RW = 32 * V * U consecutive rows of one row block.
 // The block's diagonals are taken D at a time: the D * U 16-byte value loads
 // of a group are issued first, then the x loads, then the FMAs, so a warp
@@ -170,9 +189,24 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
 #pragma unroll
         for (int d = 0; d < DD; d++) {
             const int64_t jw = xrow0 + off[d];
+            const int64_t r = ((jw % V) + V) % V;  // warp-uniform misalignment in elements
             // warp-uniform: the whole tile reads x inside [0, n)
             if (full && jw >= 0 && jw + RW <= n) {
-                const bool al = x_al && ((jw % V) == 0);
+                if constexpr (VEC && V * sizeof(X) == 16 && V > 2) {
+                    if (x_al && r != 0 && jw - r + RW + V <= n) {
+                        // two aligned 16-byte loads and a byte shift per vector
+#pragma unroll
+                        for (int u = 0; u < U; u++) {
+                            const X *a = x + (jw - r) + (tl[u] - tw);
+                            const uint4 lo = __ldg(reinterpret_cast<const uint4 *>(a));
+                            const uint4 hi = __ldg(reinterpret_cast<const uint4 *>(a + V));
+                            const uint4 q = window16(lo, hi, (int)(r * sizeof(X)));
+                            memcpy(xv[d][u], &q, 16);
+                        }
+                        continue;
+                    }
+                }
+                const bool al = x_al && r == 0;
 #pragma unroll
                 for (int u = 0; u < U; u++) load_x<X, V>(x, jw + (tl[u] - tw), al, xv[d][u]);
             } else {
