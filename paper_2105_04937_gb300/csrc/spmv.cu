@@ -136,24 +136,32 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
 #pragma unroll
         for (int m = 0; m < V; m++) acc[u][m] = Acc(0);
 
-    // CSR remainder rows of the tile (Fig. 13, first loop)
+    // CSR remainder rows of the tile (Fig. 13, first loop).  Each lane sums
+    // whole rows (row tw + rr for rr = lane, lane + 32, ...), in column order
+    // from zero, and the sums reach their owners through shared memory: the
+    // same operations as summing into acc directly, with one row per lane.
     {
         const int32_t tend = full ? tw + RW : rows;
         const int32_t q0 = csr_row_ptr[r0 + tw], q1 = csr_row_ptr[r0 + tend];
         if (q0 != q1) {
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-#pragma unroll
-                for (int m = 0; m < V; m++) {
-                    const int32_t t = tl[u] + m;
-                    if (t < rows) {
-                        const int64_t i = r0 + t;
-                        const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
-                        for (int32_t k = a; k < b; k++)
-                            acc[u][m] += widen(csr_val[k]) * widen(ldg_elem(x + csr_col[k]));
-                    }
+            __shared__ Acc rsum[SPMV_WARPS][RW];
+            Acc *rs = rsum[threadIdx.x >> 5];
+            for (int rr = lane; rr < RW; rr += 32) {
+                Acc sum = Acc(0);
+                if (tw + rr < rows) {
+                    const int64_t i = r0 + tw + rr;
+                    const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
+                    for (int32_t k = a; k < b; k++)
+                        sum += widen(csr_val[k]) * widen(ldg_elem(x + csr_col[k]));
                 }
+                rs[rr] = sum;
             }
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int m = 0; m < V; m++) acc[u][m] = rs[tl[u] - tw + m];
+            __syncwarp();
         }
     }
 
@@ -674,7 +682,7 @@ Variant pick_variant(int32_t n_b, int id)
         if (n_b >= 32 * 4) return {(const void *)k_mhdc_spmv<VT, 4, 2, false>, 32 * 4};
         return {(const void *)k_mhdc_spmv<VT, 1, 4, false>, 32};
     }
-    if (id < 0) id = (n_b >= 64 * V) ? 2 : 0;
+    if (id < 0) id = 5;  // U = 1, D = 2: the fastest on every measured workload
     return vec_variant<VT>(id);
 }
 
