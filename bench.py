@@ -159,6 +159,16 @@ def profiled_traffic(variant):
     return int(fields["traffic_bytes"])
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest `value` over all ranks of the process group (the step time
+    of the slowest replica); device is where the collective runs (a CUDA
+    device for NCCL, the CPU for gloo)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def gflops(nnz, sec):
     return 2.0 * nnz / sec / 1e9
 
@@ -378,7 +388,50 @@ def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
         h.destroy()
     out["a9_batched_fp64"] = bt
     log(f"batched: {json.dumps(bt)}")
+    out["a10_select"] = measure_selector(mh, torch, A, rp, col, val, log)
     return out
+
+
+def measure_selector(mh, torch, A, rp, col, val, log):
+    """The selector on the headline matrix: the trained MLP's choice, the
+    paper's fixed policy and the paper's model against the exhaustive
+    autotuner (regret = t(choice) / t(best) - 1), for FP64-only and for an
+    FP32-admitting tolerance; plus the held-out evaluation stored with the
+    trained weights."""
+    from paper_2105_04937_gb300 import selector as S
+    res = {}
+    try:
+        net = S.load()
+    except (OSError, ValueError) as e:
+        return {"unavailable": f"no trained selector weights: {e}"}
+    t0 = time.perf_counter()
+    times = mh.mhdc_autotune(A.n, rp, col, val, reps=10)
+    res["autotune_s"] = round(time.perf_counter() - t0, 2)
+    c = A.nnz / A.n
+    for name, tol in (("fp64_only", 1e-12), ("fp32_ok", 1e-5)):
+        ok = S.allowed_mask(tol, c) & (times > 0)
+        best = float(np.min(times[ok]))
+        t1 = time.perf_counter()
+        mlp = mh.mhdc_select(A.n, rp, col, val, tol, mh.MHDC_SELECT_MLP, mlp=net)
+        sel_ms = (time.perf_counter() - t1) * 1e3
+        model = mh.mhdc_select(A.n, rp, col, val, tol, mh.MHDC_SELECT_MODEL)
+        pc = S.paper_choice(tol, c)
+        row = {"best_us": round(best, 2), "best": mh.mhdc_candidate(int(np.argmin(
+            np.where(ok, times, np.inf))))}
+        for nm_, sel in (("mlp", mlp), ("paper_model", model)):
+            k = S._index_of(sel)
+            row[nm_] = {"choice": sel, "us": round(float(times[k]), 2),
+                        "regret": round(float(times[k] / best - 1), 4)}
+        row["mlp"]["select_ms"] = round(sel_ms, 2)
+        row["paper_policy"] = {"choice": mh.mhdc_candidate(pc), "us": round(float(times[pc]), 2),
+                               "regret": round(float(times[pc] / best - 1), 4)}
+        res[name] = row
+    ev = os.path.join(ROOT, "paper_2105_04937_gb300", "selector_eval.json")
+    if os.path.exists(ev):
+        with open(ev) as f:
+            res["held_out"] = json.load(f).get("held_out")
+    log(f"selector: {json.dumps(res)[:400]}")
+    return res
 
 
 def main():
@@ -464,9 +517,7 @@ def main():
     total_ms = ev0.elapsed_time(ev1)
     kern_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, torch.device("cuda", local))
     clocks = sampler.stop() if rank == 0 else None
 
     ms_step = total_ms / args.steps

@@ -126,8 +126,10 @@ def _index_of(sel: dict) -> int:
 
 
 def load_records(path):
+    import gzip
     recs = []
-    with open(path) as f:
+    opener = gzip.open if path.endswith(".gz") else open
+    with opener(path, "rt") as f:
         for line in f:
             try:
                 recs.append(json.loads(line))

@@ -80,3 +80,15 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(m, "SO", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="not built"):
         m.lib()
+
+
+def test_selector_weight_file_is_intact():
+    import hashlib
+    import struct
+    path = os.path.join(ROOT, "paper_2105_04937_gb300", "selector_weights.bin")
+    data = open(path, "rb").read()
+    assert data[:8] == b"MHDCMLP1"
+    assert hashlib.sha256(data[:-32]).digest() == data[-32:]
+    F, H, O = struct.unpack("<iii", data[8:20])
+    assert (F, O) == (64, 45)
+    assert len(data) == 20 + 4 * (H * F + H + H * H + H + O * H + O) + 32
