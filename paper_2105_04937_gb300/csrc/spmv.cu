@@ -373,26 +373,31 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
 
     const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
     const int64_t xrow0 = r0 + tw;
-    // Software pipeline: the value and x loads of the next D diagonals are
-    // issued before the double-word arithmetic of the current D, so a warp
-    // keeps memory requests in flight while it computes.
-    auto load_group = [&](int32_t pg, float2 (&v)[D][U][V], float2 (&xv)[D][U][V]) {
+    int32_t p = p0;
+    auto group = [&](auto Dc) {
+        constexpr int DD = decltype(Dc)::value;
+        int64_t off[DD];
 #pragma unroll
-        for (int d = 0; d < D; d++) {
-            const bool live = pg + d < p1;
-            const int64_t off = live ? (int64_t)dia_offset[pg + d] : 0;
-            const float2 *vp = dia_dw + (int64_t)(live ? pg + d : pg) * n_b;
+        for (int d = 0; d < DD; d++) off[d] = dia_offset[p + d];
+        float2 v[DD][U][V];
+#pragma unroll
+        for (int d = 0; d < DD; d++) {
+            const float2 *vp = dia_dw + (int64_t)(p + d) * n_b;
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                if (live && (full || tl[u] < rows)) {
+                if (full || tl[u] < rows) {
                     const uint4 r = ld_stream16(vp + tl[u]);
                     memcpy(v[d][u], &r, 16);
                 } else {
                     v[d][u][0] = v[d][u][1] = make_float2(0.f, 0.f);
                 }
             }
-            const int64_t jw = xrow0 + off;
-            if (live && full && jw >= 0 && jw + RW <= n) {
+        }
+        float2 xv[DD][U][V];
+#pragma unroll
+        for (int d = 0; d < DD; d++) {
+            const int64_t jw = xrow0 + off[d];
+            if (full && jw >= 0 && jw + RW <= n) {
                 const bool al = (jw & 1) == 0;
 #pragma unroll
                 for (int u = 0; u < U; u++) {
@@ -411,37 +416,22 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
 #pragma unroll
                     for (int m = 0; m < V; m++) {
                         const int64_t jm = jw + (tl[u] - tw) + m;
-                        xv[d][u][m] = (live && tl[u] + m < rows && jm >= 0 && jm < n)
+                        xv[d][u][m] = (tl[u] + m < rows && jm >= 0 && jm < n)
                                           ? __ldg(x_dw + jm)
                                           : make_float2(0.f, 0.f);
                     }
             }
         }
+#pragma unroll
+        for (int d = 0; d < DD; d++)
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int m = 0; m < V; m++) dw::dw_fma(sh[u][m], sl[u][m], v[d][u][m], xv[d][u][m]);
+        p += DD;
     };
-    float2 va[D][U][V], xa[D][U][V], vb[D][U][V], xb[D][U][V];
-    if (p0 < p1) load_group(p0, va, xa);
-    for (int32_t p = p0; p < p1; p += D) {
-        const bool more = p + D < p1;
-        if (more) load_group(p + D, vb, xb);
-#pragma unroll
-        for (int d = 0; d < D; d++)
-            if (p + d < p1)
-#pragma unroll
-                for (int u = 0; u < U; u++)
-#pragma unroll
-                    for (int m = 0; m < V; m++) dw::dw_fma(sh[u][m], sl[u][m], va[d][u][m], xa[d][u][m]);
-        if (more) {
-#pragma unroll
-            for (int d = 0; d < D; d++)
-#pragma unroll
-                for (int u = 0; u < U; u++)
-#pragma unroll
-                    for (int m = 0; m < V; m++) {
-                        va[d][u][m] = vb[d][u][m];
-                        xa[d][u][m] = xb[d][u][m];
-                    }
-        }
-    }
+    for (; p + D <= p1;) group(std::integral_constant<int, D>{});
+    for (; p < p1;) group(std::integral_constant<int, 1>{});
 
 #pragma unroll
     for (int u = 0; u < U; u++)
