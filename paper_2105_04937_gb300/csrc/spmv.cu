@@ -136,14 +136,29 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
 #pragma unroll
         for (int m = 0; m < V; m++) acc[u][m] = Acc(0);
 
-    // CSR remainder rows of the tile (Fig. 13, first loop).  Each lane sums
-    // whole rows (row tw + rr for rr = lane, lane + 32, ...), in column order
-    // from zero, and the sums reach their owners through shared memory: the
-    // same operations as summing into acc directly, with one row per lane.
+    // CSR remainder rows of the tile (Fig. 13, first loop).  With V >= 4 rows
+    // per lane (FP32, BF16) each lane instead sums whole rows (row tw + rr for
+    // rr = lane, lane + 32, ...), in column order from zero, and the sums reach
+    // their owners through shared memory: the same operations as summing into
+    // acc directly, with one row per lane instead of V in sequence.
     {
         const int32_t tend = full ? tw + RW : rows;
         const int32_t q0 = csr_row_ptr[r0 + tw], q1 = csr_row_ptr[r0 + tend];
-        if (q0 != q1) {
+        if (q0 != q1 && V < 4) {
+            // two rows per lane (FP64): sum them in place
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int m = 0; m < V; m++) {
+                    const int32_t t = tl[u] + m;
+                    if (t < rows) {
+                        const int64_t i = r0 + t;
+                        const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
+                        for (int32_t k = a; k < b; k++)
+                            acc[u][m] += widen(csr_val[k]) * widen(ldg_elem(x + csr_col[k]));
+                    }
+                }
+        } else if (q0 != q1) {
             __shared__ Acc rsum[SPMV_WARPS][RW];
             Acc *rs = rsum[threadIdx.x >> 5];
             for (int rr = lane; rr < RW; rr += 32) {
