@@ -150,13 +150,13 @@ def profiled_traffic(variant):
         src = open(os.path.join(ROOT, "paper_2105_04937_gb300", "csrc", "spmv.cu"), "rb").read()
     except OSError:
         return None
-    fields = dict(line.split(": ", 1) for line in md.splitlines()
-                  if line.startswith(("traffic_bytes:", "kernel:", "source_sha1_16:")))
-    if fields.get("kernel") != f"k_mhdc_spmv<double> variant {variant}":
-        return None
-    if fields.get("source_sha1_16") != hashlib.sha1(src).hexdigest()[:16]:
-        return None
-    return int(fields["traffic_bytes"])
+    sha = hashlib.sha1(src).hexdigest()[:16]
+    for line in md.splitlines():
+        # "traffic: <variant> <bytes> <source sha1 prefix>"
+        parts = line.split()
+        if len(parts) == 4 and parts[0] == "traffic:" and parts[1] == str(variant) and parts[3] == sha:
+            return int(parts[2])
+    return None
 
 
 def max_over_ranks(value: float, dist, device) -> float:
