@@ -51,6 +51,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--variant", type=int, default=None,
                     help="use this SpMV tile shape instead of the autotuner's choice")
+    ap.add_argument("--sweep", default=None, choices=["stencil", "model"],
+                    help="instead of the headline line: the stencil sweep of Sec. 6.3 "
+                         "(CSR / DIA / B-DIA / M-HDC over n, plus an n_b sweep) or the "
+                         "model-accuracy grid of Sec. 6.4.3; JSON lines to --out")
+    ap.add_argument("--out", default=None, help="file for the sweep's JSON lines")
+    ap.add_argument("--sizes", default="1e4,3e4,1e5,3e5,1e6,3e6,1e7,2e7,5e7",
+                    help="matrix sizes n of the stencil sweep")
     return ap.parse_args()
 
 
@@ -84,11 +91,13 @@ class ClockSampler:
         self.t0 = self.t1 = None
 
     def start(self):
+        import tempfile
+        self.buf = tempfile.TemporaryFile(mode="w+")  # a pipe would fill up on long runs
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                stdout=self.buf, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         time.sleep(0.3)
@@ -102,10 +111,12 @@ class ClockSampler:
         time.sleep(0.25)
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-            out = ""
+        self.buf.seek(0)
+        out = self.buf.read()
+        self.buf.close()
         rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
         sm, smax, reasons, pw = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -434,6 +445,204 @@ def measure_selector(mh, torch, A, rp, col, val, log):
     return res
 
 
+# ------------------------------------------------------------------ sweeps
+
+def _product_us(fn, torch, stream, target_ms=60.0):
+    """Mean time of one product over back-to-back repetitions (warm: inputs
+    smaller than L2 stay there, as in the paper's in-cache regime)."""
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    one = max(e0.elapsed_time(e1), 1e-3)
+    reps = int(min(5000, max(10, target_ms / one)))
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / reps
+
+
+def _timed_build(fn, torch):
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    h = fn()
+    torch.cuda.synchronize()
+    return h, (time.perf_counter() - t) * 1e3
+
+
+def sweep_stencil(args, mh, torch, log):
+    """Sec. 6.3 on the GPU: the 1D 3-point, 2D 5-point and 3D 7-point stencil
+    matrices over n, with the CSR kernel (Fig. 2), the unblocked DIA order
+    (Fig. 5), B-DIA (all nonempty diagonals kept in every block, n_b = 4096,
+    Fig. 9) and M-HDC (n_b = 4096, theta = 0.6), against the model of
+    Sec. 5.2; then B-DIA over n_b at n = 1e7.  Each point also checks that DIA
+    and B-DIA agree bit for bit and CSR agrees within 1e-12 sum |a||x|."""
+    import synth
+    from paper_2105_04937_gb300 import model as pm
+    stream = torch.cuda.current_stream()
+    sizes = [int(float(v)) for v in args.sizes.split(",") if v]
+    out = open(args.out, "w") if args.out else None
+    gam = {1: 1 / 3, 2: 1 / 5, 3: 3 / 7}
+    ndiag = {1: 3, 2: 5, 3: 7}
+    clocks = ClockSampler(0)
+    clocks.start()
+
+    def emit(rec):
+        if out:
+            out.write(json.dumps(rec) + "\n")
+            out.flush()
+
+    def check(A_n, rp, col, val, x, y_csr, y_dia, y_bdia):
+        absr = torch.empty_like(y_csr)
+        mh.csr_spmv(A_n, rp, col, val.abs(), x.abs(), absr)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(y_dia, y_bdia))
+        ok = bool(((y_csr - y_bdia).abs() <= 1e-12 * absr).all())
+        return same, ok
+
+    for dim in (1, 2, 3):
+        for n in sizes:
+            A = synth.paper_stencil(n, dim)
+            rp = torch.from_numpy(A.row_ptr).cuda()
+            col = torch.from_numpy(A.col).cuda()
+            val = torch.from_numpy(A.val).cuda()
+            x = torch.from_numpy(synth.uniform_vector(n, 11)).cuda()
+            ys = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(4)]
+            Hb, tb_b = _timed_build(lambda: mh.hdc_build(n, rp, col, val, N_B, 0.0, "f64"), torch)
+            Hm, tb_m = _timed_build(lambda: mh.mhdc_build(n, rp, col, val, N_B, THETA, "f64"), torch)
+            t = {"csr": _product_us(lambda: mh.csr_spmv(n, rp, col, val, x, ys[0]), torch, stream),
+                 "dia": _product_us(lambda: mh.mhdc_dia_spmv(Hb, x, ys[1]), torch, stream),
+                 "bdia": _product_us(lambda: mh.mhdc_spmv(Hb, x, ys[2]), torch, stream),
+                 "mhdc": _product_us(lambda: mh.mhdc_spmv(Hm, x, ys[3]), torch, stream)}
+            same, ok = check(n, rp, col, val, x, ys[0], ys[1], ys[2])
+            gf = {k: 2 * A.nnz / (v * 1e3) for k, v in t.items()}
+            nd = ndiag[dim]
+            rec = {"sweep": "stencil", "dim": dim, "n": n, "nnz": A.nnz, "n_b": N_B,
+                   "us": {k: round(v, 3) for k, v in t.items()},
+                   "gflops": {k: round(v, 2) for k, v in gf.items()},
+                   "measured": {"dia_over_csr": t["csr"] / t["dia"],
+                                "bdia_over_csr": t["csr"] / t["bdia"],
+                                "bdia_over_dia": t["dia"] / t["bdia"],
+                                "mhdc_over_csr": t["csr"] / t["mhdc"]},
+                   "model_paper_gamma": pm.stencil_speedups(nd, gam[dim]),
+                   "model_gamma_1_over_nd": pm.stencil_speedups(nd, 1 / nd),
+                   "build_ms": {"bdia": round(tb_b, 2), "mhdc": round(tb_m, 2)},
+                   "dia_bits_equal_bdia": same, "csr_within_tol": ok,
+                   "mhdc_nnz_rem": Hm.info["nnz_rem"]}
+            emit(rec)
+            log(f"{dim}D n={n:>9d} GFLOP/s csr {gf['csr']:7.1f} dia {gf['dia']:7.1f} "
+                f"bdia {gf['bdia']:7.1f} mhdc {gf['mhdc']:7.1f} | B-DIA/CSR "
+                f"{rec['measured']['bdia_over_csr']:.3f} (model "
+                f"{rec['model_paper_gamma']['bdia_over_csr']:.3f}) DIA/CSR "
+                f"{rec['measured']['dia_over_csr']:.3f} (model "
+                f"{rec['model_paper_gamma']['dia_over_csr']:.3f}) same={same} ok={ok}")
+            Hb.destroy()
+            Hm.destroy()
+            del rp, col, val, x, ys, A
+            torch.cuda.empty_cache()
+    # block width sweep (Sec. 6.3, last experiment) at n = 1e7
+    n = 10_000_000
+    for dim in (1, 2, 3):
+        A = synth.paper_stencil(n, dim)
+        rp = torch.from_numpy(A.row_ptr).cuda()
+        col = torch.from_numpy(A.col).cuda()
+        val = torch.from_numpy(A.val).cuda()
+        x = torch.from_numpy(synth.uniform_vector(n, 11)).cuda()
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        y_ref = torch.empty(n, dtype=torch.float64, device="cuda")
+        t_csr = _product_us(lambda: mh.csr_spmv(n, rp, col, val, x, y_ref), torch, stream)
+        for n_b in (1, 4, 16, 64, 256, 1024, 4096, 16384, 65536, 262144, 1048576):
+            H, tb = _timed_build(lambda: mh.hdc_build(n, rp, col, val, n_b, 0.0, "f64"), torch)
+            tt = _product_us(lambda: mh.mhdc_spmv(H, x, y), torch, stream)
+            td = _product_us(lambda: mh.mhdc_dia_spmv(H, x, y), torch, stream) if n_b == N_B else None
+            torch.cuda.synchronize()
+            d = float(((y - y_ref).abs()).max())
+            rec = {"sweep": "stencil_nb", "dim": dim, "n": n, "n_b": n_b, "us_bdia": round(tt, 3),
+                   "gflops_bdia": round(2 * A.nnz / (tt * 1e3), 2),
+                   "us_csr": round(t_csr, 3), "us_dia": None if td is None else round(td, 3),
+                   "build_ms": round(tb, 2), "max_abs_diff_vs_csr": d}
+            emit(rec)
+            log(f"{dim}D n_b={n_b:>8d} B-DIA {rec['gflops_bdia']:7.1f} GFLOP/s "
+                f"({tt:8.1f} us; CSR {t_csr:.1f} us) build {tb:.1f} ms")
+            H.destroy()
+        del rp, col, val, x, y, y_ref, A
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    emit({"sweep": "clocks", **clk})
+    log(f"clocks: {clk}")
+    if out:
+        out.close()
+
+
+def sweep_model(args, mh, torch, log):
+    """Sec. 6.4.3 on the GPU: for each matrix and each (n_b, theta) of the
+    paper's grid, the measured relative performance RP_exe = T_CSR / T_M-HDC
+    (FP64) against RP_est from the model of Sec. 5.3 with the built handle's
+    alpha and beta, c = nnz / n and v_x = 1; RE = (RP_est - RP_exe) / RP_exe."""
+    import synth
+    from paper_2105_04937_gb300 import model as pm
+    stream = torch.cuda.current_stream()
+    out = open(args.out, "w") if args.out else None
+    mats = [("stencil27_128", lambda: synth.config_matrix("stencil27_128")),
+            ("scattered_4m", lambda: synth.config_matrix("scattered_4m")),
+            ("paper_3d7_1e7", lambda: synth.paper_stencil(10_000_000, 3)),
+            ("paper_2d5_1e7", lambda: synth.paper_stencil(10_000_000, 2))]
+    for k in range(8):
+        p = synth.family_params(k, base_seed=5000, min_dim=96, max_dim=160)
+        mats.append((f"family_{5000 + k}", lambda p=p: synth.family_matrix(p)))
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, make in mats:
+        A = make()
+        n = A.n
+        rp = torch.from_numpy(A.row_ptr).cuda()
+        col = torch.from_numpy(A.col).cuda()
+        val = torch.from_numpy(A.val).cuda()
+        x = torch.from_numpy(synth.uniform_vector(n, 13)).cuda()
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        t_csr = _product_us(lambda: mh.csr_spmv(n, rp, col, val, x, y), torch, stream)
+        c = A.nnz / n
+        for mode in ("block", "global"):
+            for n_b in (10, 50, 100, 500, 1000, 5000, 10000):
+                for theta in (0.5, 0.6, 0.7, 0.8, 0.9):
+                    fn = mh.mhdc_build if mode == "block" else mh.hdc_build
+                    H = fn(n, rp, col, val, n_b, theta, "f64")
+                    inf = H.info
+                    t = _product_us(lambda: mh.mhdc_spmv(H, x, y), torch, stream, target_ms=30.0)
+                    beta = inf["nnz_rem"] / A.nnz
+                    alpha = inf["alpha"] if inf["P"] > 0 else 1.0
+                    exe = t_csr / t
+                    est = pm.rp_est(alpha, beta, c) if beta < 1 else 1.0
+                    rec = {"sweep": "model", "matrix": name, "n": n, "nnz": A.nnz, "mode": mode,
+                           "n_b": n_b, "theta": theta, "alpha": alpha, "beta": beta, "c": c,
+                           "us_csr": round(t_csr, 3), "us": round(t, 3), "rp_exe": exe,
+                           "rp_est": est, "re": pm.relative_error(est, exe)}
+                    if out:
+                        out.write(json.dumps(rec) + "\n")
+                        out.flush()
+                    H.destroy()
+        sel = [json.loads(l) for l in open(args.out)] if out else []
+        mine = [r for r in sel if r.get("matrix") == name and r["mode"] == "block"]
+        if mine:
+            best = max(mine, key=lambda r: r["rp_exe"])
+            log(f"{name}: CSR {t_csr:.1f} us; best M-HDC RP_exe {best['rp_exe']:.3f} at n_b "
+                f"{best['n_b']} theta {best['theta']} (RP_est {best['rp_est']:.3f}); |RE| <= 0.05 "
+                f"in {np.mean([abs(r['re']) <= 0.05 for r in mine]) * 100:.0f}% of the grid")
+        del rp, col, val, x, y, A
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    if out:
+        out.write(json.dumps({"sweep": "clocks", **clk}) + "\n")
+        out.close()
+    log(f"clocks: {clk}")
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -456,6 +665,8 @@ def main():
     import synth
     mh.lib()
     stream = torch.cuda.current_stream()
+    if args.sweep:
+        return (sweep_stencil if args.sweep == "stencil" else sweep_model)(args, mh, torch, log)
 
     A = synth.config_matrix("stencil27_128")
     rp = torch.from_numpy(A.row_ptr).cuda()

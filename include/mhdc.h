@@ -144,6 +144,22 @@ int mhdc_spmm(mhdc_handle A, int32_t k, const void *d_X, int64_t ldx, void *d_Y,
               void *stream);
 
 /*
+ * mhdc_dia_spmv -- y = A x in the unblocked DIA order (Sec. 3.3, Fig. 5) for a
+ * handle made by hdc_build: y is first set to the CSR remainder's product
+ * (zero for rows without remainder), then every diagonal is one pass over
+ * all n rows, y[i] += val * x[i + offset], so y is read and written once per
+ * diagonal (the main-memory traffic the DIA model of Sec. 5.2 counts).  Each
+ * row sees the same operations in the same order as mhdc_spmv, so y is
+ * bit-identical to mhdc_spmv on the same handle.
+ *
+ *   d_x, d_y   as mhdc_spmv (must not overlap)
+ * Launches 1 + D kernels (D diagonals) on `stream`, asynchronous.
+ * MHDC_ERR_UNSUPPORTED for handles from mhdc_build (block-wise selection:
+ * blocks hold different diagonals).
+ */
+int mhdc_dia_spmv(mhdc_handle A, const void *d_x, void *d_y, void *stream);
+
+/*
  * csr_spmv -- the plain FP64 CSR kernel (Sec. 3.2, Fig. 2): y[i] =
  * sum_k val[k] x[col[k]] over row i.  Arrays as mhdc_build's input (not
  * checked here); d_x, d_y double[n].  Asynchronous on `stream`.

@@ -36,6 +36,8 @@ __all__ = [
 
 MHDC_F64, MHDC_F32, MHDC_BF16 = 0, 1, 2
 DTYPES = {"f64": MHDC_F64, "f32": MHDC_F32, "bf16": MHDC_BF16}
+(MHDC_OK, MHDC_ERR_INVALID_ARG, MHDC_ERR_BAD_CSR, MHDC_ERR_OOM, MHDC_ERR_CUDA,
+ MHDC_ERR_UNSUPPORTED, MHDC_ERR_DEVICE_CHECK, MHDC_ERR_TIMEOUT) = 0, -1, -2, -3, -4, -5, -6, -7
 _NP_STORE = {MHDC_F64: np.float64, MHDC_F32: np.float32, MHDC_BF16: np.uint16}
 
 _lock = threading.Lock()
@@ -63,6 +65,7 @@ _SIGS = {
     "hdc_build": [_I64, _P, _P, _P, _I32, _D, _I32, _P, C.POINTER(C.c_void_p)],
     "mhdc_spmv": [_P, _P, _P, _P],
     "mhdc_spmv_host": [_P, _P, _P, _P],
+    "mhdc_dia_spmv": [_P, _P, _P, _P],
     "mhdc_spmm": [_P, _I32, _P, _I64, _P, _I64, _P],
     "csr_spmv": [_I64, _P, _P, _P, _P, _P, _P],
     "mhdc_export": [_P, _P, _P, _P, _P, _P, _P],
@@ -235,6 +238,16 @@ def mhdc_spmv(A: Matrix, x, y, stream=None):
     _check_dev(x, xt, A.n, "x")
     _check_dev(y, yt, A.n, "y")
     _check(lib().mhdc_spmv(C.c_void_p(A.handle), _ptr(x), _ptr(y), _stream(stream)), "mhdc_spmv")
+    return y
+
+
+def mhdc_dia_spmv(A: Matrix, x, y, stream=None):
+    """y = A x in the unblocked DIA order (Fig. 5); A must come from hdc_build."""
+    xt, yt = _xy_types(A)
+    _check_dev(x, xt, A.n, "x")
+    _check_dev(y, yt, A.n, "y")
+    _check(lib().mhdc_dia_spmv(C.c_void_p(A.handle), _ptr(x), _ptr(y), _stream(stream)),
+           "mhdc_dia_spmv")
     return y
 
 

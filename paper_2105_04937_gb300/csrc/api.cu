@@ -83,6 +83,19 @@ int mhdc_spmv_host(mhdc_handle A, const void *h_x, void *h_y, void *stream)
     return MHDC_OK;
 }
 
+int mhdc_dia_spmv(mhdc_handle A, const void *d_x, void *d_y, void *stream)
+{
+    if (!A || (A->n > 0 && (!d_x || !d_y))) {
+        set_error_msg("mhdc_dia_spmv: null argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    if (A->mode != MHDC_MODE_GLOBAL) {
+        set_error_msg("mhdc_dia_spmv: needs a handle from hdc_build (same diagonals in every block)");
+        return MHDC_ERR_UNSUPPORTED;
+    }
+    return launch_dia(A, d_x, d_y, (cudaStream_t)stream);
+}
+
 int mhdc_spmm(mhdc_handle A, int32_t k, const void *d_X, int64_t ldx, void *d_Y, int64_t ldy,
               void *stream)
 {

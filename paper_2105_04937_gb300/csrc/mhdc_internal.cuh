@@ -96,6 +96,7 @@ int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double
 int launch_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream);
 int launch_spmm(mhdc_matrix *A, int k, const void *d_X, int64_t ldx, void *d_Y,
                 int64_t ldy, cudaStream_t stream);
+int launch_dia(const mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream);
 int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                const double *x, double *y, cudaStream_t stream);
 int launch_stream_bench(int64_t N, const double *A, const double *B, const int32_t *I, double *C,

@@ -592,6 +592,94 @@ k_csr_spmv(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict_
     y[i] = s;
 }
 
+// Unblocked DIA order (Fig. 5) on a handle built with global selection, where
+// every row block holds the same D diagonals (dia_ptr[ib] = ib * D): the
+// remainder rows initialise y (the "y = 0" pass plus the remainder's CSR
+// terms, in column order), then each diagonal is one pass over all n rows,
+// y[i] += dia_val * x[i + off], so y is read and written once per diagonal.
+// The operations of each row are those of the blocked kernel in the same
+// order, so both give bit-identical y.
+constexpr int DIA_THREADS = 256;
+
+template <typename VT>
+__global__ void __launch_bounds__(DIA_THREADS)
+k_dia_rem(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+          const VT *__restrict__ val, const typename Tr<VT>::X *__restrict__ x,
+          typename Tr<VT>::Y *__restrict__ y)
+{
+    using Acc = typename Tr<VT>::Acc;
+    const int64_t i = (int64_t)blockIdx.x * DIA_THREADS + threadIdx.x;
+    if (i >= n) return;
+    const int32_t a = rp[i], b = rp[i + 1];
+    Acc s = Acc(0);
+    for (int32_t k = a; k < b; k++) s += widen(val[k]) * widen(ldg_elem(x + col[k]));
+    y[i] = s;
+}
+
+// Pass of diagonal k: thread g owns rows [g V, g V + V), all inside one row
+// block (n_b % V == 0 when VEC), and reads their V values with one 16-byte
+// load; rows whose column falls outside [0, n) add 0 * 0 as the blocked
+// kernel does.
+template <typename VT, bool VEC>
+__global__ void __launch_bounds__(DIA_THREADS)
+k_dia_pass(int64_t n, int32_t n_b, int32_t D, int32_t k, const int32_t *__restrict__ dia_offset,
+           const VT *__restrict__ dia_val, const typename Tr<VT>::X *__restrict__ x,
+           typename Tr<VT>::Y *__restrict__ y)
+{
+    using X = typename Tr<VT>::X;
+    constexpr int V = VEC ? Tr<VT>::V : 1;
+    const int64_t i0 = ((int64_t)blockIdx.x * DIA_THREADS + threadIdx.x) * V;
+    if (i0 >= n) return;
+    const int64_t ib = i0 / n_b;
+    const int64_t t = i0 - ib * n_b;
+    const VT *vp = dia_val + (ib * D + k) * (int64_t)n_b + t;
+    VT v[V];
+    if constexpr (VEC) {
+        const uint4 r = ld_stream16(vp);
+        memcpy(v, &r, 16);
+    } else {
+        v[0] = vp[0];
+    }
+    const int64_t off = dia_offset[k];
+#pragma unroll
+    for (int m = 0; m < V; m++) {
+        const int64_t i = i0 + m;
+        if (i < n) {
+            const int64_t j = i + off;
+            const X xv = (j >= 0 && j < n) ? ldg_elem(x + j) : X(0);
+            y[i] = y[i] + widen(v[m]) * widen(xv);
+        }
+    }
+}
+
+template <typename VT>
+int dia_typed(const mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t st)
+{
+    using X = typename Tr<VT>::X;
+    using Y = typename Tr<VT>::Y;
+    const X *x = static_cast<const X *>(d_x);
+    Y *y = static_cast<Y *>(d_y);
+    const int64_t n = A->n;
+    k_dia_rem<VT><<<(unsigned)((n + DIA_THREADS - 1) / DIA_THREADS), DIA_THREADS, 0, st>>>(
+        n, A->csr_row_ptr, A->csr_col, static_cast<const VT *>(A->csr_val), x, y);
+    MHDC_LAUNCH_CHECK("k_dia_rem");
+    const int32_t D = (int32_t)(A->P / A->n_blocks);
+    constexpr int VV = Tr<VT>::V;
+    const bool vec = (A->n_b % VV) == 0;
+    const int64_t groups = vec ? (n + VV - 1) / VV : n;
+    const unsigned grid = (unsigned)((groups + DIA_THREADS - 1) / DIA_THREADS);
+    for (int32_t k = 0; k < D; k++) {
+        if (vec)
+            k_dia_pass<VT, true><<<grid, DIA_THREADS, 0, st>>>(
+                n, A->n_b, D, k, A->dia_offset, static_cast<const VT *>(A->dia_val), x, y);
+        else
+            k_dia_pass<VT, false><<<grid, DIA_THREADS, 0, st>>>(
+                n, A->n_b, D, k, A->dia_offset, static_cast<const VT *>(A->dia_val), x, y);
+        MHDC_LAUNCH_CHECK("k_dia_pass");
+    }
+    return MHDC_OK;
+}
+
 // Read-only member of the memory benchmarks: out[cta] = bitwise XOR of the
 // 64-bit words of the CTA's share of A (16-byte loads, 4 in flight per
 // thread).  Integer XOR keeps the FP64 pipe, which on GB300 is slower than
@@ -832,6 +920,16 @@ int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *v
     k_csr_spmv<<<(unsigned)grid, CSR_THREADS, 0, stream>>>(n, rp, col, val, x, y);
     MHDC_LAUNCH_CHECK("k_csr_spmv");
     return MHDC_OK;
+}
+
+int launch_dia(const mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream)
+{
+    if (A->n == 0) return MHDC_OK;
+    switch (A->dtype) {
+    case MHDC_F64: return dia_typed<double>(A, d_x, d_y, stream);
+    case MHDC_F32: return dia_typed<float>(A, d_x, d_y, stream);
+    default: return dia_typed<__nv_bfloat16>(A, d_x, d_y, stream);
+    }
 }
 
 int launch_read_bench(int64_t N, const double *A, double *out, int grid, cudaStream_t stream)

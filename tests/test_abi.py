@@ -52,6 +52,9 @@ def test_status_codes_and_strerror(built_lib):
         txt = built_lib.mhdc_strerror(code).decode()
         assert txt and txt != "unknown status", name
     assert built_lib.mhdc_strerror(12345).decode() == "unknown status"
+    import paper_2105_04937_gb300 as m
+    for name, code in codes.items():
+        assert getattr(m, name) == code, name
 
 
 def test_python_binding_names_match_abi():
