@@ -199,6 +199,12 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  * terms; the handle checks its values at build and each product checks x on
  * the device, and outside that window the product runs the native FP64 path
  * (variant -1's arithmetic) instead.
+ * Variants 16-18 (FP64 handles only) mix the two: one warp tile in 4 (16,
+ * 18) or in 8 (17) runs the emulated arithmetic on the FP32 pipe, splitting x
+ * as it loads it, while the other tiles run the native FP64 tile, so both
+ * pipes work at once.  Rows of emulated tiles carry the emulated error bound
+ * above, the others are native FP64; an emulated tile that meets an x
+ * outside the window is recomputed natively by the same warp.
  *
  * mhdc_set_variant -- use variant v for this handle (-1: default chosen from n_b).
  * mhdc_tune        -- time every variant on (d_x, d_y) (overwriting d_y), keep
@@ -206,7 +212,7 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  *                     times_us is not NULL, each variant's mean time in
  *                     microseconds to times_us[MHDC_NUM_VARIANTS].  Synchronous.
  */
-#define MHDC_NUM_VARIANTS 16
+#define MHDC_NUM_VARIANTS 19
 int mhdc_set_variant(mhdc_handle A, int32_t v);
 int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *best,
               float *times_us);
