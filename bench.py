@@ -516,11 +516,20 @@ def sweep_stencil(args, mh, torch, log):
             ys = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(4)]
             Hb, tb_b = _timed_build(lambda: mh.hdc_build(n, rp, col, val, N_B, 0.0, "f64"), torch)
             Hm, tb_m = _timed_build(lambda: mh.mhdc_build(n, rp, col, val, N_B, THETA, "f64"), torch)
+            # the library's autotuner picks each handle's tile shape (not timed)
+            vb, _ = mh.mhdc_tune(Hb, x, ys[2])
+            vm, _ = mh.mhdc_tune(Hm, x, ys[3])
             t = {"csr": _product_us(lambda: mh.csr_spmv(n, rp, col, val, x, ys[0]), torch, stream),
                  "dia": _product_us(lambda: mh.mhdc_dia_spmv(Hb, x, ys[1]), torch, stream),
                  "bdia": _product_us(lambda: mh.mhdc_spmv(Hb, x, ys[2]), torch, stream),
                  "mhdc": _product_us(lambda: mh.mhdc_spmv(Hm, x, ys[3]), torch, stream)}
+            # DIA order against the same handle's native product (variant -1)
+            mh.mhdc_set_variant(Hb, -1)
+            mh.mhdc_spmv(Hb, x, ys[2])
             same, ok = check(n, rp, col, val, x, ys[0], ys[1], ys[2])
+            mh.mhdc_set_variant(Hb, vb)
+            mh.mhdc_spmv(Hb, x, ys[2])
+            ok = ok and check(n, rp, col, val, x, ys[0], ys[1], ys[2])[1]
             gf = {k: 2 * A.nnz / (v * 1e3) for k, v in t.items()}
             nd = ndiag[dim]
             rec = {"sweep": "stencil", "dim": dim, "n": n, "nnz": A.nnz, "n_b": N_B,
@@ -533,6 +542,7 @@ def sweep_stencil(args, mh, torch, log):
                    "model_paper_gamma": pm.stencil_speedups(nd, gam[dim]),
                    "model_gamma_1_over_nd": pm.stencil_speedups(nd, 1 / nd),
                    "build_ms": {"bdia": round(tb_b, 2), "mhdc": round(tb_m, 2)},
+                   "variant": {"bdia": vb, "mhdc": vm},
                    "dia_bits_equal_bdia": same, "csr_within_tol": ok,
                    "mhdc_nnz_rem": Hm.info["nnz_rem"]}
             emit(rec)
@@ -541,7 +551,8 @@ def sweep_stencil(args, mh, torch, log):
                 f"{rec['measured']['bdia_over_csr']:.3f} (model "
                 f"{rec['model_paper_gamma']['bdia_over_csr']:.3f}) DIA/CSR "
                 f"{rec['measured']['dia_over_csr']:.3f} (model "
-                f"{rec['model_paper_gamma']['dia_over_csr']:.3f}) same={same} ok={ok}")
+                f"{rec['model_paper_gamma']['dia_over_csr']:.3f}) same={same} ok={ok} "
+                f"variants {vb}/{vm}")
             Hb.destroy()
             Hm.destroy()
             del rp, col, val, x, ys, A
@@ -559,6 +570,7 @@ def sweep_stencil(args, mh, torch, log):
         t_csr = _product_us(lambda: mh.csr_spmv(n, rp, col, val, x, y_ref), torch, stream)
         for n_b in (1, 4, 16, 64, 256, 1024, 4096, 16384, 65536, 262144, 1048576):
             H, tb = _timed_build(lambda: mh.hdc_build(n, rp, col, val, n_b, 0.0, "f64"), torch)
+            v_nb, _ = mh.mhdc_tune(H, x, y)
             tt = _product_us(lambda: mh.mhdc_spmv(H, x, y), torch, stream)
             td = _product_us(lambda: mh.mhdc_dia_spmv(H, x, y), torch, stream) if n_b == N_B else None
             torch.cuda.synchronize()
@@ -566,10 +578,10 @@ def sweep_stencil(args, mh, torch, log):
             rec = {"sweep": "stencil_nb", "dim": dim, "n": n, "n_b": n_b, "us_bdia": round(tt, 3),
                    "gflops_bdia": round(2 * A.nnz / (tt * 1e3), 2),
                    "us_csr": round(t_csr, 3), "us_dia": None if td is None else round(td, 3),
-                   "build_ms": round(tb, 2), "max_abs_diff_vs_csr": d}
+                   "build_ms": round(tb, 2), "max_abs_diff_vs_csr": d, "variant": v_nb}
             emit(rec)
             log(f"{dim}D n_b={n_b:>8d} B-DIA {rec['gflops_bdia']:7.1f} GFLOP/s "
-                f"({tt:8.1f} us; CSR {t_csr:.1f} us) build {tb:.1f} ms")
+                f"({tt:8.1f} us; CSR {t_csr:.1f} us) build {tb:.1f} ms variant {v_nb}")
             H.destroy()
         del rp, col, val, x, y, y_ref, A
         torch.cuda.empty_cache()
@@ -613,6 +625,10 @@ def sweep_model(args, mh, torch, log):
                 for theta in (0.5, 0.6, 0.7, 0.8, 0.9):
                     fn = mh.mhdc_build if mode == "block" else mh.hdc_build
                     H = fn(n, rp, col, val, n_b, theta, "f64")
+                    if args.variant is None:
+                        mh.mhdc_tune(H, x, y)
+                    else:
+                        mh.mhdc_set_variant(H, args.variant)
                     inf = H.info
                     t = _product_us(lambda: mh.mhdc_spmv(H, x, y), torch, stream, target_ms=30.0)
                     beta = inf["nnz_rem"] / A.nnz
@@ -622,7 +638,8 @@ def sweep_model(args, mh, torch, log):
                     rec = {"sweep": "model", "matrix": name, "n": n, "nnz": A.nnz, "mode": mode,
                            "n_b": n_b, "theta": theta, "alpha": alpha, "beta": beta, "c": c,
                            "us_csr": round(t_csr, 3), "us": round(t, 3), "rp_exe": exe,
-                           "rp_est": est, "re": pm.relative_error(est, exe)}
+                           "rp_est": est, "re": pm.relative_error(est, exe),
+                           "variant": inf["variant"]}
                     if out:
                         out.write(json.dumps(rec) + "\n")
                         out.flush()
@@ -692,6 +709,28 @@ def main():
         best_variant, variant_us = args.variant, []
     log(f"tuned: variant {best_variant}; per-variant us {[round(t, 2) for t in variant_us]}")
     info = H.info
+    accuracy = None
+    if best_variant >= mh.FIRST_EMULATED_VARIANT:
+        # emulated or mixed arithmetic: its distance from the native FP64
+        # product, per row relative to sum_j |a_ij||x_j| (not timed)
+        y_nat = torch.empty_like(y)
+        absr = torch.empty_like(y)
+        mh.mhdc_spmv(H, x, y)
+        mh.mhdc_set_variant(H, -1)
+        mh.mhdc_spmv(H, x, y_nat)
+        mh.mhdc_set_variant(H, best_variant)
+        mh.csr_spmv(A.n, rp, col, val.abs(), x.abs(), absr)
+        torch.cuda.synchronize()
+        rel = float(((y - y_nat).abs() / absr.clamp_min(1e-300)).max())
+        accuracy = {"max_row_err_vs_native_over_sum_abs": rel, "tolerance": 1e-12,
+                    "bound": 7e-13, "within": rel <= 1e-12}
+        log(f"accuracy of variant {best_variant}: {accuracy}")
+    launches_per_step = 2 if mh.FIRST_EMULATED_VARIANT <= best_variant < mh.FIRST_MIXED_VARIANT else 1
+    kernel_name = ("k_mhdc_spmv<double>" if best_variant < 6 else
+                   "k_mhdc_spmv_tma<double>" if best_variant < mh.FIRST_EMULATED_VARIANT else
+                   "k_split_x + k_mhdc_spmv_dw" if best_variant < 13 else
+                   "k_split_x + k_mhdc_spmv_tma_dw" if best_variant < mh.FIRST_MIXED_VARIANT else
+                   "k_mhdc_spmv_mixed")
 
     peak, peak_src = measured_peak()
     vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
@@ -838,6 +877,25 @@ def main():
         cpu = cpu_baseline(A, args.cpu_seconds, log)
 
     read_ceiling = extra.get("w_mem_gbs", {}).get("read_only")
+    hbm = {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+           "frac": round(achieved / peak, 4), "bytes_per_launch": info["bytes_model"],
+           "peak_source": peak_src, "read_only_probe_gbs": read_ceiling}
+    alu = {"achieved": round(alu_achieved, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+           "frac": round(alu_achieved / fp64_peak, 4), "flops_per_launch": 2 * slots,
+           "peak_source": "FP64: 2 FMA/clk/SM x 2 flop x SMs x max SM clock "
+                          "(GB300 nominal 1.25 TFLOP/s)",
+           "fp64_measured_tflops": extra.get("fma_measured", {}).get("fp64_tflops")}
+    common = {"traffic": profiled_traffic(best_variant),
+              "kernel": f"{kernel_name} variant {best_variant}", "kernel_us": round(kern_ms * 1e3, 3)}
+    if best_variant < mh.FIRST_EMULATED_VARIANT:
+        # native FP64: every slot is an FMA on the FP64 pipe, which bounds the kernel
+        roofline = {"bound": "alu", **alu, **common, "hbm": hbm}
+    else:
+        # emulated / mixed: the FP32 pipe takes part of the arithmetic, HBM is the bound
+        roofline = {"bound": "hbm", **{k: hbm[k] for k in ("achieved", "peak", "unit", "frac")},
+                    **common, "bytes_per_launch": info["bytes_model"], "peak_source": peak_src,
+                    "read_only_probe_gbs": read_ceiling,
+                    "alu_fp64_equivalent": alu}
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": ws,
@@ -851,24 +909,11 @@ def main():
                        "l2": "inputs larger than L2 (M-HDC arrays "
                              f"{info['bytes_model'] / 1e6:.0f} MB > 129 MB L2); no flush",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "roofline": {"bound": "alu", "achieved": round(alu_achieved, 4),
-                         "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                         "frac": round(alu_achieved / fp64_peak, 4),
-                         "traffic": profiled_traffic(best_variant),
-                         "kernel": f"k_mhdc_spmv<double> variant {best_variant}",
-                         "flops_per_launch": 2 * slots,
-                         "peak_source": "FP64: 2 FMA/clk/SM x 2 flop x SMs x max SM clock "
-                                        "(GB300 nominal 1.25 TFLOP/s)",
-                         "kernel_us": round(kern_ms * 1e3, 3),
-                         "fp64_measured_tflops": extra.get("fma_measured", {}).get("fp64_tflops"),
-                         "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                                 "frac": round(achieved / peak, 4),
-                                 "bytes_per_launch": info["bytes_model"],
-                                 "peak_source": peak_src,
-                                 "read_only_probe_gbs": read_ceiling}},
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * launches_per_step,
+            "accuracy": accuracy,
             "clocks": clocks,
             "build_ms": round(build_ms, 1),
             "baselines": extra,

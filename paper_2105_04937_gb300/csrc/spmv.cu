@@ -130,6 +130,9 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
 #pragma unroll
     for (int u = 0; u < U; u++) tl[u] = tw + (u * 32 + lane) * V;
 
+    // the block's diagonal range, loaded with the remainder bounds below (independent)
+    const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
+
     Acc acc[U][V];
 #pragma unroll
     for (int u = 0; u < U; u++)
@@ -181,7 +184,6 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
     }
 
     // the block's partial diagonals (Fig. 13, second loop)
-    const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
     const int64_t xrow0 = r0 + tw;  // x index of the tile's first row at offset 0
     int32_t p = p0;
     auto group = [&](auto Dc) {
