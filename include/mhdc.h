@@ -199,10 +199,10 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  * terms; the handle checks its values at build and each product checks x on
  * the device, and outside that window the product runs the native FP64 path
  * (variant -1's arithmetic) instead.
- * Variants 16-18 (FP64 handles only) mix the two: one warp tile in 4 (16,
- * 18) or in 8 (17) runs the emulated arithmetic on the FP32 pipe, splitting x
- * as it loads it, while the other tiles run the native FP64 tile, so both
- * pipes work at once.  Rows of emulated tiles carry the emulated error bound
+ * Variants 16-18 (FP64 handles only) mix the two: one warp tile in 4 (16),
+ * one CTA in 4 (17) or one CTA in 8 (18) runs the emulated arithmetic on the
+ * FP32 pipe, splitting x as it loads it, while the other tiles run the native
+ * FP64 tile, so both pipes work at once.  Rows of emulated tiles carry the emulated error bound
  * above, the others are native FP64; an emulated tile that meets an x
  * outside the window is recomputed natively by the same warp.
  *

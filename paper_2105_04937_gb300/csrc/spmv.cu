@@ -580,7 +580,7 @@ dw_tile_x64(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__res
     return true;
 }
 
-template <int U, int D, int KDW>
+template <int U, int D, int KDW, bool BY_CTA>
 __global__ void __launch_bounds__(SPMV_THREADS, 4)  // 64 registers: four CTAs per SM
 k_mhdc_spmv_mixed(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
                   const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
@@ -591,7 +591,9 @@ k_mhdc_spmv_mixed(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
 {
     const int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5);
     if (w >= n_tiles) return;
-    if (w % KDW == KDW - 1 &&
+    // BY_CTA: whole CTAs are emulated, so no CTA waits on warps of the other kind
+    const int64_t unit = BY_CTA ? (int64_t)blockIdx.x : w;
+    if (unit % KDW == KDW - 1 &&
         dw_tile_x64<U, D>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_dw, csr_row_ptr, csr_col, csr_dw,
                           x, y))
         return;
@@ -970,8 +972,8 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
 
 int launch_mixed(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_t stream)
 {
-    constexpr int RWs[3] = {128, 128, 64};
-    const int rw = RWs[shape];
+    (void)shape;
+    const int rw = 128;
     int32_t tpb = (int32_t)((A->n_b + rw - 1) / rw);
     int64_t tiles = (int64_t)tpb * A->n_blocks;
     const int64_t grid = (tiles + SPMV_WARPS - 1) / SPMV_WARPS;
@@ -982,9 +984,9 @@ int launch_mixed(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStre
             (const double *)d_x, (double *)d_y);
     };
     switch (shape) {
-    case 0: args(k_mhdc_spmv_mixed<2, 2, 4>); break;
-    case 1: args(k_mhdc_spmv_mixed<2, 2, 8>); break;
-    default: args(k_mhdc_spmv_mixed<1, 2, 4>); break;
+    case 0: args(k_mhdc_spmv_mixed<2, 2, 4, false>); break;
+    case 1: args(k_mhdc_spmv_mixed<2, 2, 4, true>); break;
+    default: args(k_mhdc_spmv_mixed<2, 2, 8, true>); break;
     }
     MHDC_LAUNCH_CHECK("k_mhdc_spmv_mixed");
     return MHDC_OK;
