@@ -302,6 +302,19 @@ k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
 // significant bits (half-up on the magnitude), lo = x - hi (exact, at most 29
 // bits) rounded to FP32.  Any nonzero |x| outside [2^DW_EMIN, 2^DW_EMAX] or
 // non-finite raises the epoch's flag so that the product falls back to FP64.
+// RN(d) for |d| < 2^29 on the FP32 pipe: d = dh 2^15 + dl with dl in
+// [0, 2^15) and |dh| < 2^14, each half exact in FP32 by the magic-number
+// construction (1.5 * 2^23 + dh, 2^23 + dl), and one FMA rounds the exact sum
+// once.  (On GB300 the int-to-float conversion shares the slow FP64 pipe.)
+__device__ __forceinline__ float i29_to_float_rn(int32_t d)
+{
+    const int32_t dh = d >> 15;  // floor(d / 2^15)
+    const int32_t dl = d & 0x7FFF;
+    const float fh = __fsub_rn(__int_as_float(0x4B400000 + dh), 12582912.0f);
+    const float fl = __fsub_rn(__int_as_float(0x4B000000 + dl), 8388608.0f);
+    return __fmaf_rn(fh, 32768.0f, fl);
+}
+
 __device__ __forceinline__ bool split_dw(double xd, float2 &o)
 {
     const unsigned long long u = (unsigned long long)__double_as_longlong(xd);
@@ -317,7 +330,7 @@ __device__ __forceinline__ bool split_dw(double xd, float2 &o)
                         (uint32_t)((magr >> 29) & 0x7FFFFFu);
     const int32_t d = (int32_t)(long long)(mag - magr);  // x - hi in units of ulp(x)
     // lo = d * 2^(E - 52): |d| < 2^29, E - 52 >= DW_EMIN - 52 > -126
-    float lo = __fmul_rn(__int2float_rn(d), __uint_as_float((uint32_t)(E - 52 + 127) << 23));
+    float lo = __fmul_rn(i29_to_float_rn(d), __uint_as_float((uint32_t)(E - 52 + 127) << 23));
     if (sign) lo = -lo;
     o = make_float2(__uint_as_float(hb), lo);
     return true;
