@@ -711,7 +711,7 @@ def main():
     info = H.info
     accuracy = None
     if best_variant >= mh.FIRST_EMULATED_VARIANT:
-        # emulated or mixed arithmetic: its distance from the native FP64
+        # emulated arithmetic: its distance from the native FP64
         # product, per row relative to sum_j |a_ij||x_j| (not timed)
         y_nat = torch.empty_like(y)
         absr = torch.empty_like(y)
@@ -725,12 +725,11 @@ def main():
         accuracy = {"max_row_err_vs_native_over_sum_abs": rel, "tolerance": 1e-12,
                     "bound": 7e-13, "within": rel <= 1e-12}
         log(f"accuracy of variant {best_variant}: {accuracy}")
-    launches_per_step = 2 if mh.FIRST_EMULATED_VARIANT <= best_variant < mh.FIRST_MIXED_VARIANT else 1
+    launches_per_step = 2 if best_variant >= mh.FIRST_EMULATED_VARIANT else 1
     kernel_name = ("k_mhdc_spmv<double>" if best_variant < 6 else
                    "k_mhdc_spmv_tma<double>" if best_variant < mh.FIRST_EMULATED_VARIANT else
                    "k_split_x + k_mhdc_spmv_dw" if best_variant < 13 else
-                   "k_split_x + k_mhdc_spmv_tma_dw" if best_variant < mh.FIRST_MIXED_VARIANT else
-                   "k_mhdc_spmv_mixed")
+                   "k_split_x + k_mhdc_spmv_tma_dw")
 
     peak, peak_src = measured_peak()
     vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
@@ -891,7 +890,7 @@ def main():
         # native FP64: every slot is an FMA on the FP64 pipe, which bounds the kernel
         roofline = {"bound": "alu", **alu, **common, "hbm": hbm}
     else:
-        # emulated / mixed: the FP32 pipe takes part of the arithmetic, HBM is the bound
+        # emulated FP64: the FP32 pipe does the arithmetic, HBM is the bound
         roofline = {"bound": "hbm", **{k: hbm[k] for k in ("achieved", "peak", "unit", "frac")},
                     **common, "bytes_per_launch": info["bytes_model"], "peak_source": peak_src,
                     "read_only_probe_gbs": read_ceiling,

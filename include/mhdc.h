@@ -192,19 +192,13 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  * product (10-12 in registers, 13-15 streamed by TMA like 6-9) with pairs of
  * FP32 numbers (values and x split into hi + lo, about
  * 49 significant bits; products and sums by error-free transformations): on
- * GB300 the FP64 pipe is about 64x slower than FP32, and this keeps the
- * product bound by memory.  Their per-row error stays below
+ * GB300 the FP64 pipe is about 64x slower than FP32, and these variants move
+ * the arithmetic to the FP32 pipe.  Their per-row error stays below
  * 7e-13 * sum_j |a_ij||x_j| (inside the FP64 tolerance 1e-12) as long as every
  * nonzero |a_ij| and |x_j| lies in [2^-51, 2^60] and a row has at most 64
  * terms; the handle checks its values at build and each product checks x on
  * the device, and outside that window the product runs the native FP64 path
  * (variant -1's arithmetic) instead.
- * Variants 16-18 (FP64 handles only) mix the two: one warp tile in 4 (16),
- * one CTA in 4 (17) or one CTA in 8 (18) runs the emulated arithmetic on the
- * FP32 pipe, splitting x as it loads it, while the other tiles run the native
- * FP64 tile, so both pipes work at once.  Rows of emulated tiles carry the emulated error bound
- * above, the others are native FP64; an emulated tile that meets an x
- * outside the window is recomputed natively by the same warp.
  *
  * mhdc_set_variant -- use variant v for this handle (-1: default chosen from n_b).
  * mhdc_tune        -- time every variant on (d_x, d_y) (overwriting d_y), keep
@@ -212,7 +206,7 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  *                     times_us is not NULL, each variant's mean time in
  *                     microseconds to times_us[MHDC_NUM_VARIANTS].  Synchronous.
  */
-#define MHDC_NUM_VARIANTS 19
+#define MHDC_NUM_VARIANTS 16
 int mhdc_set_variant(mhdc_handle A, int32_t v);
 int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *best,
               float *times_us);

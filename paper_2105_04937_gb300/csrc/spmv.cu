@@ -473,148 +473,6 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
 }
 
 // ---------------------------------------------------------------------------
-// Mixed product (variants 16-18 of FP64 handles): one warp tile in KDW runs
-// the emulated arithmetic on the FP32 pipe while the others run the native
-// FP64 tile, so both pipes work at once.  The emulated tiles split x into
-// FP32 pairs as they load it (split_dw, no separate pass over x); a tile that
-// meets an x outside the window is redone natively by the same warp.  Rows
-// of emulated tiles carry the error bound above, the others native FP64.
-// ---------------------------------------------------------------------------
-template <int U, int D>
-__device__ __forceinline__ bool
-dw_tile_x64(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restrict__ dia_ptr,
-            const int32_t *__restrict__ dia_offset, const float2 *__restrict__ dia_dw,
-            const int32_t *__restrict__ csr_row_ptr, const int32_t *__restrict__ csr_col,
-            const float2 *__restrict__ csr_dw, const double *__restrict__ x,
-            double *__restrict__ y)
-{
-    constexpr int V = 2;
-    constexpr int RW = 32 * V * U;
-    const int lane = threadIdx.x & 31;
-    const int64_t ib = w / tpb;
-    const int32_t tw = (int32_t)(w - ib * tpb) * RW;
-    const int64_t r0 = ib * (int64_t)n_b;
-    const int32_t rows = (int32_t)((n - r0 < n_b) ? (n - r0) : n_b);
-    if (tw >= rows) return true;  // warp-uniform
-    const bool full = tw + RW <= rows;
-    const bool x_al = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
-    bool ok = true;
-    int32_t tl[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) tl[u] = tw + (u * 32 + lane) * V;
-    float sh[U][V], sl[U][V];
-#pragma unroll
-    for (int u = 0; u < U; u++)
-#pragma unroll
-        for (int m = 0; m < V; m++) sh[u][m] = sl[u][m] = 0.f;
-
-    {
-        const int32_t tend = full ? tw + RW : rows;
-        if (csr_row_ptr[r0 + tw] != csr_row_ptr[r0 + tend]) {
-#pragma unroll
-            for (int u = 0; u < U; u++)
-#pragma unroll
-                for (int m = 0; m < V; m++) {
-                    const int32_t t = tl[u] + m;
-                    if (t < rows) {
-                        const int64_t i = r0 + t;
-                        const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
-                        for (int32_t k = a; k < b; k++) {
-                            float2 xs;
-                            ok &= split_dw(__ldg(x + __ldg(csr_col + k)), xs);
-                            dw::dw_fma(sh[u][m], sl[u][m], __ldg(csr_dw + k), xs);
-                        }
-                    }
-                }
-        }
-    }
-
-    const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
-    const int64_t xrow0 = r0 + tw;
-    int32_t p = p0;
-    auto group = [&](auto Dc) {
-        constexpr int DD = decltype(Dc)::value;
-        int64_t off[DD];
-#pragma unroll
-        for (int d = 0; d < DD; d++) off[d] = dia_offset[p + d];
-        float2 v[DD][U][V];
-#pragma unroll
-        for (int d = 0; d < DD; d++) {
-            const float2 *vp = dia_dw + (int64_t)(p + d) * n_b;
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                if (full || tl[u] < rows) {
-                    const uint4 r = ld_stream16(vp + tl[u]);
-                    memcpy(v[d][u], &r, 16);
-                } else {
-                    v[d][u][0] = v[d][u][1] = make_float2(0.f, 0.f);
-                }
-            }
-        }
-        double xv[DD][U][V];
-#pragma unroll
-        for (int d = 0; d < DD; d++) {
-            const int64_t jw = xrow0 + off[d];
-            if (full && jw >= 0 && jw + RW <= n) {
-                const bool al = x_al && (jw & 1) == 0;
-#pragma unroll
-                for (int u = 0; u < U; u++) load_x<double, V>(x, jw + (tl[u] - tw), al, xv[d][u]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < U; u++)
-#pragma unroll
-                    for (int m = 0; m < V; m++) {
-                        const int64_t jm = jw + (tl[u] - tw) + m;
-                        xv[d][u][m] = (tl[u] + m < rows && jm >= 0 && jm < n) ? __ldg(x + jm) : 0.0;
-                    }
-            }
-        }
-#pragma unroll
-        for (int d = 0; d < DD; d++)
-#pragma unroll
-            for (int u = 0; u < U; u++)
-#pragma unroll
-                for (int m = 0; m < V; m++) {
-                    float2 xs;
-                    ok &= split_dw(xv[d][u][m], xs);
-                    dw::dw_fma(sh[u][m], sl[u][m], v[d][u][m], xs);
-                }
-        p += DD;
-    };
-    for (; p + D <= p1;) group(std::integral_constant<int, D>{});
-    for (; p < p1;) group(std::integral_constant<int, 1>{});
-
-    if (__any_sync(0xffffffffu, !ok)) return false;  // x outside the window: redo natively
-#pragma unroll
-    for (int u = 0; u < U; u++)
-#pragma unroll
-        for (int m = 0; m < V; m++)
-            if (tl[u] + m < rows) y[r0 + tl[u] + m] = dw::f32_to_f64(sh[u][m]) + dw::f32_to_f64(sl[u][m]);
-    return true;
-}
-
-template <int U, int D, int KDW, bool BY_CTA>
-__global__ void __launch_bounds__(SPMV_THREADS, 4)  // 64 registers: four CTAs per SM
-k_mhdc_spmv_mixed(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
-                  const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
-                  const double *__restrict__ dia_val, const int32_t *__restrict__ csr_row_ptr,
-                  const int32_t *__restrict__ csr_col, const double *__restrict__ csr_val,
-                  const float2 *__restrict__ dia_dw, const float2 *__restrict__ csr_dw,
-                  const double *__restrict__ x, double *__restrict__ y)
-{
-    const int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5);
-    if (w >= n_tiles) return;
-    // BY_CTA: whole CTAs are emulated, so no CTA waits on warps of the other kind
-    const int64_t unit = BY_CTA ? (int64_t)blockIdx.x : w;
-    if (unit % KDW == KDW - 1 &&
-        dw_tile_x64<U, D>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_dw, csr_row_ptr, csr_col, csr_dw,
-                          x, y))
-        return;
-    reg_tile<double, U, D, true>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_val, csr_row_ptr,
-                                 csr_col, csr_val, x, y);
-}
-
-// ---------------------------------------------------------------------------
 // SpMM: Y = A X for k right-hand sides (row-major X, Y), the M-HDC kernel of
 // Fig. 13 with each scalar x_j replaced by row j of X.  A lane owns U rows
 // (r, r + 32, ...) of a warp tile and KC columns [c0, c0 + KC) of Y; per
@@ -983,35 +841,8 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
     return MHDC_OK;
 }
 
-int launch_mixed(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_t stream)
-{
-    (void)shape;
-    const int rw = 128;
-    int32_t tpb = (int32_t)((A->n_b + rw - 1) / rw);
-    int64_t tiles = (int64_t)tpb * A->n_blocks;
-    const int64_t grid = (tiles + SPMV_WARPS - 1) / SPMV_WARPS;
-    auto args = [&](auto kern) {
-        kern<<<(unsigned)grid, SPMV_THREADS, 0, stream>>>(
-            A->n, A->n_b, tpb, tiles, A->dia_ptr, A->dia_offset, (const double *)A->dia_val,
-            A->csr_row_ptr, A->csr_col, (const double *)A->csr_val, A->dia_dw, A->csr_dw,
-            (const double *)d_x, (double *)d_y);
-    };
-    switch (shape) {
-    case 0: args(k_mhdc_spmv_mixed<2, 2, 4, false>); break;
-    case 1: args(k_mhdc_spmv_mixed<2, 2, 4, true>); break;
-    default: args(k_mhdc_spmv_mixed<2, 2, 8, true>); break;
-    }
-    MHDC_LAUNCH_CHECK("k_mhdc_spmv_mixed");
-    return MHDC_OK;
-}
-
 int launch_variant(mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStream_t stream)
 {
-    if (id >= FIRST_MIXED_VARIANT) {
-        if (A->dw_ok && A->dtype == MHDC_F64 && (A->n_b % 2) == 0)
-            return launch_mixed(A, id - FIRST_MIXED_VARIANT, d_x, d_y, stream);
-        id = -1;
-    }
     if (id >= FIRST_DW_VARIANT) {
         if (A->dw_ok && A->dtype == MHDC_F64 && (A->n_b % 2) == 0) {
             if (id < FIRST_TMA_DW_VARIANT) return launch_dw(A, id - FIRST_DW_VARIANT, d_x, d_y, stream);
