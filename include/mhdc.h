@@ -63,7 +63,9 @@ typedef struct {
     int32_t dtype;         /* enum mhdc_dtype */
     int32_t mode;          /* enum mhdc_mode */
     int32_t variant;       /* SpMV tile shape in use (-1: default) */
-    int32_t emulated_ok;   /* FP64 handle whose values allow variants 10-12 */
+    int32_t emulated_ok;   /* 1: FP64 handle whose values allow variants 10-15, 0: not,
+                              -1: not known yet (the FP32-pair arrays are made on first
+                              use: mhdc_set_variant(v >= 10) or mhdc_tune) */
     int32_t reserved;
     double theta;          /* density threshold used */
     double alpha;          /* filling rate: (nnz - nnz_rem) / (P * n_b)   (Sec. 5.3.3) */
@@ -201,6 +203,9 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  * (variant -1's arithmetic) instead.
  *
  * mhdc_set_variant -- use variant v for this handle (-1: default chosen from n_b).
+ *                     The first v >= 10 on an FP64 handle makes its FP32-pair
+ *                     arrays (device memory as large as dia_val and csr_val)
+ *                     on the legacy default stream and waits for them.
  * mhdc_tune        -- time every variant on (d_x, d_y) (overwriting d_y), keep
  *                     the fastest in the handle, write its id to *best and, if
  *                     times_us is not NULL, each variant's mean time in
@@ -373,7 +378,7 @@ int mhdc_fma_bench(int32_t fp64, int32_t iters, void *d_out, void *stream);
  *
  * Limits: n <= 262144 rows and nnz <= 262144 stored entries; larger inputs
  * return MHDC_ERR_INVALID_ARG with a message saying so.  All temporaries live
- * in one file-scope device array of about 15 MB, which every GPU that loads
+ * in one file-scope device array of about 14 MB, which every GPU that loads
  * this library holds until the process exits.  The first call on a device
  * looks that array's address up (cudaGetSymbolAddress) with the device
  * current; make the first call on each device before any stream capture.

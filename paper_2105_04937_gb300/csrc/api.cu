@@ -162,7 +162,7 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out)
     out->dtype = A->dtype;
     out->mode = A->mode;
     out->variant = A->variant;
-    out->emulated_ok = A->dw_ok ? 1 : 0;
+    out->emulated_ok = !A->dw_prepared ? -1 : A->dw_ok ? 1 : 0;
     out->theta = A->theta;
     out->alpha = A->P ? (double)(A->nnz - A->nnz_rem) / ((double)A->P * (double)A->n_b) : 0.0;
     out->beta = A->nnz ? (double)A->nnz_rem / (double)A->nnz : 0.0;
@@ -177,6 +177,11 @@ int mhdc_set_variant(mhdc_handle A, int32_t v)
         set_error_msg("mhdc_set_variant: invalid argument");
         return MHDC_ERR_INVALID_ARG;
     }
+    if (v >= FIRST_DW_VARIANT) {  // the emulated arrays are made on first use
+        int rc = ensure_dw(A, nullptr);
+        if (rc != MHDC_OK) return rc;
+        MHDC_CUDA_TRY(cudaStreamSynchronize(nullptr));
+    }
     A->variant = v;
     return MHDC_OK;
 }
@@ -188,6 +193,8 @@ int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *
         set_error_msg("mhdc_tune: null argument");
         return MHDC_ERR_INVALID_ARG;
     }
+    int rc = ensure_dw(A, (cudaStream_t)stream);
+    if (rc != MHDC_OK) return rc;
     return tune_spmv(A, d_x, d_y, (cudaStream_t)stream, best, times_us);
 }
 

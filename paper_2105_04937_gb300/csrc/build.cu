@@ -1,6 +1,6 @@
 // CSR -> M-HDC / blocked HDC conversion on the device (Sec. 3.4, 4.3; Fig. 12).
 //
-// Steps (one stream, the host only reads sizes back to allocate):
+// Steps (one stream; the host only reads sizes back to allocate):
 //   1. k_validate       CSR checks (row_ptr bounds, columns in range, strictly
 //                       increasing inside a row).
 //   2. k_count_select   M-HDC: one CTA per row block counts N(d, ib) for every
@@ -10,13 +10,17 @@
 //                       N >= theta * rows(ib), and sorts the kept offsets.
 //      k_count_all      HDC: N(d) over the whole matrix in a dense array, kept
 //                       iff N >= 1 and N >= theta * n, compacted in order.
+//      Both walk 32 rows per warp with one lane per row, so lanes holding the
+//      same offset (rows of one stencil pattern) add their count with one
+//      atomic (warp match) instead of one each.
 //   3. scan             dia_ptr = exclusive prefix sum of the kept counts.
-//   4. k_scatter        one CTA per block: dia_val zero-filled, then every
-//                       entry either lands in dia_val[p * n_b + (i - r0)] or
-//                       is flagged for the remainder.
-//   5. scan + k_rem_*   remainder positions by an exclusive prefix sum of the
-//                       flags, which keeps the input order; csr_row_ptr[i] is
-//                       that prefix sum at row_ptr[i].
+//   4. k_scatter        dia_val assembled per (block, 256-row chunk) in a
+//                       shared-memory tile and written once, coalesced; the
+//                       entries left out are counted per row.
+//   5. scan + k_rem_fill csr_row_ptr = exclusive prefix sum of those counts;
+//                       the rows holding remainder entries copy them in input
+//                       order.
+// Temporaries are stream-ordered allocations from a pool of the library.
 #include <climits>
 #include <cstdio>
 #include <cmath>
@@ -74,35 +78,57 @@ __global__ void k_validate(int64_t n, const int32_t *__restrict__ rp,
     }
 }
 
-// Insert one occurrence of `off`.  With limit > 0 a new key first reserves
-// room (used < limit < capacity, so an empty slot always exists); the probe
-// loop is bounded by the capacity in any case.  Returns false on overflow.
+// Add c occurrences of `off`.  With limit > 0 a new key first reserves room
+// (used < limit < capacity, so an empty slot always exists); the probe loop
+// is bounded by the capacity in any case.  Returns false on overflow.
 __device__ __forceinline__ bool table_insert(volatile int32_t *keys, int32_t *cnt, uint32_t mask,
-                                             int32_t off, int *used, int limit)
+                                             int32_t off, int32_t c, int *used, int limit)
 {
     uint32_t h = mix32((uint32_t)off) & mask;
     for (uint32_t probe = 0; probe <= mask; probe++) {
         const int32_t k = keys[h];
         if (k == off) {
-            atomicAdd(&cnt[h], 1);
+            atomicAdd(&cnt[h], c);
             return true;
         }
         if (k == EMPTY_KEY) {
             if (limit > 0 && atomicAdd(used, 1) >= limit) return false;
             const int32_t prev = atomicCAS((int32_t *)&keys[h], EMPTY_KEY, off);
             if (prev == EMPTY_KEY) {
-                atomicAdd(&cnt[h], 1);
+                atomicAdd(&cnt[h], c);
                 return true;
             }
             if (limit > 0) atomicSub(used, 1);
             if (prev == off) {
-                atomicAdd(&cnt[h], 1);
+                atomicAdd(&cnt[h], c);
                 return true;
             }
         }
         h = (h + 1) & mask;
     }
     return false;
+}
+
+// One lane per row: lanes walk 32 consecutive rows [g0, g0 + 32) (clipped at
+// `end`) together, entry k of every row at step k, so rows of the same
+// pattern present the same offset d = j - i in the same step.  fn(has, i, k,
+// off) runs on every lane at every step (the loop is warp-uniform); has is
+// false for lanes past their row's end, which then carry off = EMPTY_KEY.
+template <typename F>
+__device__ __forceinline__ void rows_by_lane(int64_t g0, int64_t end, const int32_t *__restrict__ rp,
+                                             const int32_t *__restrict__ col, F fn)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = g0 + lane;
+    const bool live = i < end;
+    const int32_t a = live ? rp[i] : 0;
+    const int32_t len = live ? rp[i + 1] - a : 0;
+    const int32_t maxlen = __reduce_max_sync(0xffffffffu, len);
+    for (int32_t k = 0; k < maxlen; k++) {
+        const bool has = k < len;
+        const int32_t off = has ? __ldg(col + a + k) - (int32_t)i : EMPTY_KEY;
+        fn(has, i, a + k, off);
+    }
 }
 
 // Ascending bitonic sort of a[0..P2) (P2 a power of two) by the whole CTA.
@@ -175,17 +201,16 @@ k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
     }
     __syncthreads();
 
+    // lanes holding the same offset in a step add their count once (leader lane)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t i = r0 + warp; i < r0 + rows; i += CS_WARPS) {
-        if (ovf) break;
-        const int32_t a = rp[i], b = rp[i + 1];
-        for (int32_t k = a + lane; k < b; k += 32) {
-            const int32_t off = col[k] - (int32_t)i;
-            if (!table_insert(keys, cnt, mask, off, &used, limit)) {
+    for (int64_t g0 = r0 + 32 * warp; g0 < r0 + rows; g0 += 32 * CS_WARPS) {
+        if (__any_sync(0xffffffffu, ovf != 0)) break;  // warp-uniform exit
+        rows_by_lane(g0, r0 + rows, rp, col, [&](bool has, int64_t, int32_t, int32_t off) {
+            const unsigned grp = __match_any_sync(0xffffffffu, off);
+            if (has && lane == __ffs(grp) - 1 &&
+                !table_insert(keys, cnt, mask, off, __popc(grp), &used, limit))
                 ovf = 1;
-                break;
-            }
-        }
+        });
     }
     __syncthreads();
     if (ovf) {
@@ -258,11 +283,13 @@ k_count_hist(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t i = r0 + warp; i < r0 + rows; i += CS_WARPS) {
-        const int32_t a = rp[i], b = rp[i + 1];
-        for (int32_t k = a + lane; k < b; k += 32)
-            if (!table_insert(keys, cnt, mask, col[k] - (int32_t)i, &used, limit))
-                atomicAdd(&lost, 1ull);
+    for (int64_t g0 = r0 + 32 * warp; g0 < r0 + rows; g0 += 32 * CS_WARPS) {
+        rows_by_lane(g0, r0 + rows, rp, col, [&](bool has, int64_t, int32_t, int32_t off) {
+            const unsigned grp = __match_any_sync(0xffffffffu, off);
+            if (has && lane == __ffs(grp) - 1 &&
+                !table_insert(keys, cnt, mask, off, __popc(grp), &used, limit))
+                atomicAdd(&lost, (unsigned long long)__popc(grp));
+        });
     }
     __syncthreads();
     for (int64_t s = threadIdx.x; s < cap; s += blockDim.x) {
@@ -291,10 +318,12 @@ __global__ void k_count_all(int64_t n, const int32_t *__restrict__ rp,
 {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
-        const int32_t a = rp[i], b = rp[i + 1];
-        for (int32_t k = a + lane; k < b; k += 32)
-            atomicAdd(&cnt[(int64_t)col[k] - i + n - 1], 1);
+    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); 32 * g < n;
+         g += nw) {
+        rows_by_lane(32 * g, n, rp, col, [&](bool has, int64_t, int32_t, int32_t off) {
+            const unsigned grp = __match_any_sync(0xffffffffu, off);
+            if (has && lane == __ffs(grp) - 1) atomicAdd(&cnt[(int64_t)off + n - 1], __popc(grp));
+        });
     }
 }
 
@@ -345,61 +374,131 @@ __device__ __forceinline__ int64_t find_sorted(const int32_t *__restrict__ s, in
     return (lo < m && s[lo] == d) ? lo : -1;
 }
 
-// One CTA per row block: write the block's dia_offset, zero its dia_val,
-// then place every entry (warp per row).  flags[k] = 1 marks a remainder entry.
+// Scatter (Fig. 12 layout).  CTA c of row block ib handles the block's rows
+// [c * SC_ROWS, (c + 1) * SC_ROWS), one lane per row (rows_by_lane): an entry
+// whose offset is among the block's kept diagonals (binary search in the
+// sorted list, staged in shared memory) goes to dia_val slot (p, i - r0),
+// every other one is counted in rem_cnt[i].  The slots are assembled in a
+// shared-memory tile of S diagonals x RC rows, zero-filled first, and written
+// out one contiguous run per diagonal, so each dia_val element is written
+// once; when even 32 rows of S diagonals exceed the tile the CTA zero-fills
+// its slots in global memory and writes the entries in place.  The CTA of the
+// block's last rows also zero-fills the slots past the matrix end, and CTA 0
+// writes the block's dia_offset.
+constexpr int SC_THREADS = 256;
+constexpr int SC_ROWS = 256;
+constexpr int SC_SEL_MAX = 2048;                 // offsets staged in shared memory
+constexpr int SC_TILE_BYTES = 56 * 1024;
+constexpr size_t SC_SMEM = SC_SEL_MAX * sizeof(int32_t) + SC_TILE_BYTES;
+
 template <typename VT>
-__global__ void __launch_bounds__(256)
-k_scatter(int64_t n, int32_t n_b, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-          const double *__restrict__ val, const int32_t *__restrict__ dia_ptr,
-          const int32_t *__restrict__ sel_list, const int32_t *__restrict__ sel_base_rp,
-          int32_t *__restrict__ dia_offset, VT *__restrict__ dia_val, int32_t *__restrict__ flags)
+__global__ void __launch_bounds__(SC_THREADS)
+k_scatter(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
+          const int32_t *__restrict__ col, const double *__restrict__ val,
+          const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ sel_list,
+          const int32_t *__restrict__ sel_base_rp, int32_t *__restrict__ dia_offset,
+          VT *__restrict__ dia_val, int32_t *__restrict__ rem_cnt)
 {
-    const int64_t ib = blockIdx.x;
+    extern __shared__ __align__(16) unsigned char sc_smem[];
+    int32_t *sel_s = reinterpret_cast<int32_t *>(sc_smem);
+    VT *tile = reinterpret_cast<VT *>(sc_smem + SC_SEL_MAX * sizeof(int32_t));
+    const int64_t ib = blockIdx.x / cpb;
+    const int64_t c = blockIdx.x - ib * cpb;
     const int64_t r0 = ib * (int64_t)n_b;
     const int64_t rows = (n - r0 < n_b) ? (n - r0) : n_b;
+    const int64_t t0 = c * SC_ROWS;
+    if (t0 >= rows) return;  // CTA-uniform
+    const int64_t tn = (rows - t0 < SC_ROWS) ? (rows - t0) : SC_ROWS;
     const int64_t p0 = dia_ptr[ib];
     const int64_t S = dia_ptr[ib + 1] - p0;
     // M-HDC: the block's sorted list sits at sel_list + row_ptr[r0]; HDC: one shared list
-    const int32_t *sel = sel_list + (sel_base_rp ? (int64_t)sel_base_rp[r0] : 0);
-    for (int64_t s = threadIdx.x; s < S; s += blockDim.x) dia_offset[p0 + s] = sel[s];
+    const int32_t *selg = sel_list + (sel_base_rp ? (int64_t)sel_base_rp[r0] : 0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (c == 0)
+        for (int64_t q = threadIdx.x; q < S; q += SC_THREADS) dia_offset[p0 + q] = selg[q];
+    const bool sel_shared = S <= SC_SEL_MAX;
+    if (sel_shared)
+        for (int64_t q = threadIdx.x; q < S; q += SC_THREADS) sel_s[q] = selg[q];
+    const int32_t *sel = sel_shared ? sel_s : selg;
     VT *dv = dia_val + p0 * (int64_t)n_b;
-    for (int64_t s = threadIdx.x; s < S * (int64_t)n_b; s += blockDim.x) dv[s] = round_store<VT>(0.0);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int nw = blockDim.x >> 5;
-    for (int64_t i = r0 + (threadIdx.x >> 5); i < r0 + rows; i += nw) {
-        const int32_t a = rp[i], b = rp[i + 1];
-        for (int32_t k = a + lane; k < b; k += 32) {
-            const int32_t off = col[k] - (int32_t)i;
-            const int64_t p = find_sorted(sel, S, off);
-            if (p >= 0) {
-                dv[p * n_b + (i - r0)] = round_store<VT>(val[k]);
-                flags[k] = 0;
-            } else {
-                flags[k] = 1;
-            }
+    const VT zero = round_store<VT>(0.0);
+    // padding slots past the end of the matrix (last block only)
+    if (t0 + tn == rows && rows < n_b) {
+        const int64_t pad = n_b - rows;
+        for (int64_t q = threadIdx.x; q < S * pad; q += SC_THREADS) {
+            const int64_t p = q / pad;
+            dv[p * n_b + rows + (q - p * pad)] = zero;
         }
+    }
+    int64_t RC = S > 0 ? (int64_t)(SC_TILE_BYTES / sizeof(VT)) / S / 32 * 32 : SC_ROWS;
+    if (RC > SC_ROWS) RC = SC_ROWS;
+
+    if (RC < 32) {  // too many diagonals for the tile: in place in global memory
+        for (int64_t p = 0; p < S; p++)
+            for (int64_t t = threadIdx.x; t < tn; t += SC_THREADS) dv[p * n_b + t0 + t] = zero;
+        __syncthreads();
+        for (int64_t g = 32 * warp; g < tn; g += SC_THREADS) {
+            int32_t rem = 0;
+            rows_by_lane(r0 + t0 + g, r0 + t0 + tn, rp, col,
+                         [&](bool has, int64_t i, int32_t k, int32_t off) {
+                             if (!has) return;
+                             const int64_t p = find_sorted(sel, S, off);
+                             if (p >= 0) dv[p * n_b + (i - r0)] = round_store<VT>(val[k]);
+                             else rem++;
+                         });
+            if (g + lane < tn) rem_cnt[r0 + t0 + g + lane] = rem;
+        }
+        return;
+    }
+    __syncthreads();  // sel_s complete
+    for (int64_t u0 = 0; u0 < tn; u0 += RC) {
+        const int64_t un = (tn - u0 < RC) ? (tn - u0) : RC;
+        const int64_t rb = r0 + t0 + u0;  // first row of this sub-chunk
+        for (int64_t q = threadIdx.x; q < S * RC; q += SC_THREADS) tile[q] = zero;
+        __syncthreads();
+        for (int64_t g = 32 * warp; g < un; g += SC_THREADS) {
+            int32_t rem = 0;
+            rows_by_lane(rb + g, rb + un, rp, col, [&](bool has, int64_t i, int32_t k, int32_t off) {
+                if (!has) return;
+                const int64_t p = find_sorted(sel, S, off);
+                if (p >= 0) tile[p * RC + (i - rb)] = round_store<VT>(val[k]);
+                else rem++;
+            });
+            if (g + lane < un) rem_cnt[rb + g + lane] = rem;
+        }
+        __syncthreads();
+        for (int64_t p = 0; p < S; p++)
+            for (int64_t t = threadIdx.x; t < un; t += SC_THREADS)
+                dv[p * n_b + (rb - r0) + t] = tile[p * RC + t];
+        __syncthreads();
     }
 }
 
+// Remainder (Fig. 12, CSR part), one thread per row with remainder entries:
+// the entries whose offset is not among the block's diagonals (dia_offset,
+// sorted), in input order, at csr_row_ptr[i] onwards.
 template <typename VT>
-__global__ void k_rem_scatter(int64_t nnz, const int32_t *__restrict__ flags,
-                              const int32_t *__restrict__ pos, const int32_t *__restrict__ col,
-                              const double *__restrict__ val, int32_t *__restrict__ csr_col,
-                              VT *__restrict__ csr_val)
-{
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nnz || !flags[k]) return;
-    const int32_t q = pos[k];
-    csr_col[q] = col[k];
-    csr_val[q] = round_store<VT>(val[k]);
-}
-
-__global__ void k_rem_rowptr(int64_t n, const int32_t *__restrict__ rp,
-                             const int32_t *__restrict__ pos, int32_t *__restrict__ csr_row_ptr)
+__global__ void k_rem_fill(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
+                           const int32_t *__restrict__ col, const double *__restrict__ val,
+                           const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
+                           const int32_t *__restrict__ csr_row_ptr, int32_t *__restrict__ csr_col,
+                           VT *__restrict__ csr_val)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i <= n) csr_row_ptr[i] = pos[rp[i]];
+    if (i >= n) return;
+    int32_t q = csr_row_ptr[i];
+    if (q == csr_row_ptr[i + 1]) return;
+    const int64_t ib = i / n_b;
+    const int64_t p0 = dia_ptr[ib];
+    const int64_t S = dia_ptr[ib + 1] - p0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+        const int32_t c = col[k];
+        if (find_sorted(dia_offset + p0, S, c - (int32_t)i) < 0) {
+            csr_col[q] = c;
+            csr_val[q] = round_store<VT>(val[k]);
+            q++;
+        }
+    }
 }
 
 __global__ void k_block_bounds(int64_t n, int32_t n_b, int64_t n_blocks,
@@ -414,26 +513,61 @@ __global__ void k_block_bounds(int64_t n, int32_t n_b, int64_t n_blocks,
 
 inline unsigned grid_for(int64_t m, int threads) { return (unsigned)((m + threads - 1) / threads); }
 
-// Device buffer freed on scope exit.
+// Temporaries come from a stream-ordered pool owned by the library (one per
+// device, up to 4 GB kept mapped between builds): allocation and release are
+// queued on the build's stream instead of synchronising the device.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+int build_pool(cudaMemPool_t *out)
+{
+    int dev = 0;
+    MHDC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error_msg("mhdc_build: device index out of range");
+        return MHDC_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        MHDC_CUDA_TRY(cudaMemPoolCreate(&pool, &props));
+        unsigned long long keep = 4ull << 30;
+        MHDC_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return MHDC_OK;
+}
+
+// Device temporary released (stream-ordered) on scope exit.
 struct Buf {
     void *p = nullptr;
+    cudaStream_t st = nullptr;
     ~Buf()
     {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, st);
     }
     template <typename T>
     T *as() const { return static_cast<T *>(p); }
 };
 
-int dalloc(Buf &b, size_t bytes)
+int dalloc(Buf &b, size_t bytes, cudaStream_t st)
 {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(&b.p, bytes);
+    cudaMemPool_t pool;
+    int rc = build_pool(&pool);
+    if (rc != MHDC_OK) return rc;
+    cudaError_t e = cudaMallocFromPoolAsync(&b.p, bytes, pool, st);
     if (e != cudaSuccess) {
         b.p = nullptr;
-        set_error("cudaMalloc", e);
+        set_error("cudaMallocFromPoolAsync", e);
         return cuda_status(e);
     }
+    b.st = st;
     return MHDC_OK;
 }
 
@@ -456,38 +590,47 @@ int dalloc_raw(void **p, size_t bytes)
     } while (0)
 
 template <typename VT>
+int launch_scatter(int64_t n, int32_t n_b, int64_t nb, const int32_t *rp, const int32_t *col,
+                   const double *val, const int32_t *dia_ptr, const int32_t *sel_list,
+                   const int32_t *sel_base_rp, int32_t *dia_offset, VT *dia_val, int32_t *rem_cnt,
+                   cudaStream_t st)
+{
+    if (nb == 0) return MHDC_OK;
+    const int64_t cpb = ((int64_t)n_b + SC_ROWS - 1) / SC_ROWS;
+    MHDC_CUDA_TRY(cudaFuncSetAttribute(k_scatter<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SC_SMEM));
+    k_scatter<VT><<<(unsigned)(nb * cpb), SC_THREADS, SC_SMEM, st>>>(
+        n, n_b, (int32_t)cpb, rp, col, val, dia_ptr, sel_list, sel_base_rp, dia_offset, dia_val,
+        rem_cnt);
+    MHDC_LAUNCH_CHECK("k_scatter");
+    return MHDC_OK;
+}
+
+template <typename VT>
 int scatter_all(mhdc_matrix *A, const int32_t *rp, const int32_t *col, const double *val,
                 const int32_t *sel_list, const int32_t *sel_base_rp, cudaStream_t st)
 {
-    const int64_t n = A->n, nnz = A->nnz;
-    Buf flags, pos, scr;
-    RC(dalloc(flags, sizeof(int32_t) * (size_t)nnz));
-    RC(dalloc(pos, sizeof(int32_t) * (size_t)(nnz + 1)));
-    RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(nnz)));
-    if (A->n_blocks > 0) {
-        k_scatter<VT><<<(unsigned)A->n_blocks, 256, 0, st>>>(
-            n, A->n_b, rp, col, val, A->dia_ptr, sel_list, sel_base_rp, A->dia_offset,
-            static_cast<VT *>(A->dia_val), flags.as<int32_t>());
-        MHDC_LAUNCH_CHECK("k_scatter");
-    }
-    RC(exclusive_scan_i32(flags.as<int32_t>(), pos.as<int32_t>(), nnz, scr.as<int32_t>(), st));
+    const int64_t n = A->n;
+    Buf rem, scr;
+    RC(dalloc(rem, sizeof(int32_t) * (size_t)n, st));
+    RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(n), st));
+    RC(launch_scatter<VT>(n, A->n_b, A->n_blocks, rp, col, val, A->dia_ptr, sel_list, sel_base_rp,
+                          A->dia_offset, static_cast<VT *>(A->dia_val), rem.as<int32_t>(), st));
+    RC(dalloc_raw((void **)&A->csr_row_ptr, sizeof(int32_t) * (size_t)(n + 1)));
+    RC(exclusive_scan_i32(rem.as<int32_t>(), A->csr_row_ptr, n, scr.as<int32_t>(), st));
     int32_t nr = 0;
-    MHDC_CUDA_TRY(cudaMemcpyAsync(&nr, pos.as<int32_t>() + nnz, sizeof(int32_t),
-                                  cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaMemcpyAsync(&nr, A->csr_row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                  st));
     MHDC_CUDA_TRY(cudaStreamSynchronize(st));
     A->nnz_rem = nr;
     RC(dalloc_raw((void **)&A->csr_col, sizeof(int32_t) * (size_t)nr));
     RC(dalloc_raw(&A->csr_val, sizeof(VT) * (size_t)nr));
-    RC(dalloc_raw((void **)&A->csr_row_ptr, sizeof(int32_t) * (size_t)(n + 1)));
-    if (nnz > 0) {
-        k_rem_scatter<VT><<<grid_for(nnz, 256), 256, 0, st>>>(
-            nnz, flags.as<int32_t>(), pos.as<int32_t>(), col, val, A->csr_col,
+    if (nr > 0) {
+        k_rem_fill<VT><<<grid_for(n, 256), 256, 0, st>>>(
+            n, A->n_b, rp, col, val, A->dia_ptr, A->dia_offset, A->csr_row_ptr, A->csr_col,
             static_cast<VT *>(A->csr_val));
-        MHDC_LAUNCH_CHECK("k_rem_scatter");
+        MHDC_LAUNCH_CHECK("k_rem_fill");
     }
-    k_rem_rowptr<<<grid_for(n + 1, 256), 256, 0, st>>>(n, rp, pos.as<int32_t>(), A->csr_row_ptr);
-    MHDC_LAUNCH_CHECK("k_rem_rowptr");
-    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
     return MHDC_OK;
 }
 
@@ -496,9 +639,9 @@ int select_block_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Buf
 {
     const int64_t n = A->n, nnz = A->nnz, nb = A->n_blocks;
     Buf sel_cnt, ovf, scr;
-    RC(dalloc(sel_out, sizeof(int32_t) * (size_t)nnz));
-    RC(dalloc(sel_cnt, sizeof(int32_t) * (size_t)nb));
-    RC(dalloc(ovf, sizeof(int32_t) * (size_t)nb));
+    RC(dalloc(sel_out, sizeof(int32_t) * (size_t)nnz, st));
+    RC(dalloc(sel_cnt, sizeof(int32_t) * (size_t)nb, st));
+    RC(dalloc(ovf, sizeof(int32_t) * (size_t)nb, st));
     MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_select<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CS_SMEM));
     k_count_select<false><<<(unsigned)nb, CS_THREADS, CS_SMEM, st>>>(
@@ -508,7 +651,7 @@ int select_block_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Buf
     // blocks whose distinct offsets overflowed the shared table: redo with global tables
     std::vector<int32_t> h_ovf((size_t)nb), h_bounds((size_t)nb + 1);
     Buf bounds;
-    RC(dalloc(bounds, sizeof(int32_t) * (size_t)(nb + 1)));
+    RC(dalloc(bounds, sizeof(int32_t) * (size_t)(nb + 1), st));
     k_block_bounds<<<grid_for(nb + 1, 256), 256, 0, st>>>(n, A->n_b, nb, rp, bounds.as<int32_t>());
     MHDC_LAUNCH_CHECK("k_block_bounds");
     MHDC_CUDA_TRY(cudaMemcpyAsync(h_ovf.data(), ovf.p, sizeof(int32_t) * nb,
@@ -531,11 +674,11 @@ int select_block_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Buf
     }
     if (!ids.empty()) {
         Buf gk, gc, d_ids, d_lg, d_base;
-        RC(dalloc(gk, sizeof(int32_t) * (size_t)total));
-        RC(dalloc(gc, sizeof(int32_t) * (size_t)total));
-        RC(dalloc(d_ids, sizeof(int32_t) * ids.size()));
-        RC(dalloc(d_lg, sizeof(int32_t) * lg.size()));
-        RC(dalloc(d_base, sizeof(int64_t) * base.size()));
+        RC(dalloc(gk, sizeof(int32_t) * (size_t)total, st));
+        RC(dalloc(gc, sizeof(int32_t) * (size_t)total, st));
+        RC(dalloc(d_ids, sizeof(int32_t) * ids.size(), st));
+        RC(dalloc(d_lg, sizeof(int32_t) * lg.size(), st));
+        RC(dalloc(d_base, sizeof(int64_t) * base.size(), st));
         MHDC_CUDA_TRY(cudaMemcpyAsync(d_ids.p, ids.data(), sizeof(int32_t) * ids.size(),
                                       cudaMemcpyHostToDevice, st));
         MHDC_CUDA_TRY(cudaMemcpyAsync(d_lg.p, lg.data(), sizeof(int32_t) * lg.size(),
@@ -560,7 +703,7 @@ int select_block_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Buf
         }
     }
     RC(dalloc_raw((void **)&A->dia_ptr, sizeof(int32_t) * (size_t)(nb + 1)));
-    RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(nb)));
+    RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(nb), st));
     RC(exclusive_scan_i32(sel_cnt.as<int32_t>(), A->dia_ptr, nb, scr.as<int32_t>(), st));
     int32_t P = 0;
     MHDC_CUDA_TRY(cudaMemcpyAsync(&P, A->dia_ptr + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -575,10 +718,10 @@ int select_global_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Bu
     const int64_t n = A->n, nb = A->n_blocks;
     const int64_t m = 2 * n - 1;
     Buf cnt, flags, pos, scr;
-    RC(dalloc(cnt, sizeof(int32_t) * (size_t)m));
-    RC(dalloc(flags, sizeof(int32_t) * (size_t)m));
-    RC(dalloc(pos, sizeof(int32_t) * (size_t)(m + 1)));
-    RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(m)));
+    RC(dalloc(cnt, sizeof(int32_t) * (size_t)m, st));
+    RC(dalloc(flags, sizeof(int32_t) * (size_t)m, st));
+    RC(dalloc(pos, sizeof(int32_t) * (size_t)(m + 1), st));
+    RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(m), st));
     MHDC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * (size_t)m, st));
     k_count_all<<<1024, 256, 0, st>>>(n, rp, col, cnt.as<int32_t>());
     MHDC_LAUNCH_CHECK("k_count_all");
@@ -594,7 +737,7 @@ int select_global_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Bu
         set_error_msg("hdc_build: number of partial diagonals exceeds int32");
         return MHDC_ERR_UNSUPPORTED;
     }
-    RC(dalloc(sel_out, sizeof(int32_t) * (size_t)S));
+    RC(dalloc(sel_out, sizeof(int32_t) * (size_t)S, st));
     k_compact_global<<<grid_for(m, 256), 256, 0, st>>>(m, n, flags.as<int32_t>(),
                                                         pos.as<int32_t>(), sel_out.as<int32_t>());
     MHDC_LAUNCH_CHECK("k_compact_global");
@@ -610,7 +753,7 @@ int finish_stats(mhdc_matrix *A, cudaStream_t st)
     const int64_t nb = A->n_blocks;
     std::vector<int32_t> h((size_t)nb + 1);
     Buf bounds;
-    RC(dalloc(bounds, sizeof(int32_t) * (size_t)(nb + 1)));
+    RC(dalloc(bounds, sizeof(int32_t) * (size_t)(nb + 1), st));
     k_block_bounds<<<grid_for(nb + 1, 256), 256, 0, st>>>(A->n, A->n_b, nb, A->csr_row_ptr,
                                                           bounds.as<int32_t>());
     MHDC_LAUNCH_CHECK("k_block_bounds");
@@ -643,7 +786,7 @@ int feature_hist(int64_t n, const int32_t *rp, const int32_t *col, int32_t n_b,
 {
     const int64_t nb = (n + n_b - 1) / n_b;
     Buf d;
-    RC(dalloc(d, 20 * sizeof(unsigned long long)));
+    RC(dalloc(d, 20 * sizeof(unsigned long long), st));
     MHDC_CUDA_TRY(cudaMemsetAsync(d.p, 0, 20 * sizeof(unsigned long long), st));
     if (nb > 0) {
         MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -691,21 +834,28 @@ __global__ void k_split_dw(int64_t m, const double *__restrict__ v, float2 *__re
     out[k] = make_float2(h, __double2float_rn(d - (double)h));
 }
 
-// flag |= 1 if a nonzero value lies outside [2^DW_EMIN, 2^DW_EMAX] or is not finite.
+// flag |= 1 if a nonzero value lies outside [2^DW_EMIN, 2^DW_EMAX] or is not
+// finite (exponent field tests, one atomic per warp).
 __global__ void k_value_window(int64_t m, const double *__restrict__ v, int *flag)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= m) return;
-    const double a = fabs(v[k]);
-    if (a != 0.0 && !(a >= ldexp(1.0, DW_EMIN) && a <= ldexp(1.0, DW_EMAX))) atomicOr(flag, 1);
+    bool bad = false;
+    if (k < m) {
+        const unsigned long long u =
+            (unsigned long long)__double_as_longlong(v[k]) & 0x7FFFFFFFFFFFFFFFull;
+        const int E = (int)(u >> 52) - 1023;
+        bad = u != 0 && (E < DW_EMIN || E > DW_EMAX ||
+                         (E == DW_EMAX && (u & 0xFFFFFFFFFFFFFull) != 0));
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
-// out = max over i of ptr[i + 1] - ptr[i], i < m.
+// out = max over i of ptr[i + 1] - ptr[i], i < m (one atomic per warp).
 __global__ void k_max_diff(int64_t m, const int32_t *__restrict__ ptr, int *out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    atomicMax(out, ptr[i + 1] - ptr[i]);
+    const int d = __reduce_max_sync(0xffffffffu, i < m ? ptr[i + 1] - ptr[i] : 0);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, d);
 }
 
 }  // namespace
@@ -733,7 +883,7 @@ int prepare_dw(mhdc_matrix *A, cudaStream_t st)
     }
     MHDC_CUDA_TRY(cudaMemsetAsync(A->dw_flag, 0, sizeof(unsigned long long), st));
     Buf w;
-    RC(dalloc(w, 2 * sizeof(int)));
+    RC(dalloc(w, 2 * sizeof(int), st));
     MHDC_CUDA_TRY(cudaMemsetAsync(w.p, 0, 2 * sizeof(int), st));
     if (nd > 0) {
         k_split_dw<<<grid_for(nd, 256), 256, 0, st>>>(nd, (const double *)A->dia_val, A->dia_dw);
@@ -748,7 +898,7 @@ int prepare_dw(mhdc_matrix *A, cudaStream_t st)
     MHDC_LAUNCH_CHECK("k_split_dw");
     int h[3] = {0, 0, 0};
     Buf mx;
-    RC(dalloc(mx, 2 * sizeof(int)));
+    RC(dalloc(mx, 2 * sizeof(int), st));
     MHDC_CUDA_TRY(cudaMemsetAsync(mx.p, 0, 2 * sizeof(int), st));
     k_max_diff<<<grid_for(A->n_blocks, 256), 256, 0, st>>>(A->n_blocks, A->dia_ptr, mx.as<int>());
     k_max_diff<<<grid_for(A->n, 256), 256, 0, st>>>(A->n, A->csr_row_ptr, mx.as<int>() + 1);
@@ -759,6 +909,14 @@ int prepare_dw(mhdc_matrix *A, cudaStream_t st)
     A->dw_ok = h[0] == 0 && (h[1] + h[2]) <= DW_MAX_TERMS;
     A->bytes_device += (int64_t)sizeof(float2) * (nd + A->nnz_rem + A->n);
     return MHDC_OK;
+}
+
+int ensure_dw(mhdc_matrix *A, cudaStream_t st)
+{
+    if (A->dw_prepared) return MHDC_OK;
+    const int rc = prepare_dw(A, st);
+    A->dw_prepared = rc == MHDC_OK;
+    return rc;
 }
 
 static int build_into(mhdc_matrix *A, const int32_t *rp, const int32_t *col, const double *val,
@@ -793,7 +951,7 @@ static int build_into(mhdc_matrix *A, const int32_t *rp, const int32_t *col, con
     }
     {
         Buf err;
-        RC(dalloc(err, sizeof(int)));
+        RC(dalloc(err, sizeof(int), st));
         MHDC_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), st));
         if (n > 0) {
             k_validate<<<grid_for(n, 256), 256, 0, st>>>(n, rp, col, nnz, err.as<int>());
@@ -833,7 +991,6 @@ static int build_into(mhdc_matrix *A, const int32_t *rp, const int32_t *col, con
         break;
     }
     RC(finish_stats(A, st));
-    RC(prepare_dw(A, st));
     A->spmv_grid = spmv_grid_for(A);
     return MHDC_OK;
 }
@@ -885,15 +1042,14 @@ namespace {
 constexpr int64_t NA_MAX_NNZ = 1 << 18;   // stored entries
 constexpr int64_t NA_MAX_N = 1 << 18;     // rows (so at most 2^18 row blocks)
 constexpr int64_t NA_SCAN = 2 * ((NA_MAX_NNZ + 4095) / 4096) + 8;  // scan tile sums, with room
-// int32 words: err | sel_out | sel_cnt | ovf | ovf_pos | flags | pos | scan | keys | cnt | ids | lg | base(i64)
+// int32 words: err | sel_out | sel_cnt | ovf | ovf_pos | rem | scan | keys | cnt | ids | lg | base(i64)
 constexpr int64_t NA_ERR = 0;
 constexpr int64_t NA_SEL = 64;
 constexpr int64_t NA_SELCNT = NA_SEL + NA_MAX_NNZ;
 constexpr int64_t NA_OVF = NA_SELCNT + NA_MAX_N;
 constexpr int64_t NA_OVFPOS = NA_OVF + NA_MAX_N;
-constexpr int64_t NA_FLAGS = NA_OVFPOS + NA_MAX_N + 64;
-constexpr int64_t NA_POS = NA_FLAGS + NA_MAX_NNZ;
-constexpr int64_t NA_SCANS = NA_POS + NA_MAX_NNZ + 64;
+constexpr int64_t NA_REM = NA_OVFPOS + NA_MAX_N + 64;
+constexpr int64_t NA_SCANS = NA_REM + NA_MAX_N + 64;
 constexpr int64_t NA_KEYS = NA_SCANS + NA_SCAN + 64;
 constexpr int64_t NA_CNT = NA_KEYS + 4 * NA_MAX_NNZ;
 // a block overflows its shared table only with more than 12288 entries, so at
@@ -960,32 +1116,28 @@ int read_i32(const int32_t *d, int32_t *h, cudaStream_t st)
 }
 
 template <typename VT>
-int noalloc_fill(int64_t n, int32_t n_b, int64_t nb, int64_t nnz, const int32_t *rp,
-                 const int32_t *col, const double *val, int32_t *S, int32_t *dia_ptr,
-                 int32_t *dia_offset, void *dia_val, int32_t *csr_row_ptr, int32_t *csr_col,
-                 void *csr_val, int64_t cap_rem, int64_t *h_nnz_rem, cudaStream_t st)
+int noalloc_fill(int64_t n, int32_t n_b, int64_t nb, const int32_t *rp, const int32_t *col,
+                 const double *val, int32_t *S, int32_t *dia_ptr, int32_t *dia_offset,
+                 void *dia_val, int32_t *csr_row_ptr, int32_t *csr_col, void *csr_val,
+                 int64_t cap_rem, int64_t *h_nnz_rem, cudaStream_t st)
 {
-    int32_t *flags = S + NA_FLAGS, *pos = S + NA_POS;
-    if (nb > 0) {
-        k_scatter<VT><<<(unsigned)nb, 256, 0, st>>>(n, n_b, rp, col, val, dia_ptr, S + NA_SEL, rp,
-                                                    dia_offset, static_cast<VT *>(dia_val), flags);
-        MHDC_LAUNCH_CHECK("k_scatter");
-    }
-    RC(exclusive_scan_i32(flags, pos, nnz, S + NA_SCANS, st));
+    int32_t *rem = S + NA_REM;  // per-row remainder counts (n <= NA_MAX_N words)
+    RC(launch_scatter<VT>(n, n_b, nb, rp, col, val, dia_ptr, S + NA_SEL, rp, dia_offset,
+                          static_cast<VT *>(dia_val), rem, st));
+    RC(exclusive_scan_i32(rem, csr_row_ptr, n, S + NA_SCANS, st));
     int32_t nr = 0;
-    RC(read_i32(pos + nnz, &nr, st));
+    RC(read_i32(csr_row_ptr + n, &nr, st));
     *h_nnz_rem = nr;
     if (nr > cap_rem) {
         set_error_msg("mhdc_build_noalloc: csr_col/csr_val capacity too small (needed size in *h_nnz_rem)");
         return MHDC_ERR_INVALID_ARG;
     }
-    if (nnz > 0) {
-        k_rem_scatter<VT><<<grid_for(nnz, 256), 256, 0, st>>>(nnz, flags, pos, col, val, csr_col,
-                                                             static_cast<VT *>(csr_val));
-        MHDC_LAUNCH_CHECK("k_rem_scatter");
+    if (nr > 0) {
+        k_rem_fill<VT><<<grid_for(n, 256), 256, 0, st>>>(n, n_b, rp, col, val, dia_ptr, dia_offset,
+                                                         csr_row_ptr, csr_col,
+                                                         static_cast<VT *>(csr_val));
+        MHDC_LAUNCH_CHECK("k_rem_fill");
     }
-    k_rem_rowptr<<<grid_for(n + 1, 256), 256, 0, st>>>(n, rp, pos, csr_row_ptr);
-    MHDC_LAUNCH_CHECK("k_rem_rowptr");
     MHDC_CUDA_TRY(cudaStreamSynchronize(st));
     return MHDC_OK;
 }
@@ -1081,13 +1233,13 @@ int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double
     // 4-5. scatter and remainder compaction
     switch (dtype) {
     case MHDC_F64:
-        return noalloc_fill<double>(n, n_b, nb, nnz, rp, col, val, S, dia_ptr, dia_offset, dia_val,
+        return noalloc_fill<double>(n, n_b, nb, rp, col, val, S, dia_ptr, dia_offset, dia_val,
                                     csr_row_ptr, csr_col, csr_val, cap_rem, h_nnz_rem, st);
     case MHDC_F32:
-        return noalloc_fill<float>(n, n_b, nb, nnz, rp, col, val, S, dia_ptr, dia_offset, dia_val,
+        return noalloc_fill<float>(n, n_b, nb, rp, col, val, S, dia_ptr, dia_offset, dia_val,
                                    csr_row_ptr, csr_col, csr_val, cap_rem, h_nnz_rem, st);
     default:
-        return noalloc_fill<__nv_bfloat16>(n, n_b, nb, nnz, rp, col, val, S, dia_ptr, dia_offset,
+        return noalloc_fill<__nv_bfloat16>(n, n_b, nb, rp, col, val, S, dia_ptr, dia_offset,
                                            dia_val, csr_row_ptr, csr_col, csr_val, cap_rem,
                                            h_nnz_rem, st);
     }

@@ -34,6 +34,7 @@ struct mhdc_matrix {
     unsigned long long *dw_flag = nullptr;  // (epoch << 1) | (x outside the window)
     unsigned long long dw_epoch = 0;
     bool dw_ok = false;              // values inside the window, <= DW_MAX_TERMS terms per row
+    bool dw_prepared = false;        // the FP32-pair arrays above exist (made on first use)
 };
 
 // One matrix of a batch, as the batched kernel reads it (device memory).
@@ -123,6 +124,8 @@ constexpr int DW_EMIN = -51;
 constexpr int DW_EMAX = 60;
 constexpr int DW_MAX_TERMS = 64;
 int prepare_dw(mhdc_matrix *A, cudaStream_t st);
+// prepare_dw once per handle (the emulated variants and the tuner call it).
+int ensure_dw(mhdc_matrix *A, cudaStream_t st);
 int tune_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream, int32_t *best,
               float *times_us);
 

@@ -364,6 +364,8 @@ def test_emulated_fp64_meets_the_fp64_tolerance(mh):
     for name, A, n_b, x in _emulated_cases():
         for mode in ("block", "global"):
             h, M = check_build(mh, A, n_b, 0.6, "f64", mode)
+            assert h.info["emulated_ok"] == -1, name   # made on first use
+            mh.mhdc_set_variant(h, mh.FIRST_EMULATED_VARIANT)
             assert h.info["emulated_ok"] == 1, name
             for v in range(mh.FIRST_EMULATED_VARIANT, mh.MHDC_NUM_VARIANTS):
                 mh.mhdc_set_variant(h, v)
@@ -373,6 +375,7 @@ def test_emulated_fp64_meets_the_fp64_tolerance(mh):
 def test_emulated_fp64_full_size(mh):
     A = synth.config_matrix("stencil27_128")
     h, M = check_build(mh, A, 4096, 0.6, "f64")
+    mh.mhdc_set_variant(h, mh.FIRST_EMULATED_VARIANT)
     assert h.info["emulated_ok"] == 1
     for v in range(mh.FIRST_EMULATED_VARIANT, mh.MHDC_NUM_VARIANTS):
         mh.mhdc_set_variant(h, v)
@@ -398,6 +401,7 @@ def test_emulated_fp64_falls_back_outside_its_window(mh):
     t = torch()
     A = synth.config_matrix("stencil27_128", scale=0.25)
     h = build(mh, A, 4096, 0.6, "f64")
+    mh.mhdc_set_variant(h, mh.FIRST_EMULATED_VARIANT)
     assert h.info["emulated_ok"] == 1
     base = synth.uniform_vector(A.n, 6)
     for bad in (1e30, -3e19, 1e-20, 2.0 ** -60, float("inf"), float("nan")):
@@ -427,6 +431,7 @@ def test_emulated_fp64_disabled_by_values_or_row_length(mh):
     long_rows = synth.random_sparse(300, 0.3, seed=3)          # ~90 terms per row
     for M_ in (tiny, long_rows):
         h = build(mh, M_, 64, 0.6, "f64")
+        mh.mhdc_set_variant(h, mh.FIRST_EMULATED_VARIANT)
         assert h.info["emulated_ok"] == 0
         xd = t.from_numpy(synth.uniform_vector(M_.n, 2)).cuda()
         y0, ys = _native_and_emulated(mh, h, xd)
