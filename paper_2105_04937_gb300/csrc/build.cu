@@ -114,9 +114,11 @@ __device__ __forceinline__ bool table_insert(volatile int32_t *keys, int32_t *cn
 // pattern present the same offset d = j - i in the same step.  fn(has, i, k,
 // off) runs on every lane at every step (the loop is warp-uniform); has is
 // false for lanes past their row's end, which then carry off = EMPTY_KEY.
-template <typename F>
+// SHARED: the columns come from a shared-memory copy holding entries
+// [base, ...) instead of global memory.
+template <bool SHARED = false, typename F>
 __device__ __forceinline__ void rows_by_lane(int64_t g0, int64_t end, const int32_t *__restrict__ rp,
-                                             const int32_t *__restrict__ col, F fn)
+                                             const int32_t *__restrict__ col, int32_t base, F fn)
 {
     const int lane = threadIdx.x & 31;
     const int64_t i = g0 + lane;
@@ -126,7 +128,9 @@ __device__ __forceinline__ void rows_by_lane(int64_t g0, int64_t end, const int3
     const int32_t maxlen = __reduce_max_sync(0xffffffffu, len);
     for (int32_t k = 0; k < maxlen; k++) {
         const bool has = k < len;
-        const int32_t off = has ? __ldg(col + a + k) - (int32_t)i : EMPTY_KEY;
+        int32_t c = 0;
+        if (has) c = SHARED ? col[a + k - base] : __ldg(col + a + k);
+        const int32_t off = has ? c - (int32_t)i : EMPTY_KEY;
         fn(has, i, a + k, off);
     }
 }
@@ -152,23 +156,33 @@ __device__ void cta_bitonic_sort(int32_t *a, int64_t P2)
     }
 }
 
-// M-HDC selection for one row block per CTA.  GLOBAL_TABLE == false: the
-// table lives in shared memory and the CTA processes block blockIdx.x; a
-// block with more than HLIMIT distinct offsets sets overflow[ib] and stops.
-// GLOBAL_TABLE == true: CTA c processes block ids[c] with a table of
-// 2^tab_log2[c] slots at tab_base[c] in global memory.
-template <bool GLOBAL_TABLE>
+// M-HDC selection for one row block per CTA (block ids[blockIdx.x] when ids
+// is given, else blockIdx.x), in three table levels:
+//   level 1: <false, true>  shared table of at most SMALL_CAP slots, and each
+//            warp stages its 32 rows' columns in shared memory (coalesced
+//            loads) before walking them one lane per row;
+//   level 2: <false, false> shared table of at most HCAP slots, columns read
+//            from global memory, for the blocks level 1 could not hold;
+//   level 3: <true, false>  a table of 2^tab_log2[c] slots at tab_base[c] in
+//            global memory (at least twice the block's entries: cannot fill).
+// A shared table accepting no more distinct offsets sets overflow[ib] and the
+// CTA stops; the host then runs the next level for those blocks.
+constexpr int SMALL_CAP = 2048;
+constexpr int CW = 1024;  // staged columns per warp at level 1
+constexpr size_t CS_SMEM_SMALL = (3 * SMALL_CAP + CS_WARPS * CW) * sizeof(int32_t);
+
+template <bool GLOBAL_TABLE, bool STAGE>
 __global__ void __launch_bounds__(CS_THREADS)
 k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
                const int32_t *__restrict__ col, double theta, const int32_t *__restrict__ ids,
-               int32_t *gkeys, int32_t *gcnt, const int64_t *__restrict__ tab_base,
-               const int32_t *__restrict__ tab_log2, int32_t *sel_out, int32_t *sel_cnt,
-               int32_t *overflow)
+               int32_t cap_max, int32_t *gkeys, int32_t *gcnt,
+               const int64_t *__restrict__ tab_base, const int32_t *__restrict__ tab_log2,
+               int32_t *sel_out, int32_t *sel_cnt, int32_t *overflow)
 {
     extern __shared__ int32_t smem[];
     __shared__ int used, nsel;
     __shared__ volatile int ovf;
-    const int64_t ib = GLOBAL_TABLE ? (int64_t)ids[blockIdx.x] : (int64_t)blockIdx.x;
+    const int64_t ib = ids ? (int64_t)ids[blockIdx.x] : (int64_t)blockIdx.x;
     const int64_t r0 = ib * (int64_t)n_b;
     const int64_t rows = (n - r0 < n_b) ? (n - r0) : n_b;
     int32_t *keys, *cnt;
@@ -181,13 +195,13 @@ k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
         limit = 0;
     } else {
         // distinct offsets <= entries m of the block: a table of 2m slots
-        // (at least 64, at most HCAP) never fills unless m is large
+        // (at least 64, at most cap_max) never fills unless m is large
         const int64_t m = (int64_t)rp[r0 + rows] - rp[r0];
         cap = 64;
-        while (cap < 2 * m && cap < HCAP) cap <<= 1;
+        while (cap < 2 * m && cap < cap_max) cap <<= 1;
         keys = smem;
-        cnt = smem + HCAP;
-        limit = cap == HCAP ? HLIMIT : (int)cap - 1;
+        cnt = smem + cap_max;
+        limit = cap == cap_max ? cap_max / 4 * 3 : (int)cap - 1;
     }
     const uint32_t mask = (uint32_t)(cap - 1);
     for (int64_t s = threadIdx.x; s < cap; s += blockDim.x) {
@@ -203,18 +217,28 @@ k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
 
     // lanes holding the same offset in a step add their count once (leader lane)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *stage = smem + 3 * cap_max + warp * CW;
     for (int64_t g0 = r0 + 32 * warp; g0 < r0 + rows; g0 += 32 * CS_WARPS) {
         if (__any_sync(0xffffffffu, ovf != 0)) break;  // warp-uniform exit
-        rows_by_lane(g0, r0 + rows, rp, col, [&](bool has, int64_t, int32_t, int32_t off) {
+        auto count = [&](bool has, int64_t, int32_t, int32_t off) {
             const unsigned grp = __match_any_sync(0xffffffffu, off);
             if (has && lane == __ffs(grp) - 1 &&
                 !table_insert(keys, cnt, mask, off, __popc(grp), &used, limit))
                 ovf = 1;
-        });
+        };
+        const int64_t g1 = (g0 + 32 < r0 + rows) ? g0 + 32 : r0 + rows;
+        const int32_t e0 = rp[g0], e1 = rp[g1];
+        if (STAGE && e1 - e0 <= CW) {
+            for (int32_t e = e0 + lane; e < e1; e += 32) stage[e - e0] = __ldg(col + e);
+            __syncwarp();
+            rows_by_lane<true>(g0, g1, rp, stage, e0, count);
+            __syncwarp();
+        } else {
+            rows_by_lane(g0, g1, rp, col, 0, count);
+        }
     }
     __syncthreads();
-    if (ovf) {
-        if (threadIdx.x == 0) {
+    if (ovf) {        if (threadIdx.x == 0) {
             overflow[ib] = 1;
             sel_cnt[ib] = 0;
         }
@@ -223,7 +247,7 @@ k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
 
     // keep d iff N(d, ib) >= 1 and N >= theta * rows(ib)
     const double thr = theta * (double)rows;
-    int32_t *sel = GLOBAL_TABLE ? (sel_out + rp[r0]) : (smem + 2 * HCAP);
+    int32_t *sel = GLOBAL_TABLE ? (sel_out + rp[r0]) : (smem + 2 * cap_max);
     for (int64_t s = threadIdx.x; s < cap; s += blockDim.x) {
         const int32_t k = ((volatile int32_t *)keys)[s];
         if (k != EMPTY_KEY) {
@@ -284,7 +308,7 @@ k_count_hist(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t g0 = r0 + 32 * warp; g0 < r0 + rows; g0 += 32 * CS_WARPS) {
-        rows_by_lane(g0, r0 + rows, rp, col, [&](bool has, int64_t, int32_t, int32_t off) {
+        rows_by_lane(g0, r0 + rows, rp, col, 0, [&](bool has, int64_t, int32_t, int32_t off) {
             const unsigned grp = __match_any_sync(0xffffffffu, off);
             if (has && lane == __ffs(grp) - 1 &&
                 !table_insert(keys, cnt, mask, off, __popc(grp), &used, limit))
@@ -320,7 +344,7 @@ __global__ void k_count_all(int64_t n, const int32_t *__restrict__ rp,
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); 32 * g < n;
          g += nw) {
-        rows_by_lane(32 * g, n, rp, col, [&](bool has, int64_t, int32_t, int32_t off) {
+        rows_by_lane(32 * g, n, rp, col, 0, [&](bool has, int64_t, int32_t, int32_t off) {
             const unsigned grp = __match_any_sync(0xffffffffu, off);
             if (has && lane == __ffs(grp) - 1) atomicAdd(&cnt[(int64_t)off + n - 1], __popc(grp));
         });
@@ -375,21 +399,38 @@ __device__ __forceinline__ int64_t find_sorted(const int32_t *__restrict__ s, in
 }
 
 // Scatter (Fig. 12 layout).  CTA c of row block ib handles the block's rows
-// [c * SC_ROWS, (c + 1) * SC_ROWS), one lane per row (rows_by_lane): an entry
-// whose offset is among the block's kept diagonals (binary search in the
-// sorted list, staged in shared memory) goes to dia_val slot (p, i - r0),
-// every other one is counted in rem_cnt[i].  The slots are assembled in a
-// shared-memory tile of S diagonals x RC rows, zero-filled first, and written
-// out one contiguous run per diagonal, so each dia_val element is written
-// once; when even 32 rows of S diagonals exceed the tile the CTA zero-fills
-// its slots in global memory and writes the entries in place.  The CTA of the
-// block's last rows also zero-fills the slots past the matrix end, and CTA 0
-// writes the block's dia_offset.
+// [c * SC_ROWS, (c + 1) * SC_ROWS), in sub-chunks of RC rows whose dia_val
+// slots fit a shared-memory tile (S diagonals x RC rows, row stride RC + 1
+// against bank conflicts).  Threads take the sub-chunk's entries in order
+// (coalesced loads of col and val), find each entry's row by binary search
+// in the staged row pointers and its diagonal by binary search in the
+// block's sorted offsets, and either place the value in the tile or count
+// the entry in its row's remainder count.  The tile, zero-filled first, is
+// written out one contiguous run per diagonal, so each dia_val element is
+// written once.  When even 32 rows of S diagonals exceed the tile, the CTA
+// zero-fills its slots in global memory and writes the entries in place.  The
+// CTA of the block's last rows also zero-fills the slots past the matrix end,
+// and CTA 0 writes the block's dia_offset.
 constexpr int SC_THREADS = 256;
 constexpr int SC_ROWS = 256;
 constexpr int SC_SEL_MAX = 2048;                 // offsets staged in shared memory
-constexpr int SC_TILE_BYTES = 56 * 1024;
-constexpr size_t SC_SMEM = SC_SEL_MAX * sizeof(int32_t) + SC_TILE_BYTES;
+constexpr int SC_TILE_BYTES = 48 * 1024;
+// offsets | row pointers | remainder counts, then the tile at a 16-byte boundary
+constexpr size_t SC_HDR_BYTES =
+    ((SC_SEL_MAX + (SC_ROWS + 1) + SC_ROWS) * sizeof(int32_t) + 15) / 16 * 16;
+constexpr size_t SC_SMEM = SC_HDR_BYTES + SC_TILE_BYTES;
+
+// Largest r in [0, m) with a[r] <= e (a ascending, a[0] <= e).
+__device__ __forceinline__ int32_t row_of(const int32_t *a, int32_t m, int32_t e)
+{
+    int32_t lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (a[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 template <typename VT>
 __global__ void __launch_bounds__(SC_THREADS)
@@ -401,7 +442,9 @@ k_scatter(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
 {
     extern __shared__ __align__(16) unsigned char sc_smem[];
     int32_t *sel_s = reinterpret_cast<int32_t *>(sc_smem);
-    VT *tile = reinterpret_cast<VT *>(sc_smem + SC_SEL_MAX * sizeof(int32_t));
+    int32_t *rp_s = sel_s + SC_SEL_MAX;            // SC_ROWS + 1 row pointers
+    int32_t *rem_s = rp_s + SC_ROWS + 1;           // SC_ROWS counts
+    VT *tile = reinterpret_cast<VT *>(sc_smem + SC_HDR_BYTES);
     const int64_t ib = blockIdx.x / cpb;
     const int64_t c = blockIdx.x - ib * cpb;
     const int64_t r0 = ib * (int64_t)n_b;
@@ -413,7 +456,6 @@ k_scatter(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
     const int64_t S = dia_ptr[ib + 1] - p0;
     // M-HDC: the block's sorted list sits at sel_list + row_ptr[r0]; HDC: one shared list
     const int32_t *selg = sel_list + (sel_base_rp ? (int64_t)sel_base_rp[r0] : 0);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (c == 0)
         for (int64_t q = threadIdx.x; q < S; q += SC_THREADS) dia_offset[p0 + q] = selg[q];
     const bool sel_shared = S <= SC_SEL_MAX;
@@ -430,46 +472,47 @@ k_scatter(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
             dv[p * n_b + rows + (q - p * pad)] = zero;
         }
     }
-    int64_t RC = S > 0 ? (int64_t)(SC_TILE_BYTES / sizeof(VT)) / S / 32 * 32 : SC_ROWS;
-    if (RC > SC_ROWS) RC = SC_ROWS;
-
-    if (RC < 32) {  // too many diagonals for the tile: in place in global memory
-        for (int64_t p = 0; p < S; p++)
-            for (int64_t t = threadIdx.x; t < tn; t += SC_THREADS) dv[p * n_b + t0 + t] = zero;
-        __syncthreads();
-        for (int64_t g = 32 * warp; g < tn; g += SC_THREADS) {
-            int32_t rem = 0;
-            rows_by_lane(r0 + t0 + g, r0 + t0 + tn, rp, col,
-                         [&](bool has, int64_t i, int32_t k, int32_t off) {
-                             if (!has) return;
-                             const int64_t p = find_sorted(sel, S, off);
-                             if (p >= 0) dv[p * n_b + (i - r0)] = round_store<VT>(val[k]);
-                             else rem++;
-                         });
-            if (g + lane < tn) rem_cnt[r0 + t0 + g + lane] = rem;
-        }
-        return;
+    // rows per sub-chunk: a multiple of 32 with S * (RC + 1) values in the tile
+    int64_t RC = SC_ROWS;
+    if (S > 0) {
+        RC = ((int64_t)(SC_TILE_BYTES / sizeof(VT)) / S - 1) / 32 * 32;
+        if (RC > SC_ROWS) RC = SC_ROWS;
     }
-    __syncthreads();  // sel_s complete
+    const bool tiled = RC >= 32;
+    if (!tiled) RC = SC_ROWS;  // one sub-chunk, written in place
+    const int64_t ld = RC + 1;
+
     for (int64_t u0 = 0; u0 < tn; u0 += RC) {
         const int64_t un = (tn - u0 < RC) ? (tn - u0) : RC;
         const int64_t rb = r0 + t0 + u0;  // first row of this sub-chunk
-        for (int64_t q = threadIdx.x; q < S * RC; q += SC_THREADS) tile[q] = zero;
-        __syncthreads();
-        for (int64_t g = 32 * warp; g < un; g += SC_THREADS) {
-            int32_t rem = 0;
-            rows_by_lane(rb + g, rb + un, rp, col, [&](bool has, int64_t i, int32_t k, int32_t off) {
-                if (!has) return;
-                const int64_t p = find_sorted(sel, S, off);
-                if (p >= 0) tile[p * RC + (i - rb)] = round_store<VT>(val[k]);
-                else rem++;
-            });
-            if (g + lane < un) rem_cnt[rb + g + lane] = rem;
+        for (int64_t q = threadIdx.x; q <= un; q += SC_THREADS) rp_s[q] = rp[rb + q];
+        for (int64_t q = threadIdx.x; q < un; q += SC_THREADS) rem_s[q] = 0;
+        if (tiled) {
+            for (int64_t q = threadIdx.x; q < S * ld; q += SC_THREADS) tile[q] = zero;
+        } else {
+            for (int64_t p = 0; p < S; p++)
+                for (int64_t t = threadIdx.x; t < un; t += SC_THREADS) dv[p * n_b + (rb - r0) + t] = zero;
         }
         __syncthreads();
-        for (int64_t p = 0; p < S; p++)
-            for (int64_t t = threadIdx.x; t < un; t += SC_THREADS)
-                dv[p * n_b + (rb - r0) + t] = tile[p * RC + t];
+        const int32_t e0 = rp_s[0], e1 = rp_s[un];
+        for (int32_t e = e0 + (int32_t)threadIdx.x; e < e1; e += SC_THREADS) {
+            const int32_t r = row_of(rp_s, (int32_t)un, e);
+            const int32_t off = __ldg(col + e) - (int32_t)(rb + r);
+            const int64_t p = find_sorted(sel, S, off);
+            if (p < 0) {
+                atomicAdd(&rem_s[r], 1);
+            } else if (tiled) {
+                tile[p * ld + r] = round_store<VT>(__ldg(val + e));
+            } else {
+                dv[p * n_b + (rb - r0) + r] = round_store<VT>(__ldg(val + e));
+            }
+        }
+        __syncthreads();
+        for (int64_t q = threadIdx.x; q < un; q += SC_THREADS) rem_cnt[rb + q] = rem_s[q];
+        if (tiled)
+            for (int64_t p = 0; p < S; p++)
+                for (int64_t t = threadIdx.x; t < un; t += SC_THREADS)
+                    dv[p * n_b + (rb - r0) + t] = tile[p * ld + t];
         __syncthreads();
     }
 }
@@ -634,45 +677,75 @@ int scatter_all(mhdc_matrix *A, const int32_t *rp, const int32_t *col, const dou
     return MHDC_OK;
 }
 
+// Blocks whose overflow flag is set, with their entry counts (host lists).
+int overflowed_blocks(const int32_t *d_ovf, const int32_t *d_bounds, int64_t nb,
+                      std::vector<int32_t> &ids, std::vector<int64_t> &entries, cudaStream_t st)
+{
+    std::vector<int32_t> h_ovf((size_t)nb), h_bounds((size_t)nb + 1);
+    MHDC_CUDA_TRY(cudaMemcpyAsync(h_ovf.data(), d_ovf, sizeof(int32_t) * nb,
+                                  cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaMemcpyAsync(h_bounds.data(), d_bounds, sizeof(int32_t) * (nb + 1),
+                                  cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    ids.clear();
+    entries.clear();
+    for (int64_t b = 0; b < nb; b++) {
+        if (!h_ovf[b]) continue;
+        ids.push_back((int32_t)b);
+        entries.push_back((int64_t)h_bounds[b + 1] - h_bounds[b]);
+    }
+    return MHDC_OK;
+}
+
 int select_block_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Buf &sel_out,
                       cudaStream_t st)
 {
     const int64_t n = A->n, nnz = A->nnz, nb = A->n_blocks;
-    Buf sel_cnt, ovf, scr;
+    Buf sel_cnt, ovf, scr, bounds;
     RC(dalloc(sel_out, sizeof(int32_t) * (size_t)nnz, st));
     RC(dalloc(sel_cnt, sizeof(int32_t) * (size_t)nb, st));
     RC(dalloc(ovf, sizeof(int32_t) * (size_t)nb, st));
-    MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_select<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CS_SMEM));
-    k_count_select<false><<<(unsigned)nb, CS_THREADS, CS_SMEM, st>>>(
-        n, A->n_b, rp, col, A->theta, nullptr, nullptr, nullptr, nullptr, nullptr,
-        sel_out.as<int32_t>(), sel_cnt.as<int32_t>(), ovf.as<int32_t>());
-    MHDC_LAUNCH_CHECK("k_count_select");
-    // blocks whose distinct offsets overflowed the shared table: redo with global tables
-    std::vector<int32_t> h_ovf((size_t)nb), h_bounds((size_t)nb + 1);
-    Buf bounds;
     RC(dalloc(bounds, sizeof(int32_t) * (size_t)(nb + 1), st));
+    // level 1: small shared tables, staged columns
+    MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_select<false, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)CS_SMEM_SMALL));
+    k_count_select<false, true><<<(unsigned)nb, CS_THREADS, CS_SMEM_SMALL, st>>>(
+        n, A->n_b, rp, col, A->theta, nullptr, SMALL_CAP, nullptr, nullptr, nullptr, nullptr,
+        sel_out.as<int32_t>(), sel_cnt.as<int32_t>(), ovf.as<int32_t>());
+    MHDC_LAUNCH_CHECK("k_count_select<level 1>");
     k_block_bounds<<<grid_for(nb + 1, 256), 256, 0, st>>>(n, A->n_b, nb, rp, bounds.as<int32_t>());
     MHDC_LAUNCH_CHECK("k_block_bounds");
-    MHDC_CUDA_TRY(cudaMemcpyAsync(h_ovf.data(), ovf.p, sizeof(int32_t) * nb,
-                                  cudaMemcpyDeviceToHost, st));
-    MHDC_CUDA_TRY(cudaMemcpyAsync(h_bounds.data(), bounds.p, sizeof(int32_t) * (nb + 1),
-                                  cudaMemcpyDeviceToHost, st));
-    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
-    std::vector<int32_t> ids, lg;
-    std::vector<int64_t> base;
-    int64_t total = 0;
-    for (int64_t b = 0; b < nb; b++) {
-        if (!h_ovf[b]) continue;
-        const int64_t m = (int64_t)h_bounds[b + 1] - h_bounds[b];
-        int l = 10;
-        while (((int64_t)1 << l) < 2 * m) l++;
-        ids.push_back((int32_t)b);
-        lg.push_back(l);
-        base.push_back(total);
-        total += (int64_t)1 << l;
+    std::vector<int32_t> ids;
+    std::vector<int64_t> entries;
+    RC(overflowed_blocks(ovf.as<int32_t>(), bounds.as<int32_t>(), nb, ids, entries, st));
+    if (!ids.empty()) {
+        // level 2: the largest shared tables for the blocks level 1 could not hold
+        Buf d_ids;
+        RC(dalloc(d_ids, sizeof(int32_t) * ids.size(), st));
+        MHDC_CUDA_TRY(cudaMemcpyAsync(d_ids.p, ids.data(), sizeof(int32_t) * ids.size(),
+                                      cudaMemcpyHostToDevice, st));
+        MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_select<false, false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)CS_SMEM));
+        k_count_select<false, false><<<(unsigned)ids.size(), CS_THREADS, CS_SMEM, st>>>(
+            n, A->n_b, rp, col, A->theta, d_ids.as<int32_t>(), HCAP, nullptr, nullptr, nullptr,
+            nullptr, sel_out.as<int32_t>(), sel_cnt.as<int32_t>(), ovf.as<int32_t>());
+        MHDC_LAUNCH_CHECK("k_count_select<level 2>");
+        RC(overflowed_blocks(ovf.as<int32_t>(), bounds.as<int32_t>(), nb, ids, entries, st));
     }
     if (!ids.empty()) {
+        // level 3: global tables of at least twice the block's entries
+        std::vector<int32_t> lg;
+        std::vector<int64_t> base;
+        int64_t total = 0;
+        for (int64_t m : entries) {
+            int l = 10;
+            while (((int64_t)1 << l) < 2 * m) l++;
+            lg.push_back(l);
+            base.push_back(total);
+            total += (int64_t)1 << l;
+        }
         Buf gk, gc, d_ids, d_lg, d_base;
         RC(dalloc(gk, sizeof(int32_t) * (size_t)total, st));
         RC(dalloc(gc, sizeof(int32_t) * (size_t)total, st));
@@ -685,21 +758,17 @@ int select_block_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Buf
                                       cudaMemcpyHostToDevice, st));
         MHDC_CUDA_TRY(cudaMemcpyAsync(d_base.p, base.data(), sizeof(int64_t) * base.size(),
                                       cudaMemcpyHostToDevice, st));
-        k_count_select<true><<<(unsigned)ids.size(), CS_THREADS, 0, st>>>(
-            n, A->n_b, rp, col, A->theta, d_ids.as<int32_t>(), gk.as<int32_t>(),
+        k_count_select<true, false><<<(unsigned)ids.size(), CS_THREADS, 0, st>>>(
+            n, A->n_b, rp, col, A->theta, d_ids.as<int32_t>(), 0, gk.as<int32_t>(),
             gc.as<int32_t>(), d_base.as<int64_t>(), d_lg.as<int32_t>(), sel_out.as<int32_t>(),
             sel_cnt.as<int32_t>(), ovf.as<int32_t>());
-        MHDC_LAUNCH_CHECK("k_count_select<global>");
+        MHDC_LAUNCH_CHECK("k_count_select<level 3>");
         // a global table cannot overflow (its capacity is at least twice the
         // block's entries); check the flags anyway
-        MHDC_CUDA_TRY(cudaMemcpyAsync(h_ovf.data(), ovf.p, sizeof(int32_t) * nb,
-                                      cudaMemcpyDeviceToHost, st));
-        MHDC_CUDA_TRY(cudaStreamSynchronize(st));
-        for (int32_t b : ids) {
-            if (h_ovf[b]) {
-                set_error_msg("k_count_select: global table overflow");
-                return MHDC_ERR_DEVICE_CHECK;
-            }
+        RC(overflowed_blocks(ovf.as<int32_t>(), bounds.as<int32_t>(), nb, ids, entries, st));
+        if (!ids.empty()) {
+            set_error_msg("k_count_select: global table overflow");
+            return MHDC_ERR_DEVICE_CHECK;
         }
     }
     RC(dalloc_raw((void **)&A->dia_ptr, sizeof(int32_t) * (size_t)(nb + 1)));
@@ -1188,10 +1257,10 @@ int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double
     }
     // 2. selection per row block (shared-memory tables; overflowing blocks redone
     //    with tables in the scratch array)
-    MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_select<false>,
+    MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_select<false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CS_SMEM));
-    k_count_select<false><<<(unsigned)nb, CS_THREADS, CS_SMEM, st>>>(
-        n, n_b, rp, col, theta, nullptr, nullptr, nullptr, nullptr, nullptr, S + NA_SEL,
+    k_count_select<false, false><<<(unsigned)nb, CS_THREADS, CS_SMEM, st>>>(
+        n, n_b, rp, col, theta, nullptr, HCAP, nullptr, nullptr, nullptr, nullptr, S + NA_SEL,
         S + NA_SELCNT, S + NA_OVF);
     MHDC_LAUNCH_CHECK("k_count_select");
     RC(exclusive_scan_i32(S + NA_OVF, S + NA_OVFPOS, nb, S + NA_SCANS, st));
@@ -1207,8 +1276,8 @@ int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double
                                                               S + NA_OVFPOS, S + NA_IDS, S + NA_LG,
                                                               base);
         MHDC_LAUNCH_CHECK("k_noalloc_ovf_list");
-        k_count_select<true><<<(unsigned)novf, CS_THREADS, 0, st>>>(
-            n, n_b, rp, col, theta, S + NA_IDS, S + NA_KEYS, S + NA_CNT, base, S + NA_LG,
+        k_count_select<true, false><<<(unsigned)novf, CS_THREADS, 0, st>>>(
+            n, n_b, rp, col, theta, S + NA_IDS, 0, S + NA_KEYS, S + NA_CNT, base, S + NA_LG,
             S + NA_SEL, S + NA_SELCNT, S + NA_OVF);
         MHDC_LAUNCH_CHECK("k_count_select<global>");
     }
