@@ -337,17 +337,34 @@ k_count_hist(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
 }
 
 // HDC: N(d) for d in [-(n-1), n-1] at cnt[d + n - 1].
-__global__ void k_count_all(int64_t n, const int32_t *__restrict__ rp,
-                            const int32_t *__restrict__ col, int32_t *cnt)
+// Each warp stages its 32 rows' columns in shared memory (CW per warp) when
+// they fit, as level 1 of k_count_select does.
+constexpr int CA_THREADS = 256;
+constexpr size_t CA_SMEM = (CA_THREADS / 32) * CW * sizeof(int32_t);
+
+__global__ void __launch_bounds__(CA_THREADS)
+k_count_all(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t *cnt)
 {
+    extern __shared__ int32_t ca_smem[];
     const int lane = threadIdx.x & 31;
+    int32_t *stage = ca_smem + (threadIdx.x >> 5) * CW;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    auto count = [&](bool has, int64_t, int32_t, int32_t off) {
+        const unsigned grp = __match_any_sync(0xffffffffu, off);
+        if (has && lane == __ffs(grp) - 1) atomicAdd(&cnt[(int64_t)off + n - 1], __popc(grp));
+    };
     for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); 32 * g < n;
          g += nw) {
-        rows_by_lane(32 * g, n, rp, col, 0, [&](bool has, int64_t, int32_t, int32_t off) {
-            const unsigned grp = __match_any_sync(0xffffffffu, off);
-            if (has && lane == __ffs(grp) - 1) atomicAdd(&cnt[(int64_t)off + n - 1], __popc(grp));
-        });
+        const int64_t g0 = 32 * g, g1 = (g0 + 32 < n) ? g0 + 32 : n;
+        const int32_t e0 = rp[g0], e1 = rp[g1];
+        if (e1 - e0 <= CW) {
+            for (int32_t e = e0 + lane; e < e1; e += 32) stage[e - e0] = __ldg(col + e);
+            __syncwarp();
+            rows_by_lane<true>(g0, g1, rp, stage, e0, count);
+            __syncwarp();
+        } else {
+            rows_by_lane(g0, g1, rp, col, 0, count);
+        }
     }
 }
 
@@ -415,9 +432,12 @@ constexpr int SC_THREADS = 256;
 constexpr int SC_ROWS = 256;
 constexpr int SC_SEL_MAX = 2048;                 // offsets staged in shared memory
 constexpr int SC_TILE_BYTES = 48 * 1024;
-// offsets | row pointers | remainder counts, then the tile at a 16-byte boundary
+constexpr int SC_RID_MAX = 8192;                 // entries whose row index is tabulated
+constexpr int SC_UNROLL = 4;                     // entries in flight per thread
+// offsets | row pointers | remainder counts | row index per entry (uint8),
+// then the tile at a 16-byte boundary
 constexpr size_t SC_HDR_BYTES =
-    ((SC_SEL_MAX + (SC_ROWS + 1) + SC_ROWS) * sizeof(int32_t) + 15) / 16 * 16;
+    ((SC_SEL_MAX + (SC_ROWS + 1) + SC_ROWS) * sizeof(int32_t) + SC_RID_MAX + 15) / 16 * 16;
 constexpr size_t SC_SMEM = SC_HDR_BYTES + SC_TILE_BYTES;
 
 // Largest r in [0, m) with a[r] <= e (a ascending, a[0] <= e).
@@ -444,6 +464,7 @@ k_scatter(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
     int32_t *sel_s = reinterpret_cast<int32_t *>(sc_smem);
     int32_t *rp_s = sel_s + SC_SEL_MAX;            // SC_ROWS + 1 row pointers
     int32_t *rem_s = rp_s + SC_ROWS + 1;           // SC_ROWS counts
+    uint8_t *rid_s = reinterpret_cast<uint8_t *>(rem_s + SC_ROWS);  // row of each entry
     VT *tile = reinterpret_cast<VT *>(sc_smem + SC_HDR_BYTES);
     const int64_t ib = blockIdx.x / cpb;
     const int64_t c = blockIdx.x - ib * cpb;
@@ -495,16 +516,37 @@ k_scatter(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
         }
         __syncthreads();
         const int32_t e0 = rp_s[0], e1 = rp_s[un];
-        for (int32_t e = e0 + (int32_t)threadIdx.x; e < e1; e += SC_THREADS) {
-            const int32_t r = row_of(rp_s, (int32_t)un, e);
-            const int32_t off = __ldg(col + e) - (int32_t)(rb + r);
-            const int64_t p = find_sorted(sel, S, off);
-            if (p < 0) {
-                atomicAdd(&rem_s[r], 1);
-            } else if (tiled) {
-                tile[p * ld + r] = round_store<VT>(__ldg(val + e));
-            } else {
-                dv[p * n_b + (rb - r0) + r] = round_store<VT>(__ldg(val + e));
+        // row index of every entry, tabulated by its row's thread when they fit
+        const bool rid = e1 - e0 <= SC_RID_MAX;
+        if (rid) {
+            for (int64_t q = threadIdx.x; q < un; q += SC_THREADS)
+                for (int32_t e = rp_s[q]; e < rp_s[q + 1]; e++) rid_s[e - e0] = (uint8_t)q;
+            __syncthreads();
+        }
+        for (int32_t eb = e0 + (int32_t)threadIdx.x; eb < e1; eb += SC_UNROLL * SC_THREADS) {
+            int32_t cc[SC_UNROLL];
+            double vv[SC_UNROLL];
+#pragma unroll
+            for (int u = 0; u < SC_UNROLL; u++) {  // loads of SC_UNROLL entries in flight
+                const int32_t e = eb + u * SC_THREADS;
+                if (e < e1) {
+                    cc[u] = __ldg(col + e);
+                    vv[u] = __ldg(val + e);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < SC_UNROLL; u++) {
+                const int32_t e = eb + u * SC_THREADS;
+                if (e >= e1) break;
+                const int32_t r = rid ? (int32_t)rid_s[e - e0] : row_of(rp_s, (int32_t)un, e);
+                const int64_t p = find_sorted(sel, S, cc[u] - (int32_t)(rb + r));
+                if (p < 0) {
+                    atomicAdd(&rem_s[r], 1);
+                } else if (tiled) {
+                    tile[p * ld + r] = round_store<VT>(vv[u]);
+                } else {
+                    dv[p * n_b + (rb - r0) + r] = round_store<VT>(vv[u]);
+                }
             }
         }
         __syncthreads();
@@ -792,7 +834,9 @@ int select_global_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Bu
     RC(dalloc(pos, sizeof(int32_t) * (size_t)(m + 1), st));
     RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(m), st));
     MHDC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * (size_t)m, st));
-    k_count_all<<<1024, 256, 0, st>>>(n, rp, col, cnt.as<int32_t>());
+    // six CTAs per SM (shared memory allows seven), grid-stride over the row groups
+    k_count_all<<<(unsigned)(read_bench_grid() / 8 * 6), CA_THREADS, CA_SMEM, st>>>(n, rp, col,
+                                                                            cnt.as<int32_t>());
     MHDC_LAUNCH_CHECK("k_count_all");
     k_flag_global<<<grid_for(m, 256), 256, 0, st>>>(m, cnt.as<int32_t>(), A->theta * (double)n,
                                                      flags.as<int32_t>());
