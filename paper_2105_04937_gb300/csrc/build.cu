@@ -559,9 +559,10 @@ k_scatter(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
     }
 }
 
-// Remainder (Fig. 12, CSR part), one thread per row with remainder entries:
-// the entries whose offset is not among the block's diagonals (dia_offset,
-// sorted), in input order, at csr_row_ptr[i] onwards.
+// Remainder (Fig. 12, CSR part): a warp takes 32 rows and, for each of them
+// holding remainder entries, tests the row's entries 32 at a time (one lane
+// each) against the block's sorted offsets (dia_offset) and writes the ones
+// left out in input order from csr_row_ptr[i] on (ballot prefix counts).
 template <typename VT>
 __global__ void k_rem_fill(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
                            const int32_t *__restrict__ col, const double *__restrict__ val,
@@ -569,19 +570,35 @@ __global__ void k_rem_fill(int64_t n, int32_t n_b, const int32_t *__restrict__ r
                            const int32_t *__restrict__ csr_row_ptr, int32_t *__restrict__ csr_col,
                            VT *__restrict__ csr_val)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int32_t q = csr_row_ptr[i];
-    if (q == csr_row_ptr[i + 1]) return;
-    const int64_t ib = i / n_b;
-    const int64_t p0 = dia_ptr[ib];
-    const int64_t S = dia_ptr[ib + 1] - p0;
-    for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
-        const int32_t c = col[k];
-        if (find_sorted(dia_offset + p0, S, c - (int32_t)i) < 0) {
-            csr_col[q] = c;
-            csr_val[q] = round_store<VT>(val[k]);
-            q++;
+    const int lane = threadIdx.x & 31;
+    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane);
+    if (g0 >= n) return;  // warp-uniform
+    const int64_t i = g0 + lane;
+    const bool live = i < n;
+    const int32_t q0 = live ? csr_row_ptr[i] : 0;
+    const int32_t q1 = live ? csr_row_ptr[i + 1] : 0;
+    unsigned todo = __ballot_sync(0xffffffffu, live && q1 > q0);
+    while (todo) {
+        const int l = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t row = g0 + l;
+        int32_t q = __shfl_sync(0xffffffffu, q0, l);
+        const int64_t ib = row / n_b;
+        const int64_t p0 = dia_ptr[ib];
+        const int64_t S = dia_ptr[ib + 1] - p0;
+        const int32_t a = rp[row], b = rp[row + 1];
+        for (int32_t k0 = a; k0 < b; k0 += 32) {
+            const int32_t k = k0 + lane;
+            const bool in = k < b;
+            const int32_t c = in ? col[k] : 0;
+            const bool rem = in && find_sorted(dia_offset + p0, S, c - (int32_t)row) < 0;
+            const unsigned m = __ballot_sync(0xffffffffu, rem);
+            if (rem) {
+                const int32_t pos = q + __popc(m & ((1u << lane) - 1u));
+                csr_col[pos] = c;
+                csr_val[pos] = round_store<VT>(val[k]);
+            }
+            q += __popc(m);
         }
     }
 }
