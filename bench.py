@@ -695,37 +695,65 @@ def main():
     y = torch.empty(A.n, dtype=torch.float64, device="cuda")
 
     torch.cuda.synchronize()
+    # conversion: the first call of the process (loads the build kernels and
+    # creates the temporary pool) and the mean of five later ones
     tb = time.perf_counter()
     H = mh.mhdc_build(A.n, rp, col, val, N_B, THETA, "f64")
-    build_ms = (time.perf_counter() - tb) * 1e3
+    build_first_ms = (time.perf_counter() - tb) * 1e3
+    H.destroy()
+    torch.cuda.synchronize()
+    tb = time.perf_counter()
+    for _ in range(5):
+        H = mh.mhdc_build(A.n, rp, col, val, N_B, THETA, "f64")
+        H.destroy()
+    torch.cuda.synchronize()
+    build_ms = (time.perf_counter() - tb) * 1e3 / 5
+    H = mh.mhdc_build(A.n, rp, col, val, N_B, THETA, "f64")
     info = H.info
     log(f"built: P={info['P']} nnz_rem={info['nnz_rem']} alpha={info['alpha']:.3f} "
         f"beta={info['beta']:.4f} bytes_model={info['bytes_model']} in {build_ms:.1f} ms")
 
-    # the library's own autotuner picks the tile shape (not timed)
+    # the library's own autotuner times every tile shape (not timed); the
+    # headline keeps the fastest native FP64 one (FP64 arithmetic throughout)
+    # and reports the emulated variants beside it
+    emulated = None
     if args.variant is None:
-        best_variant, variant_us = mh.mhdc_tune(H, x, y)
+        _, variant_us = mh.mhdc_tune(H, x, y)
+        nat = variant_us[:mh.FIRST_EMULATED_VARIANT]
+        best_variant = int(np.argmin(nat))
+        emu = int(np.argmin(variant_us[mh.FIRST_EMULATED_VARIANT:])) + mh.FIRST_EMULATED_VARIANT
+        emulated = {"variant": emu, "tuner_us": round(variant_us[emu], 2),
+                    "native_tuner_us": round(variant_us[best_variant], 2)}
+        mh.mhdc_set_variant(H, best_variant)
     else:
         mh.mhdc_set_variant(H, args.variant)
         best_variant, variant_us = args.variant, []
     log(f"tuned: variant {best_variant}; per-variant us {[round(t, 2) for t in variant_us]}")
     info = H.info
     accuracy = None
-    if best_variant >= mh.FIRST_EMULATED_VARIANT:
-        # emulated arithmetic: its distance from the native FP64
-        # product, per row relative to sum_j |a_ij||x_j| (not timed)
+    acc_variant = best_variant if best_variant >= mh.FIRST_EMULATED_VARIANT else (
+        emulated["variant"] if emulated else None)
+    if acc_variant is not None:
+        # emulated arithmetic: its distance from the native FP64 product, per
+        # row relative to sum_j |a_ij||x_j| (not timed)
+        y_emu = torch.empty_like(y)
         y_nat = torch.empty_like(y)
         absr = torch.empty_like(y)
-        mh.mhdc_spmv(H, x, y)
+        mh.mhdc_set_variant(H, acc_variant)
+        mh.mhdc_spmv(H, x, y_emu)
         mh.mhdc_set_variant(H, -1)
         mh.mhdc_spmv(H, x, y_nat)
         mh.mhdc_set_variant(H, best_variant)
         mh.csr_spmv(A.n, rp, col, val.abs(), x.abs(), absr)
         torch.cuda.synchronize()
-        rel = float(((y - y_nat).abs() / absr.clamp_min(1e-300)).max())
-        accuracy = {"max_row_err_vs_native_over_sum_abs": rel, "tolerance": 1e-12,
-                    "bound": 7e-13, "within": rel <= 1e-12}
-        log(f"accuracy of variant {best_variant}: {accuracy}")
+        rel = float(((y_emu - y_nat).abs() / absr.clamp_min(1e-300)).max())
+        accuracy = {"variant": acc_variant, "max_row_err_vs_native_over_sum_abs": rel,
+                    "tolerance": 1e-12, "bound": 7e-13, "within": rel <= 1e-12}
+        log(f"accuracy of emulated variant {acc_variant}: {accuracy}")
+        del y_emu, y_nat, absr
+        if emulated:
+            emulated["accuracy"] = accuracy
+            accuracy = None if best_variant < mh.FIRST_EMULATED_VARIANT else accuracy
     launches_per_step = 2 if best_variant >= mh.FIRST_EMULATED_VARIANT else 1
     kernel_name = ("k_mhdc_spmv<double>" if best_variant < 6 else
                    "k_mhdc_spmv_tma<double>" if best_variant < mh.FIRST_EMULATED_VARIANT else
@@ -915,7 +943,9 @@ def main():
             "gpu_launches": args.steps * launches_per_step,
             "accuracy": accuracy,
             "clocks": clocks,
-            "build_ms": round(build_ms, 1),
+            "build_ms": round(build_ms, 2),
+            "build_first_ms": round(build_first_ms, 2),
+            "emulated_fp64": emulated,
             "baselines": extra,
             "rows": rows,
         }
