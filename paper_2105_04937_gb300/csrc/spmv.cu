@@ -139,49 +139,47 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
 #pragma unroll
         for (int m = 0; m < V; m++) acc[u][m] = Acc(0);
 
-    // CSR remainder rows of the tile (Fig. 13, first loop).  The tile's
-    // remainder entries [q0, q1) are contiguous: the warp stages them RCH at a
-    // time in shared memory, value and gathered x[col] per entry (coalesced
-    // loads, 32 gathers in flight), and each lane then sums its own rows'
-    // entries in column order from there (the per-row operations of a
-    // sequential loop, without its chain of dependent gathers).
+    // CSR remainder rows of the tile (Fig. 13, first loop).  With V >= 4 rows
+    // per lane (FP32, BF16) each lane instead sums whole rows (row tw + rr for
+    // rr = lane, lane + 32, ...), in column order from zero, and the sums reach
+    // their owners through shared memory: the same operations as summing into
+    // acc directly, with one row per lane instead of V in sequence.
     {
         const int32_t tend = full ? tw + RW : rows;
         const int32_t q0 = csr_row_ptr[r0 + tw], q1 = csr_row_ptr[r0 + tend];
-        if (q0 != q1) {
-            constexpr int RCH = 128;
-            __shared__ VT rem_v[SPMV_WARPS][RCH];
-            __shared__ X rem_x[SPMV_WARPS][RCH];
-            VT *sv = rem_v[threadIdx.x >> 5];
-            X *sx = rem_x[threadIdx.x >> 5];
-            int32_t ra[U][V], rb[U][V];
+        if (q0 != q1 && V < 4) {
+            // two rows per lane (FP64): sum them in place
 #pragma unroll
             for (int u = 0; u < U; u++)
 #pragma unroll
                 for (int m = 0; m < V; m++) {
                     const int32_t t = tl[u] + m;
-                    const bool own = t < rows;
-                    ra[u][m] = own ? csr_row_ptr[r0 + t] : 0;
-                    rb[u][m] = own ? csr_row_ptr[r0 + t + 1] : 0;
-                }
-            for (int32_t c0 = q0; c0 < q1; c0 += RCH) {
-                const int32_t cn = (q1 - c0 < RCH) ? (q1 - c0) : RCH;
-                for (int32_t e = lane; e < cn; e += 32) {
-                    sv[e] = csr_val[c0 + e];
-                    sx[e] = ldg_elem(x + csr_col[c0 + e]);
-                }
-                __syncwarp();
-#pragma unroll
-                for (int u = 0; u < U; u++)
-#pragma unroll
-                    for (int m = 0; m < V; m++) {
-                        const int32_t k0 = ra[u][m] > c0 ? ra[u][m] : c0;
-                        const int32_t k1 = rb[u][m] < c0 + cn ? rb[u][m] : c0 + cn;
-                        for (int32_t k = k0; k < k1; k++)
-                            acc[u][m] += widen(sv[k - c0]) * widen(sx[k - c0]);
+                    if (t < rows) {
+                        const int64_t i = r0 + t;
+                        const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
+                        for (int32_t k = a; k < b; k++)
+                            acc[u][m] += widen(csr_val[k]) * widen(ldg_elem(x + csr_col[k]));
                     }
-                __syncwarp();
+                }
+        } else if (q0 != q1) {
+            __shared__ Acc rsum[SPMV_WARPS][RW];
+            Acc *rs = rsum[threadIdx.x >> 5];
+            for (int rr = lane; rr < RW; rr += 32) {
+                Acc sum = Acc(0);
+                if (tw + rr < rows) {
+                    const int64_t i = r0 + tw + rr;
+                    const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
+                    for (int32_t k = a; k < b; k++)
+                        sum += widen(csr_val[k]) * widen(ldg_elem(x + csr_col[k]));
+                }
+                rs[rr] = sum;
             }
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int m = 0; m < V; m++) acc[u][m] = rs[tl[u] - tw + m];
+            __syncwarp();
         }
     }
 
