@@ -105,7 +105,7 @@ __device__ __forceinline__ uint4 window16(const uint4 &lo, const uint4 &hi, int 
 // The block's diagonals are taken D at a time: the D * U 16-byte value loads
 // of a group are issued first, then the x loads, then the FMAs, so a warp
 // keeps D * U * 512 bytes of dia_val in flight.
-template <typename VT, int U, int D, bool VEC, bool REM_IN_Y = false>
+template <typename VT, int U, int D, bool VEC>
 __device__ __forceinline__ void
 reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restrict__ dia_ptr,
          const int32_t *__restrict__ dia_offset, const VT *__restrict__ dia_val,
@@ -144,20 +144,7 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
     // rr = lane, lane + 32, ...), in column order from zero, and the sums reach
     // their owners through shared memory: the same operations as summing into
     // acc directly, with one row per lane instead of V in sequence.
-    if constexpr (REM_IN_Y) {
-        // two-pass product: k_rem_rows already left each remainder row's sum
-        // (from zero, in column order) in y; rows without remainder start at 0
-        const int32_t tend = full ? tw + RW : rows;
-        if (csr_row_ptr[r0 + tw] != csr_row_ptr[r0 + tend]) {
-#pragma unroll
-            for (int u = 0; u < U; u++)
-#pragma unroll
-                for (int m = 0; m < V; m++) {
-                    const int64_t i = r0 + tl[u] + m;
-                    if (tl[u] + m < rows && csr_row_ptr[i + 1] != csr_row_ptr[i]) acc[u][m] = y[i];
-                }
-        }
-    } else {
+    {
         const int32_t tend = full ? tw + RW : rows;
         const int32_t q0 = csr_row_ptr[r0 + tw], q1 = csr_row_ptr[r0 + tend];
         if (q0 != q1 && V < 4) {
@@ -289,40 +276,6 @@ k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
     if (w >= n_tiles) return;
     reg_tile<VT, U, D, VEC>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_val, csr_row_ptr, csr_col,
                             csr_val, x, y);
-}
-
-// Two-pass product (variants 16, 17): first the remainder rows alone, one
-// thread per row as in the CSR kernel (all rows of the matrix in flight, each
-// row's sum from zero in column order, written to y), then the register tiles
-// starting from those sums.  Same operations per row as the one-pass tiles.
-template <typename VT>
-__global__ void __launch_bounds__(256)
-k_rem_rows(int64_t n, const int32_t *__restrict__ csr_row_ptr, const int32_t *__restrict__ csr_col,
-           const VT *__restrict__ csr_val, const typename Tr<VT>::X *__restrict__ x,
-           typename Tr<VT>::Y *__restrict__ y)
-{
-    using Acc = typename Tr<VT>::Acc;
-    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (i >= n) return;
-    const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
-    if (a == b) return;
-    Acc s = Acc(0);
-    for (int32_t k = a; k < b; k++) s += widen(csr_val[k]) * widen(ldg_elem(x + csr_col[k]));
-    y[i] = s;
-}
-
-template <typename VT, int U, int D>
-__global__ void __launch_bounds__(SPMV_THREADS)
-k_mhdc_spmv_rem_in_y(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
-                     const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
-                     const VT *__restrict__ dia_val, const int32_t *__restrict__ csr_row_ptr,
-                     const int32_t *__restrict__ csr_col, const VT *__restrict__ csr_val,
-                     const typename Tr<VT>::X *__restrict__ x, typename Tr<VT>::Y *__restrict__ y)
-{
-    const int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5);
-    if (w >= n_tiles) return;
-    reg_tile<VT, U, D, true, true>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_val, csr_row_ptr,
-                                   csr_col, csr_val, x, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -888,49 +841,8 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
     return MHDC_OK;
 }
 
-template <typename VT>
-int launch_two_pass(const mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_t st)
-{
-    using X = typename Tr<VT>::X;
-    using Y = typename Tr<VT>::Y;
-    constexpr int V = Tr<VT>::V;
-    const int rw = 32 * V * (shape == 0 ? 1 : 2);
-    int32_t tpb = (int32_t)((A->n_b + rw - 1) / rw);
-    int64_t tiles = (int64_t)tpb * A->n_blocks;
-    const int64_t grid = (tiles + SPMV_WARPS - 1) / SPMV_WARPS;
-    const X *x = static_cast<const X *>(d_x);
-    Y *y = static_cast<Y *>(d_y);
-    const VT *dv = static_cast<const VT *>(A->dia_val), *cv = static_cast<const VT *>(A->csr_val);
-    if (A->nnz_rem > 0) {
-        k_rem_rows<VT><<<(unsigned)((A->n + 255) / 256), 256, 0, st>>>(A->n, A->csr_row_ptr,
-                                                                       A->csr_col, cv, x, y);
-        MHDC_LAUNCH_CHECK("k_rem_rows");
-    }
-    auto go = [&](auto kern) {
-        kern<<<(unsigned)grid, SPMV_THREADS, 0, st>>>(A->n, A->n_b, tpb, tiles, A->dia_ptr,
-                                                      A->dia_offset, dv, A->csr_row_ptr,
-                                                      A->csr_col, cv, x, y);
-    };
-    if (shape == 0) go(k_mhdc_spmv_rem_in_y<VT, 1, 2>);
-    else go(k_mhdc_spmv_rem_in_y<VT, 2, 2>);
-    MHDC_LAUNCH_CHECK("k_mhdc_spmv_rem_in_y");
-    return MHDC_OK;
-}
-
 int launch_variant(mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStream_t stream)
 {
-    if (id >= FIRST_TWO_PASS_VARIANT) {
-        const int V = A->dtype == MHDC_F64 ? 2 : A->dtype == MHDC_F32 ? 4 : 8;
-        if (A->n_b % V == 0) {
-            const int shape = id - FIRST_TWO_PASS_VARIANT;
-            switch (A->dtype) {
-            case MHDC_F64: return launch_two_pass<double>(A, shape, d_x, d_y, stream);
-            case MHDC_F32: return launch_two_pass<float>(A, shape, d_x, d_y, stream);
-            default: return launch_two_pass<__nv_bfloat16>(A, shape, d_x, d_y, stream);
-            }
-        }
-        id = -1;
-    }
     if (id >= FIRST_DW_VARIANT) {
         if (A->dw_ok && A->dtype == MHDC_F64 && (A->n_b % 2) == 0) {
             if (id < FIRST_TMA_DW_VARIANT) return launch_dw(A, id - FIRST_DW_VARIANT, d_x, d_y, stream);
