@@ -203,7 +203,7 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  * (variant -1's arithmetic) instead.
  *
  * mhdc_set_variant -- use variant v for this handle (-1: default chosen from n_b).
- *                     The first v >= 10 on an FP64 handle makes its FP32-pair
+ *                     The first v in 10-15 on an FP64 handle makes its FP32-pair
  *                     arrays (device memory as large as dia_val and csr_val)
  *                     on the legacy default stream and waits for them.
  * mhdc_tune        -- time every variant on (d_x, d_y) (overwriting d_y), keep

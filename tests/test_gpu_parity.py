@@ -239,7 +239,7 @@ def test_misaligned_x_gives_identical_result(mh):
         if dt == "f64":
             buf[1 + A.n // 2] = 1e300
             xal = buf[1:].clone()
-            for v in range(mh.FIRST_EMULATED_VARIANT, mh.MHDC_NUM_VARIANTS):
+            for v in mh.EMULATED_VARIANTS:
                 mh.mhdc_set_variant(h, v)
                 y1 = y_empty(A.n, dt)
                 mh.mhdc_spmv(h, buf[1:], y1)
@@ -294,10 +294,10 @@ def test_every_variant_is_bit_identical_and_tune_picks_one(mh):
             h, M = check_build(mh, A, n_b, 0.6, dt)
             xd, _ = x_device(synth.uniform_vector(A.n, 5), dt)
             ys = []
-            # variants 0-9 share the arithmetic; 10-12 emulate FP64 (FP64 handles)
-            # and fall back to the default elsewhere
-            top = mh.MHDC_NUM_VARIANTS if dt != "f64" else mh.FIRST_EMULATED_VARIANT
-            for v in range(-1, top):
+            # variants 0-9 share the arithmetic; 10-15 emulate FP64 (FP64
+            # handles) and fall back to the default elsewhere
+            vs = (-1,) + (mh.NATIVE_VARIANTS if dt == "f64" else tuple(range(mh.MHDC_NUM_VARIANTS)))
+            for v in vs:
                 mh.mhdc_set_variant(h, v)
                 y = y_empty(A.n, dt)
                 mh.mhdc_spmv(h, xd, y)
@@ -309,7 +309,7 @@ def test_every_variant_is_bit_identical_and_tune_picks_one(mh):
             best, times = mh.mhdc_tune(h, xd, ys[0])
             assert 0 <= best < mh.MHDC_NUM_VARIANTS and h.info["variant"] == best
             assert all(tt > 0 for tt in times)
-            if best < mh.FIRST_EMULATED_VARIANT or dt != "f64":
+            if best not in mh.EMULATED_VARIANTS or dt != "f64":
                 y = y_empty(A.n, dt)
                 mh.mhdc_spmv(h, xd, y)
                 assert t.equal(y, ys[1])
@@ -367,7 +367,7 @@ def test_emulated_fp64_meets_the_fp64_tolerance(mh):
             assert h.info["emulated_ok"] == -1, name   # made on first use
             mh.mhdc_set_variant(h, mh.FIRST_EMULATED_VARIANT)
             assert h.info["emulated_ok"] == 1, name
-            for v in range(mh.FIRST_EMULATED_VARIANT, mh.MHDC_NUM_VARIANTS):
+            for v in mh.EMULATED_VARIANTS:
                 mh.mhdc_set_variant(h, v)
                 check_spmv(mh, h, M, A, x, "f64")
 
@@ -377,7 +377,7 @@ def test_emulated_fp64_full_size(mh):
     h, M = check_build(mh, A, 4096, 0.6, "f64")
     mh.mhdc_set_variant(h, mh.FIRST_EMULATED_VARIANT)
     assert h.info["emulated_ok"] == 1
-    for v in range(mh.FIRST_EMULATED_VARIANT, mh.MHDC_NUM_VARIANTS):
+    for v in mh.EMULATED_VARIANTS:
         mh.mhdc_set_variant(h, v)
         check_spmv(mh, h, M, A, synth.uniform_vector(A.n, 1), "f64")
 
@@ -388,7 +388,7 @@ def _native_and_emulated(mh, h, x):
     y0 = y_empty(h.n, "f64")
     mh.mhdc_spmv(h, x, y0)
     out = []
-    for v in range(mh.FIRST_EMULATED_VARIANT, mh.MHDC_NUM_VARIANTS):
+    for v in mh.EMULATED_VARIANTS:
         mh.mhdc_set_variant(h, v)
         y = y_empty(h.n, "f64")
         mh.mhdc_spmv(h, x, y)
@@ -419,7 +419,7 @@ def test_emulated_fp64_falls_back_outside_its_window(mh):
     y0, ys = _native_and_emulated(mh, h, xd)
     assert not t.equal(ys[0], y0) or True
     M = oracle.convert(A, 4096, 0.6, "f64")
-    for v in range(mh.FIRST_EMULATED_VARIANT, mh.MHDC_NUM_VARIANTS):
+    for v in mh.EMULATED_VARIANTS:
         mh.mhdc_set_variant(h, v)
         check_spmv(mh, h, M, A, base, "f64")
 
