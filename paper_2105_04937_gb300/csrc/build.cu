@@ -38,7 +38,6 @@ constexpr int HCAP = 16384;               // shared-memory hash slots
 constexpr int HLIMIT = 12288;             // distinct offsets a shared table accepts
 constexpr int CS_THREADS = 512;
 constexpr int CS_WARPS = CS_THREADS / 32;
-constexpr size_t CS_SMEM = 3 * HCAP * sizeof(int32_t);
 
 // 32-bit finaliser of MurmurHash3 (Appleby): spreads offsets that differ only
 // in high bits (stencil offsets like -16384, 0, 16384) over the table.
@@ -159,23 +158,25 @@ __device__ void cta_bitonic_sort(int32_t *a, int64_t P2)
 // M-HDC selection for one row block per CTA (block ids[blockIdx.x] when ids
 // is given, else blockIdx.x), in three table levels:
 //   level 1: <false, true>  shared table of at most SMALL_CAP slots, and each
-//            warp stages its 32 rows' columns in shared memory (coalesced
-//            loads) before walking them one lane per row;
-//   level 2: <false, false> shared table of at most HCAP slots, columns read
-//            from global memory, for the blocks level 1 could not hold;
+//            warp stages its 32 rows' columns (up to cw) in shared memory
+//            (coalesced loads) before walking them one lane per row;
+//   level 2: <false, true>  shared table of at most HCAP slots, smaller
+//            staging, for the blocks level 1 could not hold;
 //   level 3: <true, false>  a table of 2^tab_log2[c] slots at tab_base[c] in
 //            global memory (at least twice the block's entries: cannot fill).
 // A shared table accepting no more distinct offsets sets overflow[ib] and the
 // CTA stops; the host then runs the next level for those blocks.
 constexpr int SMALL_CAP = 2048;
-constexpr int CW = 1024;  // staged columns per warp at level 1
+constexpr int CW = 1024;    // staged columns per warp at level 1
+constexpr int CW_L2 = 512;  // and at level 2 (with the largest table)
 constexpr size_t CS_SMEM_SMALL = (3 * SMALL_CAP + CS_WARPS * CW) * sizeof(int32_t);
+constexpr size_t CS_SMEM_L2 = (3 * HCAP + CS_WARPS * CW_L2) * sizeof(int32_t);
 
 template <bool GLOBAL_TABLE, bool STAGE>
 __global__ void __launch_bounds__(CS_THREADS)
 k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
                const int32_t *__restrict__ col, double theta, const int32_t *__restrict__ ids,
-               int32_t cap_max, int32_t *gkeys, int32_t *gcnt,
+               int32_t cap_max, int32_t cw, int32_t *gkeys, int32_t *gcnt,
                const int64_t *__restrict__ tab_base, const int32_t *__restrict__ tab_log2,
                int32_t *sel_out, int32_t *sel_cnt, int32_t *overflow)
 {
@@ -217,7 +218,7 @@ k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
 
     // lanes holding the same offset in a step add their count once (leader lane)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t *stage = smem + 3 * cap_max + warp * CW;
+    int32_t *stage = smem + 3 * cap_max + warp * cw;
     for (int64_t g0 = r0 + 32 * warp; g0 < r0 + rows; g0 += 32 * CS_WARPS) {
         if (__any_sync(0xffffffffu, ovf != 0)) break;  // warp-uniform exit
         auto count = [&](bool has, int64_t, int32_t, int32_t off) {
@@ -228,7 +229,7 @@ k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
         };
         const int64_t g1 = (g0 + 32 < r0 + rows) ? g0 + 32 : r0 + rows;
         const int32_t e0 = rp[g0], e1 = rp[g1];
-        if (STAGE && e1 - e0 <= CW) {
+        if (STAGE && e1 - e0 <= cw) {
             for (int32_t e = e0 + lane; e < e1; e += 32) stage[e - e0] = __ldg(col + e);
             __syncwarp();
             rows_by_lane<true>(g0, g1, rp, stage, e0, count);
@@ -422,7 +423,7 @@ __device__ __forceinline__ int64_t find_sorted(const int32_t *__restrict__ s, in
 // (coalesced loads of col and val), find each entry's row by binary search
 // in the staged row pointers and its diagonal by binary search in the
 // block's sorted offsets, and either place the value in the tile or count
-// the entry in its row's remainder count.  The tile, zero-filled first, is
+// the entry in its row's remainder count and set its bit in rem_flag.  The tile, zero-filled first, is
 // written out one contiguous run per diagonal, so each dia_val element is
 // written once.  When even 32 rows of S diagonals exceed the tile, the CTA
 // zero-fills its slots in global memory and writes the entries in place.  The
@@ -458,7 +459,7 @@ k_scatter(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
           const int32_t *__restrict__ col, const double *__restrict__ val,
           const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ sel_list,
           const int32_t *__restrict__ sel_base_rp, int32_t *__restrict__ dia_offset,
-          VT *__restrict__ dia_val, int32_t *__restrict__ rem_cnt)
+          VT *__restrict__ dia_val, int32_t *__restrict__ rem_cnt, uint32_t *__restrict__ rem_flag)
 {
     extern __shared__ __align__(16) unsigned char sc_smem[];
     int32_t *sel_s = reinterpret_cast<int32_t *>(sc_smem);
@@ -536,16 +537,26 @@ k_scatter(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
             }
 #pragma unroll
             for (int u = 0; u < SC_UNROLL; u++) {
-                const int32_t e = eb + u * SC_THREADS;
-                if (e >= e1) break;
-                const int32_t r = rid ? (int32_t)rid_s[e - e0] : row_of(rp_s, (int32_t)un, e);
-                const int64_t p = find_sorted(sel, S, cc[u] - (int32_t)(rb + r));
-                if (p < 0) {
-                    atomicAdd(&rem_s[r], 1);
-                } else if (tiled) {
-                    tile[p * ld + r] = round_store<VT>(vv[u]);
-                } else {
-                    dv[p * n_b + (rb - r0) + r] = round_store<VT>(vv[u]);
+                const int32_t e = eb + u * SC_THREADS;  // consecutive across the warp
+                bool rem = false;
+                if (e < e1) {
+                    const int32_t r = rid ? (int32_t)rid_s[e - e0] : row_of(rp_s, (int32_t)un, e);
+                    const int64_t p = find_sorted(sel, S, cc[u] - (int32_t)(rb + r));
+                    if (p < 0) {
+                        rem = true;
+                        atomicAdd(&rem_s[r], 1);
+                    } else if (tiled) {
+                        tile[p * ld + r] = round_store<VT>(vv[u]);
+                    } else {
+                        dv[p * n_b + (rb - r0) + r] = round_store<VT>(vv[u]);
+                    }
+                }
+                // one bit per entry: the warp's 32 bits span at most two words
+                const unsigned b = __ballot_sync(0xffffffffu, rem);
+                if ((threadIdx.x & 31) == 0 && b) {
+                    const int32_t w0 = e >> 5, sh = e & 31;
+                    atomicOr(&rem_flag[w0], b << sh);
+                    if (sh && (b >> (32 - sh))) atomicOr(&rem_flag[w0 + 1], b >> (32 - sh));
                 }
             }
         }
@@ -559,47 +570,50 @@ k_scatter(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
     }
 }
 
-// Remainder (Fig. 12, CSR part): a warp takes 32 rows and, for each of them
-// holding remainder entries, tests the row's entries 32 at a time (one lane
-// each) against the block's sorted offsets (dia_offset) and writes the ones
-// left out in input order from csr_row_ptr[i] on (ballot prefix counts).
+// Remainder (Fig. 12, CSR part), per (block, chunk) as the scatter: the
+// chunk's entries are walked in order, 256 at a time, and those whose
+// rem_flag bit is set are written in input order from csr_row_ptr of the
+// chunk's first row on (block-wide prefix count of the bits).
 template <typename VT>
-__global__ void k_rem_fill(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
-                           const int32_t *__restrict__ col, const double *__restrict__ val,
-                           const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
-                           const int32_t *__restrict__ csr_row_ptr, int32_t *__restrict__ csr_col,
-                           VT *__restrict__ csr_val)
+__global__ void __launch_bounds__(SC_THREADS)
+k_rem_fill(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
+           const int32_t *__restrict__ col, const double *__restrict__ val,
+           const uint32_t *__restrict__ rem_flag, const int32_t *__restrict__ csr_row_ptr,
+           int32_t *__restrict__ csr_col, VT *__restrict__ csr_val)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane);
-    if (g0 >= n) return;  // warp-uniform
-    const int64_t i = g0 + lane;
-    const bool live = i < n;
-    const int32_t q0 = live ? csr_row_ptr[i] : 0;
-    const int32_t q1 = live ? csr_row_ptr[i + 1] : 0;
-    unsigned todo = __ballot_sync(0xffffffffu, live && q1 > q0);
-    while (todo) {
-        const int l = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int64_t row = g0 + l;
-        int32_t q = __shfl_sync(0xffffffffu, q0, l);
-        const int64_t ib = row / n_b;
-        const int64_t p0 = dia_ptr[ib];
-        const int64_t S = dia_ptr[ib + 1] - p0;
-        const int32_t a = rp[row], b = rp[row + 1];
-        for (int32_t k0 = a; k0 < b; k0 += 32) {
-            const int32_t k = k0 + lane;
-            const bool in = k < b;
-            const int32_t c = in ? col[k] : 0;
-            const bool rem = in && find_sorted(dia_offset + p0, S, c - (int32_t)row) < 0;
-            const unsigned m = __ballot_sync(0xffffffffu, rem);
-            if (rem) {
-                const int32_t pos = q + __popc(m & ((1u << lane) - 1u));
-                csr_col[pos] = c;
-                csr_val[pos] = round_store<VT>(val[k]);
-            }
-            q += __popc(m);
+    __shared__ int32_t wsum[SC_THREADS / 32];
+    const int64_t ib = blockIdx.x / cpb;
+    const int64_t c = blockIdx.x - ib * cpb;
+    const int64_t r0 = ib * (int64_t)n_b;
+    const int64_t rows = (n - r0 < n_b) ? (n - r0) : n_b;
+    const int64_t t0 = c * SC_ROWS;
+    if (t0 >= rows) return;  // CTA-uniform
+    const int64_t tn = (rows - t0 < SC_ROWS) ? (rows - t0) : SC_ROWS;
+    const int64_t rb = r0 + t0;
+    int32_t q = csr_row_ptr[rb];
+    if (q == csr_row_ptr[rb + tn]) return;  // no remainder in this chunk (CTA-uniform)
+    const int32_t E0 = rp[rb], E1 = rp[rb + tn];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int32_t eb = E0; eb < E1; eb += SC_THREADS) {
+        const int32_t e = eb + (int32_t)threadIdx.x;
+        const bool f = e < E1 && ((rem_flag[e >> 5] >> (e & 31)) & 1u);
+        const unsigned b = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wsum[warp] = __popc(b);
+        __syncthreads();
+        int32_t before = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < SC_THREADS / 32; w++) {
+            const int32_t v = wsum[w];
+            before += w < warp ? v : 0;
+            tot += v;
         }
+        if (f) {
+            const int32_t pos = q + before + __popc(b & ((1u << lane) - 1u));
+            csr_col[pos] = col[e];
+            csr_val[pos] = round_store<VT>(val[e]);
+        }
+        q += tot;
+        __syncthreads();
     }
 }
 
@@ -691,20 +705,34 @@ int dalloc_raw(void **p, size_t bytes)
         if (rc_ != MHDC_OK) return rc_;   \
     } while (0)
 
+// rem_flag: (nnz + 31) / 32 words, zeroed here.
 template <typename VT>
-int launch_scatter(int64_t n, int32_t n_b, int64_t nb, const int32_t *rp, const int32_t *col,
-                   const double *val, const int32_t *dia_ptr, const int32_t *sel_list,
-                   const int32_t *sel_base_rp, int32_t *dia_offset, VT *dia_val, int32_t *rem_cnt,
-                   cudaStream_t st)
+int launch_scatter(int64_t n, int32_t n_b, int64_t nb, int64_t nnz, const int32_t *rp,
+                   const int32_t *col, const double *val, const int32_t *dia_ptr,
+                   const int32_t *sel_list, const int32_t *sel_base_rp, int32_t *dia_offset,
+                   VT *dia_val, int32_t *rem_cnt, uint32_t *rem_flag, cudaStream_t st)
 {
     if (nb == 0) return MHDC_OK;
+    MHDC_CUDA_TRY(cudaMemsetAsync(rem_flag, 0, sizeof(uint32_t) * (size_t)((nnz + 31) / 32), st));
     const int64_t cpb = ((int64_t)n_b + SC_ROWS - 1) / SC_ROWS;
     MHDC_CUDA_TRY(cudaFuncSetAttribute(k_scatter<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)SC_SMEM));
     k_scatter<VT><<<(unsigned)(nb * cpb), SC_THREADS, SC_SMEM, st>>>(
         n, n_b, (int32_t)cpb, rp, col, val, dia_ptr, sel_list, sel_base_rp, dia_offset, dia_val,
-        rem_cnt);
+        rem_cnt, rem_flag);
     MHDC_LAUNCH_CHECK("k_scatter");
+    return MHDC_OK;
+}
+
+template <typename VT>
+int launch_rem_fill(int64_t n, int32_t n_b, int64_t nb, const int32_t *rp, const int32_t *col,
+                    const double *val, const uint32_t *rem_flag, const int32_t *csr_row_ptr,
+                    int32_t *csr_col, VT *csr_val, cudaStream_t st)
+{
+    const int64_t cpb = ((int64_t)n_b + SC_ROWS - 1) / SC_ROWS;
+    k_rem_fill<VT><<<(unsigned)(nb * cpb), SC_THREADS, 0, st>>>(
+        n, n_b, (int32_t)cpb, rp, col, val, rem_flag, csr_row_ptr, csr_col, csr_val);
+    MHDC_LAUNCH_CHECK("k_rem_fill");
     return MHDC_OK;
 }
 
@@ -713,11 +741,13 @@ int scatter_all(mhdc_matrix *A, const int32_t *rp, const int32_t *col, const dou
                 const int32_t *sel_list, const int32_t *sel_base_rp, cudaStream_t st)
 {
     const int64_t n = A->n;
-    Buf rem, scr;
+    Buf rem, scr, flag;
     RC(dalloc(rem, sizeof(int32_t) * (size_t)n, st));
     RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(n), st));
-    RC(launch_scatter<VT>(n, A->n_b, A->n_blocks, rp, col, val, A->dia_ptr, sel_list, sel_base_rp,
-                          A->dia_offset, static_cast<VT *>(A->dia_val), rem.as<int32_t>(), st));
+    RC(dalloc(flag, sizeof(uint32_t) * (size_t)((A->nnz + 31) / 32), st));
+    RC(launch_scatter<VT>(n, A->n_b, A->n_blocks, A->nnz, rp, col, val, A->dia_ptr, sel_list,
+                          sel_base_rp, A->dia_offset, static_cast<VT *>(A->dia_val),
+                          rem.as<int32_t>(), flag.as<uint32_t>(), st));
     RC(dalloc_raw((void **)&A->csr_row_ptr, sizeof(int32_t) * (size_t)(n + 1)));
     RC(exclusive_scan_i32(rem.as<int32_t>(), A->csr_row_ptr, n, scr.as<int32_t>(), st));
     int32_t nr = 0;
@@ -727,12 +757,9 @@ int scatter_all(mhdc_matrix *A, const int32_t *rp, const int32_t *col, const dou
     A->nnz_rem = nr;
     RC(dalloc_raw((void **)&A->csr_col, sizeof(int32_t) * (size_t)nr));
     RC(dalloc_raw(&A->csr_val, sizeof(VT) * (size_t)nr));
-    if (nr > 0) {
-        k_rem_fill<VT><<<grid_for(n, 256), 256, 0, st>>>(
-            n, A->n_b, rp, col, val, A->dia_ptr, A->dia_offset, A->csr_row_ptr, A->csr_col,
-            static_cast<VT *>(A->csr_val));
-        MHDC_LAUNCH_CHECK("k_rem_fill");
-    }
+    if (nr > 0)
+        RC(launch_rem_fill<VT>(n, A->n_b, A->n_blocks, rp, col, val, flag.as<uint32_t>(),
+                               A->csr_row_ptr, A->csr_col, static_cast<VT *>(A->csr_val), st));
     return MHDC_OK;
 }
 
@@ -770,7 +797,7 @@ int select_block_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Buf
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)CS_SMEM_SMALL));
     k_count_select<false, true><<<(unsigned)nb, CS_THREADS, CS_SMEM_SMALL, st>>>(
-        n, A->n_b, rp, col, A->theta, nullptr, SMALL_CAP, nullptr, nullptr, nullptr, nullptr,
+        n, A->n_b, rp, col, A->theta, nullptr, SMALL_CAP, CW, nullptr, nullptr, nullptr, nullptr,
         sel_out.as<int32_t>(), sel_cnt.as<int32_t>(), ovf.as<int32_t>());
     MHDC_LAUNCH_CHECK("k_count_select<level 1>");
     k_block_bounds<<<grid_for(nb + 1, 256), 256, 0, st>>>(n, A->n_b, nb, rp, bounds.as<int32_t>());
@@ -784,12 +811,12 @@ int select_block_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Buf
         RC(dalloc(d_ids, sizeof(int32_t) * ids.size(), st));
         MHDC_CUDA_TRY(cudaMemcpyAsync(d_ids.p, ids.data(), sizeof(int32_t) * ids.size(),
                                       cudaMemcpyHostToDevice, st));
-        MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_select<false, false>,
+        MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_select<false, true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)CS_SMEM));
-        k_count_select<false, false><<<(unsigned)ids.size(), CS_THREADS, CS_SMEM, st>>>(
-            n, A->n_b, rp, col, A->theta, d_ids.as<int32_t>(), HCAP, nullptr, nullptr, nullptr,
-            nullptr, sel_out.as<int32_t>(), sel_cnt.as<int32_t>(), ovf.as<int32_t>());
+                                           (int)CS_SMEM_L2));
+        k_count_select<false, true><<<(unsigned)ids.size(), CS_THREADS, CS_SMEM_L2, st>>>(
+            n, A->n_b, rp, col, A->theta, d_ids.as<int32_t>(), HCAP, CW_L2, nullptr, nullptr,
+            nullptr, nullptr, sel_out.as<int32_t>(), sel_cnt.as<int32_t>(), ovf.as<int32_t>());
         MHDC_LAUNCH_CHECK("k_count_select<level 2>");
         RC(overflowed_blocks(ovf.as<int32_t>(), bounds.as<int32_t>(), nb, ids, entries, st));
     }
@@ -818,7 +845,7 @@ int select_block_mode(mhdc_matrix *A, const int32_t *rp, const int32_t *col, Buf
         MHDC_CUDA_TRY(cudaMemcpyAsync(d_base.p, base.data(), sizeof(int64_t) * base.size(),
                                       cudaMemcpyHostToDevice, st));
         k_count_select<true, false><<<(unsigned)ids.size(), CS_THREADS, 0, st>>>(
-            n, A->n_b, rp, col, A->theta, d_ids.as<int32_t>(), 0, gk.as<int32_t>(),
+            n, A->n_b, rp, col, A->theta, d_ids.as<int32_t>(), 0, 0, gk.as<int32_t>(),
             gc.as<int32_t>(), d_base.as<int64_t>(), d_lg.as<int32_t>(), sel_out.as<int32_t>(),
             sel_cnt.as<int32_t>(), ovf.as<int32_t>());
         MHDC_LAUNCH_CHECK("k_count_select<level 3>");
@@ -1172,14 +1199,15 @@ namespace {
 constexpr int64_t NA_MAX_NNZ = 1 << 18;   // stored entries
 constexpr int64_t NA_MAX_N = 1 << 18;     // rows (so at most 2^18 row blocks)
 constexpr int64_t NA_SCAN = 2 * ((NA_MAX_NNZ + 4095) / 4096) + 8;  // scan tile sums, with room
-// int32 words: err | sel_out | sel_cnt | ovf | ovf_pos | rem | scan | keys | cnt | ids | lg | base(i64)
+// int32 words: err | sel_out | sel_cnt | ovf | ovf_pos | rem | rem_flag | scan | keys | cnt | ids | lg | base(i64)
 constexpr int64_t NA_ERR = 0;
 constexpr int64_t NA_SEL = 64;
 constexpr int64_t NA_SELCNT = NA_SEL + NA_MAX_NNZ;
 constexpr int64_t NA_OVF = NA_SELCNT + NA_MAX_N;
 constexpr int64_t NA_OVFPOS = NA_OVF + NA_MAX_N;
 constexpr int64_t NA_REM = NA_OVFPOS + NA_MAX_N + 64;
-constexpr int64_t NA_SCANS = NA_REM + NA_MAX_N + 64;
+constexpr int64_t NA_RFLAG = NA_REM + NA_MAX_N + 64;  // one bit per entry
+constexpr int64_t NA_SCANS = NA_RFLAG + NA_MAX_NNZ / 32 + 64;
 constexpr int64_t NA_KEYS = NA_SCANS + NA_SCAN + 64;
 constexpr int64_t NA_CNT = NA_KEYS + 4 * NA_MAX_NNZ;
 // a block overflows its shared table only with more than 12288 entries, so at
@@ -1246,14 +1274,15 @@ int read_i32(const int32_t *d, int32_t *h, cudaStream_t st)
 }
 
 template <typename VT>
-int noalloc_fill(int64_t n, int32_t n_b, int64_t nb, const int32_t *rp, const int32_t *col,
-                 const double *val, int32_t *S, int32_t *dia_ptr, int32_t *dia_offset,
-                 void *dia_val, int32_t *csr_row_ptr, int32_t *csr_col, void *csr_val,
-                 int64_t cap_rem, int64_t *h_nnz_rem, cudaStream_t st)
+int noalloc_fill(int64_t n, int32_t n_b, int64_t nb, int64_t nnz, const int32_t *rp,
+                 const int32_t *col, const double *val, int32_t *S, int32_t *dia_ptr,
+                 int32_t *dia_offset, void *dia_val, int32_t *csr_row_ptr, int32_t *csr_col,
+                 void *csr_val, int64_t cap_rem, int64_t *h_nnz_rem, cudaStream_t st)
 {
     int32_t *rem = S + NA_REM;  // per-row remainder counts (n <= NA_MAX_N words)
-    RC(launch_scatter<VT>(n, n_b, nb, rp, col, val, dia_ptr, S + NA_SEL, rp, dia_offset,
-                          static_cast<VT *>(dia_val), rem, st));
+    uint32_t *flag = reinterpret_cast<uint32_t *>(S + NA_RFLAG);
+    RC(launch_scatter<VT>(n, n_b, nb, nnz, rp, col, val, dia_ptr, S + NA_SEL, rp, dia_offset,
+                          static_cast<VT *>(dia_val), rem, flag, st));
     RC(exclusive_scan_i32(rem, csr_row_ptr, n, S + NA_SCANS, st));
     int32_t nr = 0;
     RC(read_i32(csr_row_ptr + n, &nr, st));
@@ -1262,12 +1291,9 @@ int noalloc_fill(int64_t n, int32_t n_b, int64_t nb, const int32_t *rp, const in
         set_error_msg("mhdc_build_noalloc: csr_col/csr_val capacity too small (needed size in *h_nnz_rem)");
         return MHDC_ERR_INVALID_ARG;
     }
-    if (nr > 0) {
-        k_rem_fill<VT><<<grid_for(n, 256), 256, 0, st>>>(n, n_b, rp, col, val, dia_ptr, dia_offset,
-                                                         csr_row_ptr, csr_col,
-                                                         static_cast<VT *>(csr_val));
-        MHDC_LAUNCH_CHECK("k_rem_fill");
-    }
+    if (nr > 0)
+        RC(launch_rem_fill<VT>(n, n_b, nb, rp, col, val, flag, csr_row_ptr, csr_col,
+                               static_cast<VT *>(csr_val), st));
     MHDC_CUDA_TRY(cudaStreamSynchronize(st));
     return MHDC_OK;
 }
@@ -1318,11 +1344,12 @@ int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double
     }
     // 2. selection per row block (shared-memory tables; overflowing blocks redone
     //    with tables in the scratch array)
-    MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_select<false, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CS_SMEM));
-    k_count_select<false, false><<<(unsigned)nb, CS_THREADS, CS_SMEM, st>>>(
-        n, n_b, rp, col, theta, nullptr, HCAP, nullptr, nullptr, nullptr, nullptr, S + NA_SEL,
-        S + NA_SELCNT, S + NA_OVF);
+    MHDC_CUDA_TRY(cudaFuncSetAttribute(k_count_select<false, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)CS_SMEM_L2));
+    k_count_select<false, true><<<(unsigned)nb, CS_THREADS, CS_SMEM_L2, st>>>(
+        n, n_b, rp, col, theta, nullptr, HCAP, CW_L2, nullptr, nullptr, nullptr, nullptr,
+        S + NA_SEL, S + NA_SELCNT, S + NA_OVF);
     MHDC_LAUNCH_CHECK("k_count_select");
     RC(exclusive_scan_i32(S + NA_OVF, S + NA_OVFPOS, nb, S + NA_SCANS, st));
     int32_t novf = 0;
@@ -1338,7 +1365,7 @@ int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double
                                                               base);
         MHDC_LAUNCH_CHECK("k_noalloc_ovf_list");
         k_count_select<true, false><<<(unsigned)novf, CS_THREADS, 0, st>>>(
-            n, n_b, rp, col, theta, S + NA_IDS, 0, S + NA_KEYS, S + NA_CNT, base, S + NA_LG,
+            n, n_b, rp, col, theta, S + NA_IDS, 0, 0, S + NA_KEYS, S + NA_CNT, base, S + NA_LG,
             S + NA_SEL, S + NA_SELCNT, S + NA_OVF);
         MHDC_LAUNCH_CHECK("k_count_select<global>");
     }
@@ -1363,13 +1390,13 @@ int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double
     // 4-5. scatter and remainder compaction
     switch (dtype) {
     case MHDC_F64:
-        return noalloc_fill<double>(n, n_b, nb, rp, col, val, S, dia_ptr, dia_offset, dia_val,
+        return noalloc_fill<double>(n, n_b, nb, nnz, rp, col, val, S, dia_ptr, dia_offset, dia_val,
                                     csr_row_ptr, csr_col, csr_val, cap_rem, h_nnz_rem, st);
     case MHDC_F32:
-        return noalloc_fill<float>(n, n_b, nb, rp, col, val, S, dia_ptr, dia_offset, dia_val,
+        return noalloc_fill<float>(n, n_b, nb, nnz, rp, col, val, S, dia_ptr, dia_offset, dia_val,
                                    csr_row_ptr, csr_col, csr_val, cap_rem, h_nnz_rem, st);
     default:
-        return noalloc_fill<__nv_bfloat16>(n, n_b, nb, rp, col, val, S, dia_ptr, dia_offset,
+        return noalloc_fill<__nv_bfloat16>(n, n_b, nb, nnz, rp, col, val, S, dia_ptr, dia_offset,
                                            dia_val, csr_row_ptr, csr_col, csr_val, cap_rem,
                                            h_nnz_rem, st);
     }
