@@ -524,7 +524,12 @@ k_scatter(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
                 for (int32_t e = rp_s[q]; e < rp_s[q + 1]; e++) rid_s[e - e0] = (uint8_t)q;
             __syncthreads();
         }
-        for (int32_t eb = e0 + (int32_t)threadIdx.x; eb < e1; eb += SC_UNROLL * SC_THREADS) {
+        // the loop bound is the warp's first entry, so whole warps iterate
+        // together (the ballot below needs every lane)
+        const int32_t lane_off = (int32_t)(threadIdx.x & 31);
+        for (int32_t wb = e0 + (int32_t)(threadIdx.x - lane_off); wb < e1;
+             wb += SC_UNROLL * SC_THREADS) {
+            const int32_t eb = wb + lane_off;
             int32_t cc[SC_UNROLL];
             double vv[SC_UNROLL];
 #pragma unroll
