@@ -71,6 +71,7 @@ def _declare(L):
         "orc_mhdc_to_coo": (I64, [I64, I64, P, P, P, P, P, P, I64, P, P, P]),
         "orc_mhdc_absrow": (None, [I64, I64, P, P, P, P, P, P, P, P, P]),
         "orc_stream_direct": (None, [I64, P, P, P]),
+        "orc_dia_to_csr": (I64, [I64, I64, P, P, P, P, P, I64]),
         "orc_stream_indirect": (None, [I64, P, P, P, P]),
         "orc_max_threads": (C.c_int, []),
     }
@@ -334,6 +335,24 @@ def bound_vs_stored(absrow_stored, terms, dtype: str) -> np.ndarray:
 # --------------------------------------------------------------------------
 # Memory benchmarks (Sec. 6.2)
 # --------------------------------------------------------------------------
+
+def dia_to_csr(n, offsets, dia_val):
+    """DIA arrays (Sec. 3.3, Fig. 4: dia_val[d, i] = a(i, i + offsets[d])) as
+    CSR (row_ptr, col, val); zeros and out-of-range positions are not entries."""
+    off = _i32(offsets)
+    dv = _f64(dia_val).reshape(-1)
+    nd = off.size
+    assert dv.size == nd * n
+    rp = np.zeros(n + 1, dtype=np.int32)
+    nnz = lib().orc_dia_to_csr(n, nd, _p(off), _p(dv), _p(rp), None, None, 0)
+    if nnz < 0:
+        raise ValueError("offsets must be strictly increasing")
+    col = np.zeros(max(nnz, 1), dtype=np.int32)
+    val = np.zeros(max(nnz, 1), dtype=np.float64)
+    got = lib().orc_dia_to_csr(n, nd, _p(off), _p(dv), _p(rp), _p(col), _p(val), nnz)
+    assert got == nnz
+    return rp, col[:nnz], val[:nnz]
+
 
 def stream_direct(A, B, Cv):
     Cv = _f64(Cv).copy()

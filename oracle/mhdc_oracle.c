@@ -459,6 +459,39 @@ void orc_mhdc_absrow(int64_t n, int64_t bl, const int32_t *dia_ptr, const int32_
 
 /* ------------------------------------------------------------------------ */
 /* The memory benchmarks of Sec. 6.2 (Figs. 19 and 20), FP64 with INT32 index. */
+/* ------------------------------------------------------------------------ */
+/* DIA input (Sec. 3.3, Fig. 4) -> CSR (Sec. 3.2).  val[d * n + i] holds
+ * a(i, i + offset[d]) for the nd diagonals (offsets strictly increasing);
+ * positions with i + offset[d] outside [0, n) and zero values are not
+ * entries (the structural reading: a zero stored in DIA is padding).
+ * Columns of a row come out increasing because the offsets are.  Pass
+ * row_ptr only (col, out = NULL) to count; returns nnz, or -1 when the
+ * offsets are not strictly increasing or cap is too small. */
+int64_t orc_dia_to_csr(int64_t n, int64_t nd, const int32_t *offset, const double *val,
+                       int32_t *row_ptr, int32_t *col, double *out, int64_t cap)
+{
+    for (int64_t d = 1; d < nd; d++)
+        if (offset[d] <= offset[d - 1]) return -1;
+    int64_t k = 0;
+    row_ptr[0] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        for (int64_t d = 0; d < nd; d++) {
+            const int64_t j = i + offset[d];
+            if (j < 0 || j >= n) continue;
+            const double a = val[d * n + i];
+            if (a == 0.0) continue;
+            if (col) {
+                if (k >= cap) return -1;
+                col[k] = (int32_t)j;
+                out[k] = a;
+            }
+            k++;
+        }
+        row_ptr[i + 1] = (int32_t)k;
+    }
+    return k;
+}
+
 void orc_stream_direct(int64_t N, const double *A, const double *B, double *C)
 {
     for (int64_t i = 0; i < N; i++) C[i] += A[i] * B[i];

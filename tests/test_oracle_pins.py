@@ -37,6 +37,35 @@ def test_example_dia_matches_fig4():
     assert H["csr_col"].size == 0
 
 
+def test_dia_input_of_fig4_gives_the_csr_of_fig3():
+    g = read_golden("example_dia.txt")
+    c = read_golden("example_csr.txt")
+    dv = np.array([g[f"val{k}"] for k in range(5)], dtype=np.float64)
+    rp, col, val = oracle.dia_to_csr(8, g["offset"], dv)
+    assert rp.tolist() == c["row_ptr"] and col.tolist() == c["col_ind"] and val.tolist() == c["val"]
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_dia_input_round_trip_through_a_dense_matrix(seed):
+    # a random sparse matrix written out as DIA by a dense scan (every offset
+    # with a nonzero, a(i, i+d) or 0), read back: the same CSR
+    A = synth.random_sparse(60 + 13 * seed, 0.05, seed=seed, diag_bias=0.5)
+    d = np.zeros((A.n, A.n))
+    for i in range(A.n):
+        d[i, A.col[A.row_ptr[i]:A.row_ptr[i + 1]]] = A.val[A.row_ptr[i]:A.row_ptr[i + 1]]
+    offs = sorted({int(j - i) for i, j in zip(*np.nonzero(d))})
+    dv = np.zeros((len(offs), A.n))
+    for k, o in enumerate(offs):
+        for i in range(A.n):
+            if 0 <= i + o < A.n:
+                dv[k, i] = d[i, i + o]
+    rp, col, val = oracle.dia_to_csr(A.n, offs, dv)
+    assert np.array_equal(rp, A.row_ptr) and np.array_equal(col, A.col)
+    assert np.array_equal(val, A.val)
+    with pytest.raises(ValueError):
+        oracle.dia_to_csr(A.n, offs[::-1], dv)
+
+
 def test_example_hdc_matches_fig7():
     g = read_golden("example_hdc_theta06.txt")
     H = oracle.hdc_global(synth.example_matrix(), g["theta"][0])
