@@ -116,6 +116,29 @@ int hdc_build(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const d
               int32_t n_b, double theta, int32_t dtype, void *stream, mhdc_handle *out);
 
 /*
+ * mhdc_build_dia -- the M-HDC format straight from DIA input (the layout of
+ * Sec. 3.3, Fig. 4), as a stencil code holds its matrix, without a CSR copy.
+ * The entries are the positions (i, i + offset[d]) inside the matrix whose
+ * value is nonzero; the handle equals the one mhdc_build gives for the CSR
+ * matrix of those entries (same selection of Sec. 4.3, layout of Fig. 12,
+ * rounding, remainder in column order), entirely on the device.
+ *
+ *   n          rows (= columns), 1 <= n < 2^31 - 1; entries fewer than 2^31
+ *   nd         number of diagonals, 0 <= nd <= 65535
+ *   d_offset   int32[nd] (device), strictly increasing, each in (-n, n)
+ *   d_val      double[nd * n] (device): d_val[d * n + i] = a(i, i + offset[d]);
+ *              values at positions outside the matrix are ignored, zeros
+ *              are not entries
+ *   n_b, theta, dtype, stream, out   as mhdc_build (the call synchronizes)
+ *
+ * The arrays are read only during the call.  Errors: MHDC_ERR_INVALID_ARG
+ * for bad sizes or offsets (checked on the device), MHDC_ERR_UNSUPPORTED for
+ * 2^31 or more entries, MHDC_ERR_OOM / MHDC_ERR_CUDA.
+ */
+int mhdc_build_dia(int64_t n, int32_t nd, const int32_t *d_offset, const double *d_val, int32_t n_b,
+                   double theta, int32_t dtype, void *stream, mhdc_handle *out);
+
+/*
  * mhdc_spmv -- y = A x with the M-HDC kernel (Fig. 13): for every row block,
  * the remainder rows plus, for each of the block's diagonals, dia_val * x
  * shifted by its offset; y is written once per row (overwritten).

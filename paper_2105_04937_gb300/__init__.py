@@ -21,7 +21,7 @@ from .build import SO, build as _build_library  # noqa: F401  (re-exported for b
 
 __all__ = [
     "MHDC_F64", "MHDC_F32", "MHDC_BF16", "MhdcError", "Matrix", "lib", "mhdc_build",
-    "hdc_build", "mhdc_spmv", "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
+    "hdc_build", "mhdc_build_dia", "mhdc_dia_spmv", "mhdc_spmv", "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
     "mhdc_info", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
     "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "mhdc_check",
     "mhdc_read_bench", "mhdc_read_bench_ctas", "mhdc_build_noalloc",
@@ -63,6 +63,7 @@ _P, _I64, _I32, _D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
 _SIGS = {
     "mhdc_build": [_I64, _P, _P, _P, _I32, _D, _I32, _P, C.POINTER(C.c_void_p)],
     "hdc_build": [_I64, _P, _P, _P, _I32, _D, _I32, _P, C.POINTER(C.c_void_p)],
+    "mhdc_build_dia": [_I64, _I32, _P, _P, _I32, _D, _I32, _P, C.POINTER(C.c_void_p)],
     "mhdc_spmv": [_P, _P, _P, _P],
     "mhdc_spmv_host": [_P, _P, _P, _P],
     "mhdc_dia_spmv": [_P, _P, _P, _P],
@@ -224,6 +225,22 @@ def mhdc_build(n, row_ptr, col, val, n_b, theta, dtype="f64", stream=None) -> Ma
 def hdc_build(n, row_ptr, col, val, n_b, theta, dtype="f64", stream=None) -> Matrix:
     """CSR -> HDC (global selection, Sec. 3.4) stored blocked for the B-HDC kernel."""
     return _build("hdc_build", n, row_ptr, col, val, n_b, theta, dtype, stream)
+
+
+def mhdc_build_dia(n, offsets, dia_val, n_b, theta, dtype="f64", stream=None) -> Matrix:
+    """DIA input (device int32 offsets[nd], float64 dia_val[nd, n] with
+    dia_val[d, i] = a(i, i + offsets[d])) -> M-HDC handle, without CSR."""
+    import torch
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    nd = int(offsets.numel())
+    _check_dev(offsets, torch.int32, nd, "offsets")
+    _check_dev(dia_val, torch.float64, nd * n, "dia_val")
+    h = C.c_void_p()
+    rc = lib().mhdc_build_dia(n, nd, _ptr(offsets), _ptr(dia_val), int(n_b), float(theta),
+                              int(dtype), _stream(stream), C.byref(h))
+    _check(rc, "mhdc_build_dia")
+    return Matrix(h.value, n)
 
 
 def _xy_types(A: Matrix):

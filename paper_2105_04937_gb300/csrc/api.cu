@@ -49,6 +49,12 @@ int mhdc_build(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const 
                         (cudaStream_t)stream, out);
 }
 
+int mhdc_build_dia(int64_t n, int32_t nd, const int32_t *d_offset, const double *d_val, int32_t n_b,
+                   double theta, int32_t dtype, void *stream, mhdc_handle *out)
+{
+    return build_matrix_dia(n, nd, d_offset, d_val, n_b, theta, dtype, (cudaStream_t)stream, out);
+}
+
 int hdc_build(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
               int32_t n_b, double theta, int32_t dtype, void *stream, mhdc_handle *out)
 {

@@ -1184,6 +1184,297 @@ int build_matrix(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, cons
     return MHDC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// M-HDC straight from DIA input (Sec. 3.3, Fig. 4 layout: val[d * n + i] =
+// a(i, i + offset[d])), as a stencil code holds its matrix: no CSR copy.
+// Entries are the in-range positions with a nonzero value, so the result is
+// the one mhdc_build gives for the CSR matrix of those entries (the same
+// counts, selection, rounding, padding and remainder order).  Every pass is
+// an elementwise walk over the DIA array (coalesced).
+// ---------------------------------------------------------------------------
+namespace {
+
+// err |= 1: an offset outside (-n, n); 2: offsets not strictly increasing
+__global__ void k_dia_check(int32_t nd, int64_t n, const int32_t *__restrict__ off, int *err)
+{
+    const int32_t d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= nd) return;
+    const int64_t o = off[d];
+    if (o <= -n || o >= n) atomicOr(err, 1);
+    if (d > 0 && (int64_t)off[d - 1] >= o) atomicOr(err, 2);
+}
+
+__device__ __forceinline__ bool dia_entry(const double *__restrict__ val, const int32_t *__restrict__ off,
+                                          int64_t n, int32_t d, int64_t i, double *v)
+{
+    const int64_t j = i + off[d];
+    if (j < 0 || j >= n) return false;
+    *v = val[(int64_t)d * n + i];
+    return *v != 0.0;
+}
+
+// cnt[ib * nd + d] = entries of diagonal d = blockIdx.y in row block ib; one
+// atomic per warp and block (lanes of one block grouped by a warp match)
+__global__ void __launch_bounds__(256)
+k_dia_count(int64_t n, int32_t n_b, int32_t nd, const int32_t *__restrict__ off,
+            const double *__restrict__ val, int32_t *cnt, unsigned long long *total)
+{
+    const int32_t d = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; i0 < n; i0 += stride) {
+        const int64_t i = i0 + lane;
+        double v;
+        const bool e = i < n && dia_entry(val, off, n, d, i, &v);
+        const int64_t ib = (i < n ? i : n - 1) / n_b;
+        const unsigned grp = __match_any_sync(0xffffffffu, (unsigned long long)ib);
+        const unsigned hits = __ballot_sync(0xffffffffu, e) & grp;
+        if (lane == __ffs(grp) - 1 && hits) {
+            atomicAdd(&cnt[ib * nd + d], __popc(hits));
+            atomicAdd(total, (unsigned long long)__popc(hits));
+        }
+    }
+}
+
+// Selection (Sec. 4.3): keep[ib * nd + d] = count >= 1 and >= theta * rows(ib)
+__global__ void k_dia_select(int64_t n, int32_t n_b, int64_t nb, int32_t nd, double theta,
+                             const int32_t *__restrict__ cnt, int32_t *keep, int32_t *sel_cnt)
+{
+    const int64_t ib = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ib >= nb) return;
+    const int64_t r0 = ib * (int64_t)n_b;
+    const double thr = theta * (double)((n - r0 < n_b) ? (n - r0) : n_b);
+    int32_t S = 0;
+    for (int32_t d = 0; d < nd; d++) {
+        const int32_t c = cnt[ib * nd + d];
+        const int32_t k = (c >= 1 && (double)c >= thr) ? 1 : 0;
+        keep[ib * nd + d] = k;
+        S += k;
+    }
+    sel_cnt[ib] = S;
+}
+
+// dia_offset and, per partial diagonal p, its source (block, diagonal);
+// keep[] becomes the position p of a kept diagonal, -1 otherwise
+__global__ void k_dia_place(int64_t nb, int32_t nd, const int32_t *__restrict__ off,
+                            const int32_t *__restrict__ dia_ptr, int32_t *keep,
+                            int32_t *dia_offset, int32_t *src_d, int32_t *src_b)
+{
+    const int64_t ib = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ib >= nb) return;
+    int32_t p = dia_ptr[ib];
+    for (int32_t d = 0; d < nd; d++) {
+        if (keep[ib * nd + d]) {
+            dia_offset[p] = off[d];
+            src_d[p] = d;
+            src_b[p] = (int32_t)ib;
+            keep[ib * nd + d] = p++;
+        } else {
+            keep[ib * nd + d] = -1;
+        }
+    }
+}
+
+// dia_val slot (p, t): the value rounded to the storage type, +0.0 where
+// there is no entry (past the matrix end, outside the columns, or zero)
+template <typename VT>
+__global__ void k_dia_fill(int64_t n, int32_t n_b, int64_t P, const int32_t *__restrict__ off,
+                           const double *__restrict__ val, const int32_t *__restrict__ src_d,
+                           const int32_t *__restrict__ src_b, VT *__restrict__ dia_val)
+{
+    const int64_t total = P * n_b;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = q / n_b;
+        const int64_t i = (int64_t)src_b[p] * n_b + (q - p * n_b);
+        double v = 0.0;
+        if (!(i < n && dia_entry(val, off, n, src_d[p], i, &v))) v = 0.0;
+        dia_val[q] = round_store<VT>(v);
+    }
+}
+
+// per row: entries on the diagonals its block does not keep
+__global__ void k_dia_rem_count(int64_t n, int32_t n_b, int32_t nd, const int32_t *__restrict__ off,
+                                const double *__restrict__ val, const int32_t *__restrict__ keep,
+                                int32_t *rem)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t *kb = keep + (i / n_b) * nd;
+    int32_t c = 0;
+    for (int32_t d = 0; d < nd; d++) {
+        double v;
+        if (kb[d] < 0 && dia_entry(val, off, n, d, i, &v)) c++;
+    }
+    rem[i] = c;
+}
+
+// the remainder entries of row i in column order (= ascending offsets)
+template <typename VT>
+__global__ void k_dia_rem_fill(int64_t n, int32_t n_b, int32_t nd, const int32_t *__restrict__ off,
+                               const double *__restrict__ val, const int32_t *__restrict__ keep,
+                               const int32_t *__restrict__ csr_row_ptr, int32_t *__restrict__ csr_col,
+                               VT *__restrict__ csr_val)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t q = csr_row_ptr[i];
+    if (q == csr_row_ptr[i + 1]) return;
+    const int32_t *kb = keep + (i / n_b) * nd;
+    for (int32_t d = 0; d < nd; d++) {
+        double v;
+        if (kb[d] < 0 && dia_entry(val, off, n, d, i, &v)) {
+            csr_col[q] = (int32_t)(i + off[d]);
+            csr_val[q] = round_store<VT>(v);
+            q++;
+        }
+    }
+}
+
+template <typename VT>
+int dia_fill_all(mhdc_matrix *A, int32_t nd, const int32_t *off, const double *val,
+                 const int32_t *keep, const int32_t *src_d, const int32_t *src_b, cudaStream_t st)
+{
+    const int64_t n = A->n;
+    if (A->P > 0) {
+        const int64_t total = A->P * (int64_t)A->n_b;
+        const unsigned grid = (unsigned)((total + 255) / 256 < 65536 ? (total + 255) / 256 : 65536);
+        k_dia_fill<VT><<<grid, 256, 0, st>>>(n, A->n_b, A->P, off, val, src_d, src_b,
+                                             static_cast<VT *>(A->dia_val));
+        MHDC_LAUNCH_CHECK("k_dia_fill");
+    }
+    Buf rem, scr;
+    RC(dalloc(rem, sizeof(int32_t) * (size_t)n, st));
+    RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(n), st));
+    k_dia_rem_count<<<grid_for(n, 256), 256, 0, st>>>(n, A->n_b, nd, off, val, keep, rem.as<int32_t>());
+    MHDC_LAUNCH_CHECK("k_dia_rem_count");
+    RC(dalloc_raw((void **)&A->csr_row_ptr, sizeof(int32_t) * (size_t)(n + 1)));
+    RC(exclusive_scan_i32(rem.as<int32_t>(), A->csr_row_ptr, n, scr.as<int32_t>(), st));
+    int32_t nr = 0;
+    MHDC_CUDA_TRY(cudaMemcpyAsync(&nr, A->csr_row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                  st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    A->nnz_rem = nr;
+    RC(dalloc_raw((void **)&A->csr_col, sizeof(int32_t) * (size_t)nr));
+    RC(dalloc_raw(&A->csr_val, sizeof(VT) * (size_t)nr));
+    if (nr > 0) {
+        k_dia_rem_fill<VT><<<grid_for(n, 256), 256, 0, st>>>(n, A->n_b, nd, off, val, keep,
+                                                             A->csr_row_ptr, A->csr_col,
+                                                             static_cast<VT *>(A->csr_val));
+        MHDC_LAUNCH_CHECK("k_dia_rem_fill");
+    }
+    return MHDC_OK;
+}
+
+int build_dia_into(mhdc_matrix *A, int32_t nd, const int32_t *off, const double *val,
+                   cudaStream_t st)
+{
+    const int64_t n = A->n, nb = A->n_blocks;
+    RC(dalloc_raw((void **)&A->status, sizeof(int)));
+    MHDC_CUDA_TRY(cudaMemsetAsync(A->status, 0, sizeof(int), st));
+    Buf err, cnt, keep, sel_cnt, scr, total;
+    RC(dalloc(err, sizeof(int), st));
+    MHDC_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    if (nd > 0) {
+        k_dia_check<<<(nd + 255) / 256, 256, 0, st>>>(nd, n, off, err.as<int>());
+        MHDC_LAUNCH_CHECK("k_dia_check");
+    }
+    int h_err = 0;
+    MHDC_CUDA_TRY(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_err) {
+        set_error_msg((h_err & 1) ? "mhdc_build_dia: an offset lies outside (-n, n)"
+                                  : "mhdc_build_dia: offsets not strictly increasing");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    const size_t cells = (size_t)nb * (size_t)(nd > 0 ? nd : 1);
+    RC(dalloc(cnt, sizeof(int32_t) * cells, st));
+    RC(dalloc(keep, sizeof(int32_t) * cells, st));
+    RC(dalloc(sel_cnt, sizeof(int32_t) * (size_t)nb, st));
+    RC(dalloc(total, sizeof(unsigned long long), st));
+    MHDC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * cells, st));
+    MHDC_CUDA_TRY(cudaMemsetAsync(total.p, 0, sizeof(unsigned long long), st));
+    if (nd > 0) {
+        const int64_t gx = (n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048;
+        k_dia_count<<<dim3((unsigned)gx, (unsigned)nd), 256, 0, st>>>(
+            n, A->n_b, nd, off, val, cnt.as<int32_t>(), total.as<unsigned long long>());
+        MHDC_LAUNCH_CHECK("k_dia_count");
+    }
+    k_dia_select<<<grid_for(nb, 256), 256, 0, st>>>(n, A->n_b, nb, nd, A->theta, cnt.as<int32_t>(),
+                                                     keep.as<int32_t>(), sel_cnt.as<int32_t>());
+    MHDC_LAUNCH_CHECK("k_dia_select");
+    RC(dalloc_raw((void **)&A->dia_ptr, sizeof(int32_t) * (size_t)(nb + 1)));
+    RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(nb), st));
+    RC(exclusive_scan_i32(sel_cnt.as<int32_t>(), A->dia_ptr, nb, scr.as<int32_t>(), st));
+    int32_t P = 0;
+    unsigned long long nnz = 0;
+    MHDC_CUDA_TRY(cudaMemcpyAsync(&P, A->dia_ptr + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaMemcpyAsync(&nnz, total.p, sizeof nnz, cudaMemcpyDeviceToHost, st));
+    MHDC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (nnz >= (unsigned long long)INT32_MAX) {
+        set_error_msg("mhdc_build_dia: more than 2^31 - 1 entries");
+        return MHDC_ERR_UNSUPPORTED;
+    }
+    A->nnz = (int64_t)nnz;
+    A->P = P;
+    Buf src_d, src_b;
+    RC(dalloc(src_d, sizeof(int32_t) * (size_t)P, st));
+    RC(dalloc(src_b, sizeof(int32_t) * (size_t)P, st));
+    RC(dalloc_raw((void **)&A->dia_offset, sizeof(int32_t) * (size_t)P));
+    RC(dalloc_raw(&A->dia_val, value_size(A->dtype) * (size_t)P * (size_t)A->n_b));
+    k_dia_place<<<grid_for(nb, 256), 256, 0, st>>>(nb, nd, off, A->dia_ptr, keep.as<int32_t>(),
+                                                    A->dia_offset, src_d.as<int32_t>(),
+                                                    src_b.as<int32_t>());
+    MHDC_LAUNCH_CHECK("k_dia_place");
+    switch (A->dtype) {
+    case MHDC_F64:
+        RC(dia_fill_all<double>(A, nd, off, val, keep.as<int32_t>(), src_d.as<int32_t>(),
+                                src_b.as<int32_t>(), st));
+        break;
+    case MHDC_F32:
+        RC(dia_fill_all<float>(A, nd, off, val, keep.as<int32_t>(), src_d.as<int32_t>(),
+                               src_b.as<int32_t>(), st));
+        break;
+    default:
+        RC(dia_fill_all<__nv_bfloat16>(A, nd, off, val, keep.as<int32_t>(), src_d.as<int32_t>(),
+                                       src_b.as<int32_t>(), st));
+        break;
+    }
+    RC(finish_stats(A, st));
+    A->spmv_grid = spmv_grid_for(A);
+    return MHDC_OK;
+}
+
+}  // namespace
+
+int build_matrix_dia(int64_t n, int32_t nd, const int32_t *d_offset, const double *d_val,
+                     int32_t n_b, double theta, int32_t dtype, cudaStream_t stream,
+                     mhdc_matrix **out)
+{
+    if (!out || n < 1 || n >= INT32_MAX || nd < 0 || nd > 65535 || n_b < 1 ||
+        !std::isfinite(theta) || theta < 0.0 || dtype < MHDC_F64 || dtype > MHDC_BF16 ||
+        (nd > 0 && (!d_offset || !d_val))) {
+        set_error_msg("mhdc_build_dia: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    mhdc_matrix *A = new mhdc_matrix();
+    A->n = n;
+    A->n_b = n_b;
+    A->n_blocks = (n + n_b - 1) / n_b;
+    A->theta = theta;
+    A->dtype = dtype;
+    A->mode = MHDC_MODE_BLOCK;
+    cudaGetDevice(&A->device);
+    int rc = build_dia_into(A, nd, d_offset, d_val, stream);
+    if (rc != MHDC_OK) {
+        cudaStreamSynchronize(stream);
+        free_matrix(A);
+        return rc;
+    }
+    *out = A;
+    return MHDC_OK;
+}
+
 }  // namespace mhdc
 
 namespace mhdc {

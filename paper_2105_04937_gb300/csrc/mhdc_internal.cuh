@@ -85,6 +85,9 @@ inline int cuda_status(cudaError_t e)
 int build_matrix(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
                  int32_t n_b, double theta, int32_t dtype, int mode, cudaStream_t stream,
                  mhdc_matrix **out);
+int build_matrix_dia(int64_t n, int32_t nd, const int32_t *d_offset, const double *d_val,
+                     int32_t n_b, double theta, int32_t dtype, cudaStream_t stream,
+                     mhdc_matrix **out);
 void free_matrix(mhdc_matrix *A);
 int feature_hist(int64_t n, const int32_t *rp, const int32_t *col, int32_t n_b,
                  cudaStream_t st, unsigned long long *h_ent, unsigned long long *h_dia);

@@ -23,7 +23,7 @@ import numpy as np
 __all__ = [
     "CSR", "Rng", "stencil_3d", "paper_stencil", "scattered_diagonals",
     "uniform_vector", "loguniform_vector", "config_matrix", "batch_matrices",
-    "family_params", "family_matrix", "example_matrix",
+    "family_params", "family_matrix", "example_matrix", "dia_matrix", "paper_stencil_offsets",
 ]
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -237,25 +237,7 @@ def paper_stencil(n: int, dim: int, *, seed: int = 0) -> CSR:
     diagonals j = i, i +- 1 (1D), also i +- n_x with n_x = floor(sqrt n) (2D),
     also i +- n_x^2 with n_x = floor(cbrt n) (3D), kept where 0 <= j < n.
     Values as in :func:`stencil_3d`."""
-    if dim == 1:
-        offs = [-1, 0, 1]
-    elif dim == 2:
-        nx = int(np.floor(np.sqrt(n)))
-        while (nx + 1) ** 2 <= n:
-            nx += 1
-        while nx * nx > n:
-            nx -= 1
-        offs = [-nx, -1, 0, 1, nx]
-    elif dim == 3:
-        nx = int(round(n ** (1.0 / 3.0)))
-        while (nx + 1) ** 3 <= n:
-            nx += 1
-        while nx ** 3 > n:
-            nx -= 1
-        offs = [-nx * nx, -nx, -1, 0, 1, nx, nx * nx]
-    else:
-        raise ValueError("dim must be 1, 2 or 3")
-    offs = sorted(set(offs))
+    offs = paper_stencil_offsets(n, dim)
     i = np.arange(n, dtype=np.int64)
     cols = i[:, None] + np.array(offs, dtype=np.int64)[None, :]
     mask = (cols >= 0) & (cols < n)
@@ -263,6 +245,48 @@ def paper_stencil(n: int, dim: int, *, seed: int = 0) -> CSR:
     row_ptr, col = _from_sorted_keys(n, keys)
     val = _dominant_values(n, row_ptr, col, Rng(seed, 3))
     return CSR(n, row_ptr, col, val, dict(kind="paper_stencil", dim=dim, n=n, seed=seed))
+
+
+def paper_stencil_offsets(n: int, dim: int) -> list[int]:
+    """Offsets of the paper's 1D/2D/3D stencils (Sec. 6.3) for n rows."""
+    if dim == 1:
+        return [-1, 0, 1]
+    if dim == 2:
+        nx = int(np.floor(np.sqrt(n)))
+        while (nx + 1) ** 2 <= n:
+            nx += 1
+        while nx * nx > n:
+            nx -= 1
+        return sorted({-nx, -1, 0, 1, nx})
+    if dim == 3:
+        nx = int(round(n ** (1.0 / 3.0)))
+        while (nx + 1) ** 3 <= n:
+            nx += 1
+        while nx ** 3 > n:
+            nx -= 1
+        return sorted({-nx * nx, -nx, -1, 0, 1, nx, nx * nx})
+    raise ValueError("dim must be 1, 2 or 3")
+
+
+def dia_matrix(n: int, offsets, *, seed: int, zero_rate: float = 0.0,
+               pad: float = float("nan")) -> tuple[np.ndarray, np.ndarray]:
+    """A seeded matrix in DIA input layout (Sec. 3.3, Fig. 4): returns
+    (offsets int32[nd], val float64[nd, n]) with val[d, i] = a(i, i + offsets[d])
+    drawn U[-1, 1] without exact zeros, a random ``zero_rate`` share of them
+    set to 0.0 (positions without an entry), and ``pad`` at the positions
+    outside the matrix (which the format ignores)."""
+    off = np.asarray(sorted(set(int(o) for o in offsets)), dtype=np.int32)
+    nd = off.size
+    rng = Rng(seed, 17)
+    val = rng.uniform(nd * n, -1.0, 1.0).reshape(nd, n)
+    val[val == 0.0] = 0.5
+    if zero_rate > 0:
+        val[rng.bernoulli(nd * n, zero_rate).reshape(nd, n)] = 0.0
+    i = np.arange(n, dtype=np.int64)
+    for k, o in enumerate(off.tolist()):
+        out = (i + o < 0) | (i + o >= n)
+        val[k, out] = pad
+    return off, val
 
 
 def _loguniform(rng: Rng, k: int, lo_exp: float = -3.0, hi_exp: float = 3.0) -> np.ndarray:

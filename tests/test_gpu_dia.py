@@ -107,3 +107,89 @@ def test_dia_rejects_block_mode_and_handles_empty(mh):
     E = synth.CSR(300, np.zeros(301, np.int32), np.zeros(0, np.int32), np.zeros(0))
     h, M = check_build(mh, E, 64, 0.5, "f64", mode="global")
     dia_matches_blocked(mh, h, M, E, synth.uniform_vector(300, 1), "f64")
+
+
+# ---------------------------------------------------------------- DIA input (mhdc_build_dia)
+
+def _dia_case(mh, n, offs, val, n_b, theta, dt, x=None):
+    """mhdc_build_dia against the oracle's conversion of the same entries
+    (oracle.dia_to_csr, then oracle.convert): every array bit-exact, then
+    the product within the stated bounds."""
+    from gpu_util import assert_same_structure
+    t = torch()
+    rp, col, v = oracle.dia_to_csr(n, offs, val)
+    A = synth.CSR(n, rp, col, v, {})
+    M = oracle.convert(A, n_b, theta, dt)
+    h = mh.mhdc_build_dia(n, t.from_numpy(np.ascontiguousarray(offs, np.int32)).cuda(),
+                          t.from_numpy(np.ascontiguousarray(val, np.float64)).cuda(), n_b, theta, dt)
+    assert_same_structure(mh.mhdc_export(h), M, (n, n_b, theta, dt))
+    inf = h.info
+    assert inf["nnz"] == A.nnz and inf["P"] == M["P"] and inf["nnz_rem"] == M["nnz_rem"]
+    if x is not None:
+        check_spmv(mh, h, M, A, x, dt)
+    return h
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_dia_input_random(mh, seed):
+    rng = synth.Rng(seed, 23)
+    n = int(rng.integers(1, 2, 260)[0])
+    k = int(rng.integers(1, 1, 12)[0])
+    offs = sorted({int(o) for o in rng.integers(k, -(n - 1), n)} | {0, n - 1, -(n - 1)})
+    x = synth.uniform_vector(n, seed)
+    for zr in (0.0, 0.3, 0.9):
+        off, val = synth.dia_matrix(n, offs, seed=seed, zero_rate=zr)
+        for n_b in sorted({1, 3, 8, 64, 100, n, 2 * n + 1}):
+            for theta in (0.0, 0.5, 0.9):
+                for dt in ("f64", "f32", "bf16"):
+                    _dia_case(mh, n, off, val, n_b, theta, dt, x if theta == 0.5 else None)
+
+
+def test_dia_input_paper_stencils(mh):
+    for dim in (1, 2, 3):
+        n = 50000
+        off, val = synth.dia_matrix(n, synth.paper_stencil_offsets(n, dim), seed=dim,
+                                    zero_rate=0.1)
+        x = synth.uniform_vector(n, dim)
+        for n_b in (10, 500, 4096):
+            for dt in ("f64", "f32", "bf16"):
+                _dia_case(mh, n, off, val, n_b, 0.6, dt, x)
+
+
+def test_dia_input_large_equals_csr_build(mh):
+    # 3D 7-point stencil, n = 1e7, 5% zeros: the handle from DIA input equals
+    # the handle built from the CSR of the same entries
+    t = torch()
+    n = 10_000_000
+    off, val = synth.dia_matrix(n, synth.paper_stencil_offsets(n, 3), seed=5, zero_rate=0.05)
+    rp, col, v = oracle.dia_to_csr(n, off, val)
+    h1 = mh.mhdc_build_dia(n, t.from_numpy(off).cuda(), t.from_numpy(val).cuda(), 4096, 0.6)
+    h2 = mh.mhdc_build(n, t.from_numpy(rp).cuda(), t.from_numpy(col).cuda(), t.from_numpy(v).cuda(),
+                       4096, 0.6)
+    E1, E2 = mh.mhdc_export(h1), mh.mhdc_export(h2)
+    for k in E1:
+        assert np.array_equal(np.asarray(E1[k]).view(np.uint8), np.asarray(E2[k]).view(np.uint8)), k
+    A = synth.CSR(n, rp, col, v, {})
+    x = synth.uniform_vector(n, 6)
+    y = y_empty(n, "f64")
+    mh.mhdc_spmv(h1, t.from_numpy(x).cuda(), y)
+    ref = oracle.csr_spmv(A, x)
+    assert np.all(np.abs(y.cpu().numpy() - ref) <= oracle.FP64_ROW_TOL * oracle.csr_absrow(A, x))
+
+
+def test_dia_input_rejects_bad_offsets(mh):
+    t = torch()
+    n = 100
+    _, val = synth.dia_matrix(n, [-1, 0, 1], seed=1)
+    dv = t.from_numpy(val).cuda()
+    for offs in ([0, -1, 1], [-1, 0, 0], [-100, 0, 1], [-1, 0, 100]):
+        with pytest.raises(mh.MhdcError) as e:
+            mh.mhdc_build_dia(n, t.tensor(offs, dtype=t.int32, device="cuda"), dv, 16, 0.5)
+        assert e.value.code == mh.MHDC_ERR_INVALID_ARG
+    # no diagonals at all: every row empty
+    h = mh.mhdc_build_dia(n, t.zeros(0, dtype=t.int32, device="cuda"),
+                          t.zeros(1, dtype=t.float64, device="cuda"), 16, 0.5)
+    assert h.info["nnz"] == 0 and h.info["P"] == 0
+    y = y_empty(n, "f64")
+    mh.mhdc_spmv(h, t.ones(n, dtype=t.float64, device="cuda"), y)
+    assert t.all(y == 0)
