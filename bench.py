@@ -404,7 +404,58 @@ def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
     out["a9_batched_fp64"] = bt
     log(f"batched: {json.dumps(bt)}")
     out["a10_select"] = measure_selector(mh, torch, A, rp, col, val, log)
+    out["a2_a4_conversion"] = measure_conversion(mh, torch, stream, log)
     return out
+
+
+def measure_conversion(mh, torch, stream, log):
+    """Conversion on the 3D 7-point stencil of Sec. 6.3 with 10^7 rows: from
+    CSR (mhdc_build) and straight from DIA input (mhdc_build_dia), each the
+    mean of five builds after a first one, against the product time and the
+    CSR kernel's (products needed to repay the conversion)."""
+    import synth
+    n = 10_000_000
+    offs = synth.paper_stencil_offsets(n, 3)
+    C = synth.paper_stencil(n, 3)
+    rp = torch.from_numpy(C.row_ptr).cuda()
+    col = torch.from_numpy(C.col).cuda()
+    val = torch.from_numpy(C.val).cuda()
+    off, dv = synth.dia_matrix(n, offs, seed=4)
+    offd = torch.from_numpy(off).cuda()
+    dvd = torch.from_numpy(dv).cuda()
+    del dv
+
+    def timed(make):
+        h = make()
+        h.destroy()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(5):
+            h = make()
+            h.destroy()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) * 1e3 / 5
+
+    ms_csr = timed(lambda: mh.mhdc_build(n, rp, col, val, N_B, THETA, "f64"))
+    ms_dia = timed(lambda: mh.mhdc_build_dia(n, offd, dvd, N_B, THETA, "f64"))
+    H = mh.mhdc_build(n, rp, col, val, N_B, THETA, "f64")
+    x = torch.from_numpy(synth.uniform_vector(n, 5)).cuda()
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    best, times = mh.mhdc_tune(H, x, y)
+    best = min(mh.NATIVE_VARIANTS, key=lambda v: times[v])
+    mh.mhdc_set_variant(H, best)
+    us_mhdc = _mean_launch_us(lambda: mh.mhdc_spmv(H, x, y, stream), 200, 5, stream, torch)
+    us_csr = _mean_launch_us(lambda: mh.csr_spmv(n, rp, col, val, x, y, stream), 200, 5, stream,
+                             torch)
+    H.destroy()
+    gain = us_csr - us_mhdc
+    res = {"workload": "paper 3D 7-point stencil, n = 1e7 (Sec. 6.3), FP64, n_b=4096, theta=0.6",
+           "nnz": C.nnz, "build_from_csr_ms": round(ms_csr, 3), "build_from_dia_ms": round(ms_dia, 3),
+           "mhdc_us": round(us_mhdc, 2), "csr_us": round(us_csr, 2),
+           "break_even_products_from_csr": round(ms_csr * 1e3 / gain, 1) if gain > 0 else None,
+           "break_even_products_from_dia": round(ms_dia * 1e3 / gain, 1) if gain > 0 else None}
+    log(f"conversion: {json.dumps(res)}")
+    return res
 
 
 def measure_selector(mh, torch, A, rp, col, val, log):
