@@ -34,6 +34,7 @@ extern "C" {
 #endif
 
 typedef struct mhdc_matrix *mhdc_handle;
+typedef struct sell_matrix *sell_handle;
 
 /* Storage precision of matrix values and x. */
 enum mhdc_dtype { MHDC_F64 = 0, MHDC_F32 = 1, MHDC_BF16 = 2 };
@@ -427,6 +428,38 @@ int mhdc_build_noalloc(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col
                        int32_t *d_dia_ptr, int32_t *d_dia_offset, void *d_dia_val, int64_t cap_P,
                        int32_t *d_csr_row_ptr, int32_t *d_csr_col, void *d_csr_val,
                        int64_t cap_rem, int64_t *h_P, int64_t *h_nnz_rem, void *stream);
+
+/*
+ * SELL-C-sigma baseline (Kreutzer, Hager, Wellein, Fehske, Bishop, SIAM J.
+ * Sci. Comput. 36(5), 2014): the ELL-type format the paper leaves to future
+ * work (Sec. 7), for comparison with CSR and M-HDC on the same GPU.  FP64.
+ *
+ * sell_build -- from CSR (arrays as mhdc_build, not checked beyond
+ *   row_ptr[n]): rows sorted by length, longest first, inside windows of
+ *   sigma rows (ties keep input order); chunks of C consecutive sorted rows,
+ *   each padded to its longest row and stored column by column (slot
+ *   chunk_ptr[c] + k * C + r holds entry k of row r of chunk c; padding:
+ *   column 0, value +0.0).  1 <= C <= 1024 (32 = one warp per chunk),
+ *   1 <= sigma <= 8192 (1: no sorting).  Synchronizes `stream`; *out
+ *   receives the handle (device memory owned by it).
+ * sell_spmv -- y = A x (FP64 device arrays of n values; must not overlap):
+ *   one thread per sorted row sums its own entries (never the padding) in
+ *   column order with one FMA each, so y is bit-identical to csr_spmv.
+ *   Asynchronous on `stream`.
+ * sell_info -- rows, entries, stored slots (entries + padding), chunks.
+ * sell_export -- copy perm[n] (input row of each sorted position),
+ *   rowlen[n] (its length), chunk_ptr[chunks + 1], col[slots], val[slots] to
+ *   host memory; any pointer may be NULL.  Synchronous.
+ * sell_destroy -- free the handle (waits for the device).
+ * Errors as mhdc_build; MHDC_ERR_UNSUPPORTED past 2^31 - 1 slots.
+ */
+int sell_build(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
+               int32_t C, int32_t sigma, void *stream, sell_handle *out);
+int sell_spmv(sell_handle S, const double *d_x, double *d_y, void *stream);
+int sell_info(sell_handle S, int64_t *n, int64_t *nnz, int64_t *slots, int64_t *chunks);
+int sell_export(sell_handle S, int32_t *h_perm, int32_t *h_rowlen, int32_t *h_chunk_ptr,
+                int32_t *h_col, double *h_val);
+int sell_destroy(sell_handle S);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,8 @@ from .build import SO, build as _build_library  # noqa: F401  (re-exported for b
 
 __all__ = [
     "MHDC_F64", "MHDC_F32", "MHDC_BF16", "MhdcError", "Matrix", "lib", "mhdc_build",
-    "hdc_build", "mhdc_build_dia", "mhdc_dia_spmv", "mhdc_spmv", "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
+    "hdc_build", "mhdc_build_dia", "mhdc_dia_spmv", "Sell", "sell_build", "sell_spmv",
+    "sell_info", "sell_export", "sell_destroy", "mhdc_spmv", "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
     "mhdc_info", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
     "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "mhdc_check",
     "mhdc_read_bench", "mhdc_read_bench_ctas", "mhdc_build_noalloc",
@@ -64,6 +65,11 @@ _SIGS = {
     "mhdc_build": [_I64, _P, _P, _P, _I32, _D, _I32, _P, C.POINTER(C.c_void_p)],
     "hdc_build": [_I64, _P, _P, _P, _I32, _D, _I32, _P, C.POINTER(C.c_void_p)],
     "mhdc_build_dia": [_I64, _I32, _P, _P, _I32, _D, _I32, _P, C.POINTER(C.c_void_p)],
+    "sell_build": [_I64, _P, _P, _P, _I32, _I32, _P, C.POINTER(C.c_void_p)],
+    "sell_spmv": [_P, _P, _P, _P],
+    "sell_info": [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)],
+    "sell_export": [_P, _P, _P, _P, _P, _P],
+    "sell_destroy": [_P],
     "mhdc_spmv": [_P, _P, _P, _P],
     "mhdc_spmv_host": [_P, _P, _P, _P],
     "mhdc_dia_spmv": [_P, _P, _P, _P],
@@ -241,6 +247,73 @@ def mhdc_build_dia(n, offsets, dia_val, n_b, theta, dtype="f64", stream=None) ->
                               int(dtype), _stream(stream), C.byref(h))
     _check(rc, "mhdc_build_dia")
     return Matrix(h.value, n)
+
+
+class Sell:
+    """A SELL-C-sigma handle (device memory freed by destroy() or on collection)."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = handle
+        self.n = n
+
+    @property
+    def info(self) -> dict:
+        return sell_info(self)
+
+    def destroy(self):
+        if self.handle:
+            lib().sell_destroy(C.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sell_build(n, row_ptr, col, val, C_=32, sigma=256, stream=None) -> Sell:
+    """CSR (device int32 row_ptr/col, float64 val) -> SELL-C-sigma handle."""
+    import torch
+    _check_dev(row_ptr, torch.int32, n + 1, "row_ptr")
+    _check_dev(col, torch.int32, None, "col")
+    _check_dev(val, torch.float64, None, "val")
+    h = C.c_void_p()
+    _check(lib().sell_build(n, _ptr(row_ptr), _ptr(col), _ptr(val), int(C_), int(sigma),
+                            _stream(stream), C.byref(h)), "sell_build")
+    return Sell(h.value, n)
+
+
+def sell_spmv(S: Sell, x, y, stream=None):
+    """y = A x with the SELL-C-sigma kernel (FP64)."""
+    import torch
+    _check_dev(x, torch.float64, S.n, "x")
+    _check_dev(y, torch.float64, S.n, "y")
+    _check(lib().sell_spmv(C.c_void_p(S.handle), _ptr(x), _ptr(y), _stream(stream)), "sell_spmv")
+    return y
+
+
+def sell_info(S: Sell) -> dict:
+    v = [C.c_int64() for _ in range(4)]
+    _check(lib().sell_info(C.c_void_p(S.handle), *[C.byref(a) for a in v]), "sell_info")
+    return dict(zip(("n", "nnz", "slots", "chunks"), (a.value for a in v)))
+
+
+def sell_export(S: Sell) -> dict:
+    inf = sell_info(S)
+    n, c, s = inf["n"], inf["chunks"], inf["slots"]
+    out = {"perm": np.zeros(n, np.int32), "rowlen": np.zeros(n, np.int32),
+           "chunk_ptr": np.zeros(c + 1, np.int32), "col": np.zeros(max(s, 1), np.int32),
+           "val": np.zeros(max(s, 1), np.float64)}
+    _check(lib().sell_export(C.c_void_p(S.handle), *[out[k].ctypes.data_as(C.c_void_p)
+                                                      for k in ("perm", "rowlen", "chunk_ptr",
+                                                                "col", "val")]), "sell_export")
+    out["col"], out["val"] = out["col"][:s], out["val"][:s]
+    return out
+
+
+def sell_destroy(S: Sell):
+    S.destroy()
 
 
 def _xy_types(A: Matrix):

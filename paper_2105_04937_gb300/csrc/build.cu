@@ -1447,6 +1447,20 @@ int build_dia_into(mhdc_matrix *A, int32_t nd, const int32_t *off, const double 
 
 }  // namespace
 
+int tmp_alloc(void **p, size_t bytes, cudaStream_t st)
+{
+    Buf b;
+    RC(dalloc(b, bytes, st));
+    *p = b.p;
+    b.p = nullptr;  // ownership passes to the caller (tmp_free)
+    return MHDC_OK;
+}
+
+void tmp_free(void *p, cudaStream_t st)
+{
+    if (p) cudaFreeAsync(p, st);
+}
+
 int build_matrix_dia(int64_t n, int32_t nd, const int32_t *d_offset, const double *d_val,
                      int32_t n_b, double theta, int32_t dtype, cudaStream_t stream,
                      mhdc_matrix **out)

@@ -89,6 +89,9 @@ int build_matrix_dia(int64_t n, int32_t nd, const int32_t *d_offset, const doubl
                      int32_t n_b, double theta, int32_t dtype, cudaStream_t stream,
                      mhdc_matrix **out);
 void free_matrix(mhdc_matrix *A);
+// Stream-ordered temporaries from the library's pool (build.cu).
+int tmp_alloc(void **p, size_t bytes, cudaStream_t st);
+void tmp_free(void *p, cudaStream_t st);
 int feature_hist(int64_t n, const int32_t *rp, const int32_t *col, int32_t n_b,
                  cudaStream_t st, unsigned long long *h_ent, unsigned long long *h_dia);
 int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int32_t n_b,
