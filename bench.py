@@ -872,17 +872,20 @@ def main():
                              "gbs": round(csr_bytes / (mean / 1e3) / 1e9, 1),
                              "hbm_frac": round(csr_bytes / (mean / 1e3) / 1e9 / peak, 4),
                              "kernel_us": round(mean * 1e3, 2), "bytes": csr_bytes}
-        # SELL-C-sigma (C = 32, sigma = 256), the ELL-type format of Sec. 7's future work
-        Ss = mh.sell_build(A.n, rp, col, val, 32, 256)
-        si = Ss.info
-        tot, mean_s, _ = time_launches(lambda: mh.sell_spmv(Ss, x, y, stream),
-                                       min(args.steps, 5000), args.warmup, stream, torch)
-        sell_bytes = 12 * si["slots"] + 8 * A.n + 8 * A.n + 8 * A.n + 4 * (si["chunks"] + 1)
-        extra["sell_c32_s256_fp64"] = {
-            "gflops": round(gflops(A.nnz, mean_s / 1e3), 2), "kernel_us": round(mean_s * 1e3, 2),
-            "slots": si["slots"], "padding_frac": round(1 - A.nnz / si["slots"], 4),
-            "gbs": round(sell_bytes / (mean_s / 1e3) / 1e9, 1), "bytes": sell_bytes}
-        Ss.destroy()
+        # SELL-C-sigma (C = 32; sigma = 1: no sorting, 256), the ELL-type format of
+        # Sec. 7's future work
+        for sigma in (1, 256):
+            Ss = mh.sell_build(A.n, rp, col, val, 32, sigma)
+            si = Ss.info
+            tot, mean_s, _ = time_launches(lambda: mh.sell_spmv(Ss, x, y, stream),
+                                           min(args.steps, 5000), args.warmup, stream, torch)
+            sell_bytes = 12 * si["slots"] + 8 * A.n * 3 + 4 * (si["chunks"] + 1)
+            extra[f"sell_c32_s{sigma}_fp64"] = {
+                "gflops": round(gflops(A.nnz, mean_s / 1e3), 2),
+                "kernel_us": round(mean_s * 1e3, 2), "slots": si["slots"],
+                "padding_frac": round(1 - A.nnz / si["slots"], 4),
+                "gbs": round(sell_bytes / (mean_s / 1e3) / 1e9, 1), "bytes": sell_bytes}
+            Ss.destroy()
         # HDC (global selection, B-HDC kernel) on the same matrix (Sec. 3.4, Fig. 10)
         Hh = mh.hdc_build(A.n, rp, col, val, N_B, THETA, "f64")
         ih = Hh.info

@@ -1217,7 +1217,7 @@ __device__ __forceinline__ bool dia_entry(const double *__restrict__ val, const 
 // atomic per warp and block (lanes of one block grouped by a warp match)
 __global__ void __launch_bounds__(256)
 k_dia_count(int64_t n, int32_t n_b, int32_t nd, const int32_t *__restrict__ off,
-            const double *__restrict__ val, int32_t *cnt, unsigned long long *total)
+            const double *__restrict__ val, int32_t *cnt)
 {
     const int32_t d = blockIdx.y;
     const int lane = threadIdx.x & 31;
@@ -1229,29 +1229,30 @@ k_dia_count(int64_t n, int32_t n_b, int32_t nd, const int32_t *__restrict__ off,
         const int64_t ib = (i < n ? i : n - 1) / n_b;
         const unsigned grp = __match_any_sync(0xffffffffu, (unsigned long long)ib);
         const unsigned hits = __ballot_sync(0xffffffffu, e) & grp;
-        if (lane == __ffs(grp) - 1 && hits) {
-            atomicAdd(&cnt[ib * nd + d], __popc(hits));
-            atomicAdd(total, (unsigned long long)__popc(hits));
-        }
+        if (lane == __ffs(grp) - 1 && hits) atomicAdd(&cnt[ib * nd + d], __popc(hits));
     }
 }
 
 // Selection (Sec. 4.3): keep[ib * nd + d] = count >= 1 and >= theta * rows(ib)
 __global__ void k_dia_select(int64_t n, int32_t n_b, int64_t nb, int32_t nd, double theta,
-                             const int32_t *__restrict__ cnt, int32_t *keep, int32_t *sel_cnt)
+                             const int32_t *__restrict__ cnt, int32_t *keep, int32_t *sel_cnt,
+                             unsigned long long *total)
 {
     const int64_t ib = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ib >= nb) return;
     const int64_t r0 = ib * (int64_t)n_b;
     const double thr = theta * (double)((n - r0 < n_b) ? (n - r0) : n_b);
     int32_t S = 0;
+    unsigned long long entries = 0;
     for (int32_t d = 0; d < nd; d++) {
         const int32_t c = cnt[ib * nd + d];
         const int32_t k = (c >= 1 && (double)c >= thr) ? 1 : 0;
         keep[ib * nd + d] = k;
         S += k;
+        entries += (unsigned long long)c;
     }
     sel_cnt[ib] = S;
+    if (entries) atomicAdd(total, entries);  // one atomic per row block
 }
 
 // dia_offset and, per partial diagonal p, its source (block, diagonal);
@@ -1277,19 +1278,21 @@ __global__ void k_dia_place(int64_t nb, int32_t nd, const int32_t *__restrict__ 
 
 // dia_val slot (p, t): the value rounded to the storage type, +0.0 where
 // there is no entry (past the matrix end, outside the columns, or zero)
+// (grid y walks the partial diagonals, grid x the slots of one)
 template <typename VT>
 __global__ void k_dia_fill(int64_t n, int32_t n_b, int64_t P, const int32_t *__restrict__ off,
                            const double *__restrict__ val, const int32_t *__restrict__ src_d,
                            const int32_t *__restrict__ src_b, VT *__restrict__ dia_val)
 {
-    const int64_t total = P * n_b;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = q / n_b;
-        const int64_t i = (int64_t)src_b[p] * n_b + (q - p * n_b);
-        double v = 0.0;
-        if (!(i < n && dia_entry(val, off, n, src_d[p], i, &v))) v = 0.0;
-        dia_val[q] = round_store<VT>(v);
+    for (int64_t p = blockIdx.y; p < P; p += gridDim.y) {
+        const int32_t d = src_d[p];
+        const int64_t r0 = (int64_t)src_b[p] * n_b;
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_b;
+             t += (int64_t)gridDim.x * blockDim.x) {
+            double v = 0.0;
+            if (!(r0 + t < n && dia_entry(val, off, n, d, r0 + t, &v))) v = 0.0;
+            dia_val[p * n_b + t] = round_store<VT>(v);
+        }
     }
 }
 
@@ -1337,10 +1340,10 @@ int dia_fill_all(mhdc_matrix *A, int32_t nd, const int32_t *off, const double *v
 {
     const int64_t n = A->n;
     if (A->P > 0) {
-        const int64_t total = A->P * (int64_t)A->n_b;
-        const unsigned grid = (unsigned)((total + 255) / 256 < 65536 ? (total + 255) / 256 : 65536);
-        k_dia_fill<VT><<<grid, 256, 0, st>>>(n, A->n_b, A->P, off, val, src_d, src_b,
-                                             static_cast<VT *>(A->dia_val));
+        const int64_t gx = ((int64_t)A->n_b + 255) / 256 < 64 ? ((int64_t)A->n_b + 255) / 256 : 64;
+        const int64_t gy = A->P < 65535 ? A->P : 65535;
+        k_dia_fill<VT><<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(
+            n, A->n_b, A->P, off, val, src_d, src_b, static_cast<VT *>(A->dia_val));
         MHDC_LAUNCH_CHECK("k_dia_fill");
     }
     Buf rem, scr;
@@ -1396,12 +1399,13 @@ int build_dia_into(mhdc_matrix *A, int32_t nd, const int32_t *off, const double 
     MHDC_CUDA_TRY(cudaMemsetAsync(total.p, 0, sizeof(unsigned long long), st));
     if (nd > 0) {
         const int64_t gx = (n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048;
-        k_dia_count<<<dim3((unsigned)gx, (unsigned)nd), 256, 0, st>>>(
-            n, A->n_b, nd, off, val, cnt.as<int32_t>(), total.as<unsigned long long>());
+        k_dia_count<<<dim3((unsigned)gx, (unsigned)nd), 256, 0, st>>>(n, A->n_b, nd, off, val,
+                                                                      cnt.as<int32_t>());
         MHDC_LAUNCH_CHECK("k_dia_count");
     }
     k_dia_select<<<grid_for(nb, 256), 256, 0, st>>>(n, A->n_b, nb, nd, A->theta, cnt.as<int32_t>(),
-                                                     keep.as<int32_t>(), sel_cnt.as<int32_t>());
+                                                     keep.as<int32_t>(), sel_cnt.as<int32_t>(),
+                                                     total.as<unsigned long long>());
     MHDC_LAUNCH_CHECK("k_dia_select");
     RC(dalloc_raw((void **)&A->dia_ptr, sizeof(int32_t) * (size_t)(nb + 1)));
     RC(dalloc(scr, sizeof(int32_t) * (size_t)scan_scratch_elems(nb), st));
