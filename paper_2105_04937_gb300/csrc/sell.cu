@@ -124,7 +124,20 @@ k_sell_spmv(int64_t n, int32_t C, const int32_t *__restrict__ perm,
     const int64_t base = chunk_ptr[c] + r;
     const int32_t len = rowlen[pos];
     double s = 0.0;
-    for (int32_t k = 0; k < len; k++) {
+    int32_t k = 0;
+    for (; k + 4 <= len; k += 4) {  // four entries' loads in flight, FMAs in order
+        const int64_t q = base + (int64_t)k * C;
+        const double v0 = __ldg(val + q), v1 = __ldg(val + q + C), v2 = __ldg(val + q + 2 * C),
+                     v3 = __ldg(val + q + 3 * C);
+        const int32_t c0 = __ldg(col + q), c1 = __ldg(col + q + C), c2 = __ldg(col + q + 2 * C),
+                      c3 = __ldg(col + q + 3 * C);
+        const double x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+        s = fma(v0, x0, s);
+        s = fma(v1, x1, s);
+        s = fma(v2, x2, s);
+        s = fma(v3, x3, s);
+    }
+    for (; k < len; k++) {
         const int64_t q = base + (int64_t)k * C;
         s = fma(__ldg(val + q), __ldg(x + __ldg(col + q)), s);
     }
