@@ -811,8 +811,7 @@ def main():
     kernel_name = ("k_mhdc_spmv<double>" if best_variant < 6 else
                    "k_mhdc_spmv_tma<double>" if best_variant < mh.FIRST_EMULATED_VARIANT else
                    "k_split_x + k_mhdc_spmv_dw" if best_variant < 13 else
-                   "k_split_x + k_mhdc_spmv_tma_dw" if best_variant < 16 else
-                   "k_mhdc_spmv_gs<double>")
+                   "k_split_x + k_mhdc_spmv_tma_dw")
 
     peak, peak_src = measured_peak()
     vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]

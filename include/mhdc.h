@@ -226,12 +226,6 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  * the device, and outside that window the product runs the native FP64 path
  * (variant -1's arithmetic) instead.
  *
- * Variants 16 and 17 are the register tiles of variants 5 and 1 run by a
- * persistent grid (SMs x resident CTAs) whose warps walk the tiles with a
- * stride: the same per-row operations (bit-identical y) without a partial
- * last wave of CTAs.  They need n_b to be a multiple of 16 bytes / value
- * size, else they run variant -1.
- *
  * mhdc_set_variant -- use variant v for this handle (-1: default chosen from n_b).
  *                     The first v in 10-15 on an FP64 handle makes its FP32-pair
  *                     arrays (device memory as large as dia_val and csr_val)
@@ -241,7 +235,7 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  *                     times_us is not NULL, each variant's mean time in
  *                     microseconds to times_us[MHDC_NUM_VARIANTS].  Synchronous.
  */
-#define MHDC_NUM_VARIANTS 18
+#define MHDC_NUM_VARIANTS 16
 int mhdc_set_variant(mhdc_handle A, int32_t v);
 int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *best,
               float *times_us);

@@ -121,7 +121,6 @@ int launch_spmv_tma(const mhdc_matrix *A, int shape, const void *d_x, void *d_y,
 constexpr int NUM_REG_VARIANTS = 6;
 constexpr int FIRST_DW_VARIANT = 10;
 constexpr int FIRST_TMA_DW_VARIANT = 13;
-constexpr int FIRST_GS_VARIANT = 16;
 int launch_spmv_tma_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y,
                        unsigned long long epoch, cudaStream_t stream);
 int launch_split_x(mhdc_matrix *A, const void *d_x, unsigned long long epoch, cudaStream_t stream);

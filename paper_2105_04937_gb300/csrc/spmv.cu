@@ -278,23 +278,6 @@ k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
                             csr_val, x, y);
 }
 
-// Persistent register tiles (variants 16, 17): one grid of (SMs x resident
-// CTAs) whose warps walk the tiles with a stride, so no partial last wave of
-// CTAs idles part of the GPU at the end of the launch.
-template <typename VT, int U, int D>
-__global__ void __launch_bounds__(SPMV_THREADS)
-k_mhdc_spmv_gs(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
-               const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
-               const VT *__restrict__ dia_val, const int32_t *__restrict__ csr_row_ptr,
-               const int32_t *__restrict__ csr_col, const VT *__restrict__ csr_val,
-               const typename Tr<VT>::X *__restrict__ x, typename Tr<VT>::Y *__restrict__ y)
-{
-    const int64_t nw = (int64_t)gridDim.x * SPMV_WARPS;
-    for (int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5); w < n_tiles; w += nw)
-        reg_tile<VT, U, D, true>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_val, csr_row_ptr,
-                                 csr_col, csr_val, x, y);
-}
-
 // ---------------------------------------------------------------------------
 // Emulated FP64 product (variants 10-12 of FP64 handles).
 //
@@ -858,44 +841,8 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
     return MHDC_OK;
 }
 
-template <typename VT>
-int launch_gs(const mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_t st)
-{
-    constexpr int V = Tr<VT>::V;
-    const void *fn = shape == 0 ? (const void *)k_mhdc_spmv_gs<VT, 1, 2>
-                                : (const void *)k_mhdc_spmv_gs<VT, 2, 2>;
-    const int rw = 32 * V * (shape == 0 ? 1 : 2);
-    int32_t tpb = (int32_t)((A->n_b + rw - 1) / rw);
-    int64_t tiles = (int64_t)tpb * A->n_blocks;
-    int per_sm = 0;
-    MHDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SPMV_THREADS, 0));
-    int64_t grid = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (tiles + SPMV_WARPS - 1) / SPMV_WARPS;
-    if (grid > need) grid = need;
-    int64_t n = A->n;
-    int32_t n_b = A->n_b;
-    const void *dv = A->dia_val, *cv = A->csr_val;
-    const int32_t *dp = A->dia_ptr, *doff = A->dia_offset, *crp = A->csr_row_ptr, *cc = A->csr_col;
-    void *args[] = {&n, &n_b, &tpb, &tiles, (void *)&dp, (void *)&doff, (void *)&dv, (void *)&crp,
-                    (void *)&cc, (void *)&cv, (void *)&d_x, &d_y};
-    MHDC_CUDA_TRY(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(SPMV_THREADS), args, 0, st));
-    return MHDC_OK;
-}
-
 int launch_variant(mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStream_t stream)
 {
-    if (id >= FIRST_GS_VARIANT) {
-        const int V = A->dtype == MHDC_F64 ? 2 : A->dtype == MHDC_F32 ? 4 : 8;
-        if (A->n_b % V == 0) {
-            const int shape = id - FIRST_GS_VARIANT;
-            switch (A->dtype) {
-            case MHDC_F64: return launch_gs<double>(A, shape, d_x, d_y, stream);
-            case MHDC_F32: return launch_gs<float>(A, shape, d_x, d_y, stream);
-            default: return launch_gs<__nv_bfloat16>(A, shape, d_x, d_y, stream);
-            }
-        }
-        id = -1;
-    }
     if (id >= FIRST_DW_VARIANT) {
         if (A->dw_ok && A->dtype == MHDC_F64 && (A->n_b % 2) == 0) {
             if (id < FIRST_TMA_DW_VARIANT) return launch_dw(A, id - FIRST_DW_VARIANT, d_x, d_y, stream);
