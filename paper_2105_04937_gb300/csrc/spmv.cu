@@ -578,50 +578,34 @@ k_mhdc_spmm(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles, int32_t c0, in
 }
 
 // Plain CSR (Fig. 2), one thread per row: s = fma(val[k], x[col_ind[k]], s)
-// over the row in column order.  One FP64 FMA per nonzero and no cross-lane
-// reduction: on GB300 the FP64 pipe (about 0.6 T FMA/s) rather than HBM
-// bounds an FP64 SpMV, so the baseline must not spend extra FP64 adds.  The
-// CTA's 256 rows are contiguous in val / col_ind: the CTA first copies them
-// to shared memory with coalesced loads (when they fit, CSR_STAGE entries),
-// then each thread walks its row there, four entries per step.
+// over the row, four entries per step.  One FP64 FMA per nonzero and no
+// cross-lane reduction: on GB300 the FP64 pipe (about 0.6 T FMA/s) rather
+// than HBM bounds an FP64 SpMV, so the baseline must not spend extra FP64
+// adds.  A warp's 32 rows are contiguous in val / col_ind, so the per-thread
+// strided loads are served from L1 lines the warp already fetched.
 constexpr int CSR_THREADS = 256;
-constexpr int CSR_STAGE = 3072;  // entries staged per CTA (36 KB)
 
 __global__ void __launch_bounds__(CSR_THREADS)
 k_csr_spmv(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
            const double *__restrict__ val, const double *__restrict__ x, double *__restrict__ y)
 {
-    __shared__ double sv[CSR_STAGE];
-    __shared__ int32_t sc[CSR_STAGE];
-    const int64_t r0 = (int64_t)blockIdx.x * CSR_THREADS;
-    const int64_t r1 = (r0 + CSR_THREADS < n) ? r0 + CSR_THREADS : n;
-    const int32_t e0 = rp[r0], e1 = rp[r1];
-    const bool staged = e1 - e0 <= CSR_STAGE;  // CTA-uniform
-    if (staged) {
-        for (int32_t e = e0 + threadIdx.x; e < e1; e += CSR_THREADS) {
-            sv[e - e0] = __ldg(val + e);
-            sc[e - e0] = __ldg(col + e);
-        }
-        __syncthreads();
-    }
-    const int64_t i = r0 + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * CSR_THREADS + threadIdx.x;
     if (i >= n) return;
-    // the row's entries at v[0 .. m), c[0 .. m): shared copy or global arrays
-    const int32_t a = rp[i], m = rp[i + 1] - a;
-    const double *v = staged ? sv + (a - e0) : val + a;
-    const int32_t *c = staged ? sc + (a - e0) : col + a;
+    const int32_t a = rp[i], b = rp[i + 1];
     double s = 0.0;
-    int32_t k = 0;
-    for (; k + 4 <= m; k += 4) {
-        const double v0 = v[k], v1 = v[k + 1], v2 = v[k + 2], v3 = v[k + 3];
-        const int32_t c0 = c[k], c1 = c[k + 1], c2 = c[k + 2], c3 = c[k + 3];
+    int32_t k = a;
+    for (; k + 4 <= b; k += 4) {
+        const double v0 = __ldg(val + k), v1 = __ldg(val + k + 1), v2 = __ldg(val + k + 2),
+                     v3 = __ldg(val + k + 3);
+        const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + 1), c2 = __ldg(col + k + 2),
+                      c3 = __ldg(col + k + 3);
         const double x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
         s = fma(v0, x0, s);
         s = fma(v1, x1, s);
         s = fma(v2, x2, s);
         s = fma(v3, x3, s);
     }
-    for (; k < m; k++) s = fma(v[k], __ldg(x + c[k]), s);
+    for (; k < b; k++) s = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
     y[i] = s;
 }
 
