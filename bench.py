@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--out", default=None, help="file for the sweep's JSON lines")
     ap.add_argument("--sizes", default="1e4,3e4,1e5,3e5,1e6,3e6,1e7,2e7,5e7",
                     help="matrix sizes n of the stencil sweep")
+    ap.add_argument("--nb-n", type=float, default=1e7,
+                    help="matrix size of the stencil sweep's block-width part")
     return ap.parse_args()
 
 
@@ -613,7 +615,7 @@ def sweep_stencil(args, mh, torch, log):
             del rp, col, val, x, ys, A
             torch.cuda.empty_cache()
     # block width sweep (Sec. 6.3, last experiment) at n = 1e7
-    n = 10_000_000
+    n = int(args.nb_n)
     for dim in (1, 2, 3):
         A = synth.paper_stencil(n, dim)
         rp = torch.from_numpy(A.row_ptr).cuda()
