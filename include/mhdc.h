@@ -158,6 +158,25 @@ int mhdc_spmv(mhdc_handle A, const void *d_x, void *d_y, void *stream);
 int mhdc_spmv_host(mhdc_handle A, const void *h_x, void *h_y, void *stream);
 
 /*
+ * mhdc_spmv_host_async -- mhdc_spmv_host without waiting, for a sequence of
+ * products on host data: the copy of h_x (pinned host memory, n values of
+ * the handle's x dtype) into one of two device slots, the product and the
+ * copy of y back to h_y (pinned, n values of the y dtype) are queued on the
+ * handle's own streams for copies in, products and copies out, chained by
+ * events, so that the copy-in of one call and the copy-out of the previous
+ * one overlap the product between them.  When the call returns, the call
+ * made two calls earlier has completed: its h_y holds the result and its
+ * h_x / h_y may be reused; h_x and h_y of the last two calls must stay
+ * untouched until a later call or mhdc_host_wait.  The caller's streams are
+ * not used; the product runs the handle's tile shape (mhdc_set_variant).
+ *
+ * mhdc_host_wait -- wait until every queued host call of the handle has
+ * completed (all h_y written).
+ */
+int mhdc_spmv_host_async(mhdc_handle A, const void *h_x, void *h_y);
+int mhdc_host_wait(mhdc_handle A);
+
+/*
  * mhdc_spmm -- Y = A X for k right-hand sides (the M-HDC kernel of Fig. 13
  * applied to k vectors at once, reading A once).
  *

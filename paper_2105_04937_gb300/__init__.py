@@ -21,7 +21,7 @@ from .build import SO, build as _build_library  # noqa: F401  (re-exported for b
 
 __all__ = [
     "MHDC_F64", "MHDC_F32", "MHDC_BF16", "MhdcError", "Matrix", "lib", "mhdc_build",
-    "hdc_build", "mhdc_build_dia", "mhdc_dia_spmv", "Sell", "sell_build", "sell_spmv",
+    "hdc_build", "mhdc_build_dia", "mhdc_dia_spmv", "mhdc_spmv_host_async", "mhdc_host_wait", "Sell", "sell_build", "sell_spmv",
     "sell_info", "sell_export", "sell_destroy", "mhdc_spmv", "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
     "mhdc_info", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
     "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "mhdc_check",
@@ -72,6 +72,8 @@ _SIGS = {
     "sell_destroy": [_P],
     "mhdc_spmv": [_P, _P, _P, _P],
     "mhdc_spmv_host": [_P, _P, _P, _P],
+    "mhdc_spmv_host_async": [_P, _P, _P],
+    "mhdc_host_wait": [_P],
     "mhdc_dia_spmv": [_P, _P, _P, _P],
     "mhdc_spmm": [_P, _I32, _P, _I64, _P, _I64, _P],
     "csr_spmv": [_I64, _P, _P, _P, _P, _P, _P],
@@ -331,6 +333,22 @@ def mhdc_spmv(A: Matrix, x, y, stream=None):
     _check_dev(y, yt, A.n, "y")
     _check(lib().mhdc_spmv(C.c_void_p(A.handle), _ptr(x), _ptr(y), _stream(stream)), "mhdc_spmv")
     return y
+
+
+def mhdc_spmv_host_async(A: Matrix, x, y):
+    """Queue y = A x on pinned host tensors (two calls in flight; see the C
+    header for when x and y may be reused).  mhdc_host_wait(A) drains."""
+    xt, yt = _xy_types(A)
+    for t, dt, nm in ((x, xt, "x"), (y, yt, "y")):
+        if t.is_cuda or t.dtype != dt or not t.is_contiguous() or t.numel() < A.n:
+            raise ValueError(f"{nm} must be a contiguous host tensor of {dt} with n elements")
+    _check(lib().mhdc_spmv_host_async(C.c_void_p(A.handle), _ptr(x), _ptr(y)),
+           "mhdc_spmv_host_async")
+    return y
+
+
+def mhdc_host_wait(A: Matrix):
+    _check(lib().mhdc_host_wait(C.c_void_p(A.handle)), "mhdc_host_wait")
 
 
 def mhdc_dia_spmv(A: Matrix, x, y, stream=None):

@@ -102,6 +102,57 @@ int mhdc_dia_spmv(mhdc_handle A, const void *d_x, void *d_y, void *stream)
     return launch_dia(A, d_x, d_y, (cudaStream_t)stream);
 }
 
+int mhdc_spmv_host_async(mhdc_handle A, const void *h_x, void *h_y)
+{
+    if (!A || (A->n > 0 && (!h_x || !h_y))) {
+        set_error_msg("mhdc_spmv_host_async: null argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    if (A->n == 0) return MHDC_OK;
+    const size_t bx = value_size(A->dtype) * (size_t)A->n, by = y_size(A->dtype) * (size_t)A->n;
+    if (!A->ae_done[1]) {  // first call (or one that failed to set up): make what is missing
+        const unsigned fl = cudaStreamNonBlocking;
+        if (!A->as_in) MHDC_CUDA_TRY(cudaStreamCreateWithFlags(&A->as_in, fl));
+        if (!A->as_comp) MHDC_CUDA_TRY(cudaStreamCreateWithFlags(&A->as_comp, fl));
+        if (!A->as_out) MHDC_CUDA_TRY(cudaStreamCreateWithFlags(&A->as_out, fl));
+        for (int k = 0; k < 2; k++) {
+            if (!A->ax[k]) MHDC_CUDA_TRY(cudaMalloc(&A->ax[k], bx));
+            if (!A->ay[k]) MHDC_CUDA_TRY(cudaMalloc(&A->ay[k], by));
+            if (!A->ae_in[k]) MHDC_CUDA_TRY(cudaEventCreateWithFlags(&A->ae_in[k], cudaEventDisableTiming));
+            if (!A->ae_comp[k])
+                MHDC_CUDA_TRY(cudaEventCreateWithFlags(&A->ae_comp[k], cudaEventDisableTiming));
+            if (!A->ae_done[k])
+                MHDC_CUDA_TRY(cudaEventCreateWithFlags(&A->ae_done[k], cudaEventDisableTiming));
+        }
+    }
+    const int s = (int)(A->a_calls & 1);
+    // the call two back used this slot: its copy-out must be complete
+    if (A->a_used[s]) MHDC_CUDA_TRY(cudaEventSynchronize(A->ae_done[s]));
+    MHDC_CUDA_TRY(cudaMemcpyAsync(A->ax[s], h_x, bx, cudaMemcpyHostToDevice, A->as_in));
+    MHDC_CUDA_TRY(cudaEventRecord(A->ae_in[s], A->as_in));
+    MHDC_CUDA_TRY(cudaStreamWaitEvent(A->as_comp, A->ae_in[s], 0));
+    int rc = launch_spmv(A, A->ax[s], A->ay[s], A->as_comp);
+    if (rc != MHDC_OK) return rc;
+    MHDC_CUDA_TRY(cudaEventRecord(A->ae_comp[s], A->as_comp));
+    MHDC_CUDA_TRY(cudaStreamWaitEvent(A->as_out, A->ae_comp[s], 0));
+    MHDC_CUDA_TRY(cudaMemcpyAsync(h_y, A->ay[s], by, cudaMemcpyDeviceToHost, A->as_out));
+    MHDC_CUDA_TRY(cudaEventRecord(A->ae_done[s], A->as_out));
+    A->a_used[s] = true;
+    A->a_calls++;
+    return MHDC_OK;
+}
+
+int mhdc_host_wait(mhdc_handle A)
+{
+    if (!A) {
+        set_error_msg("mhdc_host_wait: null handle");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < 2; k++)
+        if (A->a_used[k]) MHDC_CUDA_TRY(cudaEventSynchronize(A->ae_done[k]));
+    return MHDC_OK;
+}
+
 int mhdc_spmm(mhdc_handle A, int32_t k, const void *d_X, int64_t ldx, void *d_Y, int64_t ldy,
               void *stream)
 {

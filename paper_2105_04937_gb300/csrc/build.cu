@@ -976,6 +976,17 @@ void free_matrix(mhdc_matrix *A)
     cudaFree(A->csr_val);
     cudaFree(A->x_stage);
     cudaFree(A->y_stage);
+    for (int k = 0; k < 2; k++) {
+        if (A->ae_done[k]) cudaEventSynchronize(A->ae_done[k]);
+        cudaFree(A->ax[k]);
+        cudaFree(A->ay[k]);
+        if (A->ae_in[k]) cudaEventDestroy(A->ae_in[k]);
+        if (A->ae_comp[k]) cudaEventDestroy(A->ae_comp[k]);
+        if (A->ae_done[k]) cudaEventDestroy(A->ae_done[k]);
+    }
+    if (A->as_in) cudaStreamDestroy(A->as_in);
+    if (A->as_comp) cudaStreamDestroy(A->as_comp);
+    if (A->as_out) cudaStreamDestroy(A->as_out);
     cudaFree(A->status);
     cudaFree(A->dia_dw);
     cudaFree(A->csr_dw);

@@ -270,6 +270,35 @@ def test_repeatable_and_host_path(mh):
         assert t.equal(yh, y1.cpu())
 
 
+def test_host_async_pipeline(mh):
+    # eight products on host buffers through the pipelined entry point, with
+    # a ring of three buffer pairs (a pair is reused three calls later, after
+    # the call that made it complete has been reported by a later call)
+    t = torch()
+    A = synth.config_matrix("stencil27_128", scale=0.25)
+    for dt in DTYPES:
+        h = build(mh, A, 4096, 0.6, dt)
+        xs = [x_device(synth.uniform_vector(A.n, 40 + k), dt)[0] for k in range(8)]
+        ref = []
+        for xd in xs:
+            y = y_empty(A.n, dt)
+            mh.mhdc_spmv(h, xd, y)
+            ref.append(y.cpu())
+        ring_x = [t.empty_like(xs[0], device="cpu").pin_memory() for _ in range(3)]
+        ring_y = [t.empty(A.n, dtype=ref[0].dtype).pin_memory() for _ in range(3)]
+        got = [None] * 8
+        for k in range(8):
+            if k >= 3:
+                got[k - 3] = ring_y[k % 3].clone()   # finished: two calls were queued since
+            ring_x[k % 3].copy_(xs[k].cpu())
+            mh.mhdc_spmv_host_async(h, ring_x[k % 3], ring_y[k % 3])
+        mh.mhdc_host_wait(h)
+        for k in range(5, 8):
+            got[k] = ring_y[k % 3].clone()
+        for k in range(8):
+            assert t.equal(got[k], ref[k]), (dt, k)
+
+
 def test_stream_bench(mh):
     t = torch()
     N = 1 << 20
