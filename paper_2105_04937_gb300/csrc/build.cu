@@ -602,6 +602,7 @@ k_rem_fill(int64_t n, int32_t n_b, int32_t cpb, const int32_t *__restrict__ rp,
     for (int32_t eb = E0; eb < E1; eb += SC_THREADS) {
         const int32_t e = eb + (int32_t)threadIdx.x;
         const bool f = e < E1 && ((rem_flag[e >> 5] >> (e & 31)) & 1u);
+        if (!__syncthreads_or(f)) continue;  // no remainder entry in these 256 (CTA-uniform)
         const unsigned b = __ballot_sync(0xffffffffu, f);
         if (lane == 0) wsum[warp] = __popc(b);
         __syncthreads();
