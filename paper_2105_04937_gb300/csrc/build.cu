@@ -113,17 +113,6 @@ __device__ __forceinline__ bool table_insert(volatile int32_t *keys, int32_t *cn
 // pattern present the same offset d = j - i in the same step.  fn(has, i, k,
 // off) runs on every lane at every step (the loop is warp-uniform); has is
 // false for lanes past their row's end, which then carry off = EMPTY_KEY.
-// The lanes holding the same offset as this lane.  A whole warp on one
-// offset (rows of one stencil pattern) costs a shuffle and a vote; other
-// steps take a warp match.  The branch is warp-uniform.
-__device__ __forceinline__ unsigned same_offset_lanes(int32_t off)
-{
-    const int32_t o0 = __shfl_sync(0xffffffffu, off, 0);
-    const unsigned eq = __ballot_sync(0xffffffffu, off == o0);
-    if (eq == 0xffffffffu) return eq;
-    return __match_any_sync(0xffffffffu, off);
-}
-
 // SHARED: the columns come from a shared-memory copy holding entries
 // [base, ...) instead of global memory.
 template <bool SHARED = false, typename F>
@@ -233,7 +222,7 @@ k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
     for (int64_t g0 = r0 + 32 * warp; g0 < r0 + rows; g0 += 32 * CS_WARPS) {
         if (__any_sync(0xffffffffu, ovf != 0)) break;  // warp-uniform exit
         auto count = [&](bool has, int64_t, int32_t, int32_t off) {
-            const unsigned grp = same_offset_lanes(off);
+            const unsigned grp = __match_any_sync(0xffffffffu, off);
             if (has && lane == __ffs(grp) - 1 &&
                 !table_insert(keys, cnt, mask, off, __popc(grp), &used, limit))
                 ovf = 1;
@@ -321,7 +310,7 @@ k_count_hist(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t g0 = r0 + 32 * warp; g0 < r0 + rows; g0 += 32 * CS_WARPS) {
         rows_by_lane(g0, r0 + rows, rp, col, 0, [&](bool has, int64_t, int32_t, int32_t off) {
-            const unsigned grp = same_offset_lanes(off);
+            const unsigned grp = __match_any_sync(0xffffffffu, off);
             if (has && lane == __ffs(grp) - 1 &&
                 !table_insert(keys, cnt, mask, off, __popc(grp), &used, limit))
                 atomicAdd(&lost, (unsigned long long)__popc(grp));
@@ -362,7 +351,7 @@ k_count_all(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
     int32_t *stage = ca_smem + (threadIdx.x >> 5) * CW;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     auto count = [&](bool has, int64_t, int32_t, int32_t off) {
-        const unsigned grp = same_offset_lanes(off);
+        const unsigned grp = __match_any_sync(0xffffffffu, off);
         if (has && lane == __ffs(grp) - 1) atomicAdd(&cnt[(int64_t)off + n - 1], __popc(grp));
     };
     for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); 32 * g < n;
