@@ -108,16 +108,20 @@ __device__ __forceinline__ bool table_insert(volatile int32_t *keys, int32_t *cn
     return false;
 }
 
-// One lane per row: lanes walk 32 consecutive rows [g0, g0 + 32) (clipped at
-// `end`) together, entry k of every row at step k, so rows of the same
-// pattern present the same offset d = j - i in the same step.  fn(has, i, k,
-// off) runs on every lane at every step (the loop is warp-uniform); has is
-// false for lanes past their row's end, which then carry off = EMPTY_KEY.
+// Offset counting over 32 consecutive rows [g0, min(g0 + 32, end)), one lane
+// per row.  A first walk (entry k of every row at step k) compares each row's
+// offsets d = j - i with those of the row before it (the lane before): rows
+// with the same length and offsets form a run, and only the first row of a
+// run adds its offsets, each with the run's length as count.  Rows of one
+// stencil pattern thus cost one addition per offset per run instead of one
+// per entry; the counts are exact (no hashing).  The first walk is
+// warp-uniform; the second runs on the run-start lanes only.  add(off, c)
+// adds c to offset off's count and returns false when the table is full.
 // SHARED: the columns come from a shared-memory copy holding entries
 // [base, ...) instead of global memory.
 template <bool SHARED = false, typename F>
-__device__ __forceinline__ void rows_by_lane(int64_t g0, int64_t end, const int32_t *__restrict__ rp,
-                                             const int32_t *__restrict__ col, int32_t base, F fn)
+__device__ __forceinline__ void runs_by_lane(int64_t g0, int64_t end, const int32_t *__restrict__ rp,
+                                             const int32_t *__restrict__ col, int32_t base, F add)
 {
     const int lane = threadIdx.x & 31;
     const int64_t i = g0 + lane;
@@ -125,13 +129,25 @@ __device__ __forceinline__ void rows_by_lane(int64_t g0, int64_t end, const int3
     const int32_t a = live ? rp[i] : 0;
     const int32_t len = live ? rp[i + 1] - a : 0;
     const int32_t maxlen = __reduce_max_sync(0xffffffffu, len);
+    auto off_at = [&](int32_t k) -> int32_t {
+        if (k >= len) return EMPTY_KEY;
+        const int32_t c = SHARED ? col[a + k - base] : __ldg(col + a + k);
+        return c - (int32_t)i;
+    };
+    bool same = lane > 0 && __shfl_up_sync(0xffffffffu, len, 1) == len;
     for (int32_t k = 0; k < maxlen; k++) {
-        const bool has = k < len;
-        int32_t c = 0;
-        if (has) c = SHARED ? col[a + k - base] : __ldg(col + a + k);
-        const int32_t off = has ? c - (int32_t)i : EMPTY_KEY;
-        fn(has, i, a + k, off);
+        const int32_t off = off_at(k);
+        same = (__shfl_up_sync(0xffffffffu, off, 1) == off) && same;
     }
+    const unsigned live_mask = __ballot_sync(0xffffffffu, live);
+    const bool start = live && !same;
+    const unsigned starts = __ballot_sync(0xffffffffu, start);
+    if (!start) return;
+    const unsigned later = starts & ~((2u << lane) - 1u);  // run starts after this lane
+    const int32_t next = later ? __ffs(later) - 1 : __popc(live_mask);
+    const int32_t run = next - lane;
+    for (int32_t k = 0; k < len; k++)
+        if (!add(off_at(k), run)) return;
 }
 
 // Ascending bitonic sort of a[0..P2) (P2 a power of two) by the whole CTA.
@@ -221,21 +237,20 @@ k_count_select(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
     int32_t *stage = smem + 3 * cap_max + warp * cw;
     for (int64_t g0 = r0 + 32 * warp; g0 < r0 + rows; g0 += 32 * CS_WARPS) {
         if (__any_sync(0xffffffffu, ovf != 0)) break;  // warp-uniform exit
-        auto count = [&](bool has, int64_t, int32_t, int32_t off) {
-            const unsigned grp = __match_any_sync(0xffffffffu, off);
-            if (has && lane == __ffs(grp) - 1 &&
-                !table_insert(keys, cnt, mask, off, __popc(grp), &used, limit))
-                ovf = 1;
+        auto count = [&](int32_t off, int32_t c) {
+            if (table_insert(keys, cnt, mask, off, c, &used, limit)) return true;
+            ovf = 1;
+            return false;
         };
         const int64_t g1 = (g0 + 32 < r0 + rows) ? g0 + 32 : r0 + rows;
         const int32_t e0 = rp[g0], e1 = rp[g1];
         if (STAGE && e1 - e0 <= cw) {
             for (int32_t e = e0 + lane; e < e1; e += 32) stage[e - e0] = __ldg(col + e);
             __syncwarp();
-            rows_by_lane<true>(g0, g1, rp, stage, e0, count);
+            runs_by_lane<true>(g0, g1, rp, stage, e0, count);
             __syncwarp();
         } else {
-            rows_by_lane(g0, g1, rp, col, 0, count);
+            runs_by_lane(g0, g1, rp, col, 0, count);
         }
     }
     __syncthreads();
@@ -307,13 +322,12 @@ k_count_hist(int64_t n, int32_t n_b, const int32_t *__restrict__ rp,
         lost = 0;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
     for (int64_t g0 = r0 + 32 * warp; g0 < r0 + rows; g0 += 32 * CS_WARPS) {
-        rows_by_lane(g0, r0 + rows, rp, col, 0, [&](bool has, int64_t, int32_t, int32_t off) {
-            const unsigned grp = __match_any_sync(0xffffffffu, off);
-            if (has && lane == __ffs(grp) - 1 &&
-                !table_insert(keys, cnt, mask, off, __popc(grp), &used, limit))
-                atomicAdd(&lost, (unsigned long long)__popc(grp));
+        runs_by_lane(g0, r0 + rows, rp, col, 0, [&](int32_t off, int32_t c) {
+            if (!table_insert(keys, cnt, mask, off, c, &used, limit))
+                atomicAdd(&lost, (unsigned long long)c);
+            return true;  // keep going: the rest counts as single-entry diagonals
         });
     }
     __syncthreads();
@@ -350,9 +364,9 @@ k_count_all(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
     const int lane = threadIdx.x & 31;
     int32_t *stage = ca_smem + (threadIdx.x >> 5) * CW;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    auto count = [&](bool has, int64_t, int32_t, int32_t off) {
-        const unsigned grp = __match_any_sync(0xffffffffu, off);
-        if (has && lane == __ffs(grp) - 1) atomicAdd(&cnt[(int64_t)off + n - 1], __popc(grp));
+    auto count = [&](int32_t off, int32_t c) {
+        atomicAdd(&cnt[(int64_t)off + n - 1], c);
+        return true;
     };
     for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); 32 * g < n;
          g += nw) {
@@ -361,10 +375,10 @@ k_count_all(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
         if (e1 - e0 <= CW) {
             for (int32_t e = e0 + lane; e < e1; e += 32) stage[e - e0] = __ldg(col + e);
             __syncwarp();
-            rows_by_lane<true>(g0, g1, rp, stage, e0, count);
+            runs_by_lane<true>(g0, g1, rp, stage, e0, count);
             __syncwarp();
         } else {
-            rows_by_lane(g0, g1, rp, col, 0, count);
+            runs_by_lane(g0, g1, rp, col, 0, count);
         }
     }
 }
