@@ -134,10 +134,13 @@ __device__ __forceinline__ void runs_by_lane(int64_t g0, int64_t end, const int3
         const int32_t c = SHARED ? col[a + k - base] : __ldg(col + a + k);
         return c - (int32_t)i;
     };
-    bool same = lane > 0 && __shfl_up_sync(0xffffffffu, len, 1) == len;
+    // every lane takes part in each shuffle (no short-circuit around them)
+    const int32_t prev_len = __shfl_up_sync(0xffffffffu, len, 1);
+    bool same = lane > 0 && prev_len == len;
     for (int32_t k = 0; k < maxlen; k++) {
         const int32_t off = off_at(k);
-        same = (__shfl_up_sync(0xffffffffu, off, 1) == off) && same;
+        const int32_t prev_off = __shfl_up_sync(0xffffffffu, off, 1);
+        same = same && prev_off == off;
     }
     const unsigned live_mask = __ballot_sync(0xffffffffu, live);
     const bool start = live && !same;
