@@ -308,11 +308,26 @@ def _mean_launch_us(fn, steps, warmup, stream, torch):
     return mean * 1e3
 
 
+def precision_bound(dt: str, terms, abs_row):
+    """Per-row bound of an FP32 / BF16 product against the exact one:
+    [(1 + u_s)^2 (1 + gamma_{k+1}) - 1] sum_j |a_ij x_j| with u_s the storage
+    unit roundoff (values and x rounded once), FP32 accumulation (gamma_k =
+    k u / (1 - k u), u = 2^-24, Higham Sec. 3.1); FP64: the 1e-12 tolerance."""
+    if dt == "f64":
+        return 1e-12 * abs_row
+    u = 2.0 ** -24
+    us = u if dt == "f32" else (1 + u) * (1 + 2.0 ** -8) - 1
+    k = terms + 1
+    g = k * u / (1 - k * u)
+    return ((1 + us) ** 2 * (1 + g) - 1) * abs_row
+
+
 def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
     """Measurements of the other rows of the hot path beside the headline:
     reduced precision (scattered 4M-row matrix), SpMM (the 128^3 matrix,
-    FP32, k right-hand sides) and the batched product (64 stencils)."""
-    import oracle
+    FP32, k right-hand sides) and the batched product (64 stencils).  The
+    reduced-precision errors are taken against this library's FP64 product
+    and sum |a||x| from its CSR kernel on |A| and |x| (all on the GPU)."""
     import synth
     out = {}
     steps = max(10, min(args.steps, 400))
@@ -322,18 +337,25 @@ def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
     scol = torch.from_numpy(S.col).cuda()
     sval = torch.from_numpy(S.val).cuda()
     x64 = synth.loguniform_vector(S.n, 2)
-    y_ex = oracle.csr_spmv(S, x64)
-    abs_ex = oracle.csr_absrow(S, x64)
+    x_csr = torch.from_numpy(x64).cuda()
+    y_csr = torch.empty(S.n, dtype=torch.float64, device="cuda")
+    abs_d = torch.empty(S.n, dtype=torch.float64, device="cuda")
+    mh.csr_spmv(S.n, srp, scol, sval, x_csr, y_csr, stream)
+    mh.csr_spmv(S.n, srp, scol, sval.abs(), x_csr.abs(), abs_d, stream)
+    torch.cuda.synchronize()
+    y_ex = y_csr.cpu().numpy()
+    abs_ex = abs_d.cpu().numpy()
+    terms = np.diff(S.row_ptr).astype(np.float64) + 19
     prec = {"workload": "scattered_4m: 4,194,304 rows, 19 offsets in [-20000, 20000] in 60% of "
                         "2048-row blocks, Poisson(3) random entries per row, |values| "
                         "log-uniform in [1e-3, 1e3]; n_b=2048, theta=0.6",
-            "nnz": S.nnz}
+            "nnz": S.nnz, "error_reference": "FP64 CSR product of the unrounded data (GPU)"}
     for dt in ("f64", "f32", "bf16"):
         Hs = mh.mhdc_build(S.n, srp, scol, sval, 2048, 0.6, dt)
         inf = Hs.info
-        xs = oracle.store(x64, dt)
-        xd = (torch.from_numpy(xs.view(np.int16)).cuda().view(torch.bfloat16) if dt == "bf16"
-              else torch.from_numpy(xs).cuda())
+        # x rounded to the storage type (nearest-even: FP64 -> FP32 -> BF16)
+        xd = (x_csr if dt == "f64" else x_csr.float() if dt == "f32"
+              else x_csr.float().to(torch.bfloat16))
         yd = torch.empty(S.n, dtype=torch.float64 if dt == "f64" else torch.float32, device="cuda")
         best, times = mh.mhdc_tune(Hs, xd, yd)
         if dt == "f64":  # FP64 arithmetic (the emulated variants are reported with the headline)
@@ -343,17 +365,14 @@ def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
         mh.mhdc_spmv(Hs, xd, yd, stream)
         torch.cuda.synchronize()
         err = np.abs(yd.double().cpu().numpy() - y_ex)
-        terms = np.diff(S.row_ptr).astype(np.float64) + 19
-        bnd = oracle.bound_vs_exact(abs_ex, terms, dt)
+        bnd = precision_bound(dt, terms, abs_ex)
         prec[dt] = {"kernel_us": round(us, 2), "gflops": round(gflops(S.nnz, us / 1e6), 1),
                     "gbs": round(inf["bytes_model"] / us / 1e3, 1), "bytes": inf["bytes_model"],
                     "variant": best, "P": inf["P"], "beta": round(inf["beta"], 4),
                     "max_rel_err": float(np.max(err / np.maximum(abs_ex, 1e-300))),
                     "max_err_over_bound": float(np.max(err / np.maximum(bnd, 1e-300)))}
         Hs.destroy()
-        del xd, yd
-    x_csr = torch.from_numpy(x64).cuda()
-    y_csr = torch.empty(S.n, dtype=torch.float64, device="cuda")
+        del yd
     us = _mean_launch_us(lambda: mh.csr_spmv(S.n, srp, scol, sval, x_csr, y_csr, stream),
                          steps, 5, stream, torch)
     prec["csr_fp64"] = {"kernel_us": round(us, 2), "gflops": round(gflops(S.nnz, us / 1e6), 1)}

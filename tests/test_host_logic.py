@@ -58,3 +58,15 @@ def test_bench_parses_sweep_options(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     a = bench.parse()
     assert a.sweep is None and a.gpus == 1 and a.warmup >= 3 and a.impl == "ours"
+
+
+def test_bench_precision_bound_equals_the_oracles():
+    import bench
+    import oracle
+    rng = np.random.default_rng(3)
+    terms = rng.integers(1, 80, 1000).astype(np.float64)
+    absr = rng.uniform(0, 10, 1000)
+    for dt in ("f32", "bf16"):
+        assert np.allclose(bench.precision_bound(dt, terms, absr),
+                           oracle.bound_vs_exact(absr, terms, dt), rtol=1e-12, atol=0)
+    assert np.array_equal(bench.precision_bound("f64", terms, absr), 1e-12 * absr)
