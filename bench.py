@@ -986,12 +986,12 @@ def main():
     e2e_sync = {"value": round(gflops(A.nnz, e2e_ms / 1e3) * ws, 3), "unit": "GFLOP/s",
                 "ms_per_step": round(e2e_ms, 4), "steps": e2e_steps,
                 "api": "mhdc_spmv_host (one call at a time: copy in, product, copy out, wait)"}
-    # pipelined: a ring of three pinned input/output pairs, each step copies its
+    # pipelined: a ring of four pinned input/output pairs, each step copies its
     # own x in and its y out; the copy-in of step k+1 and the copy-out of step
     # k-1 overlap step k's product (wall clock, drained at the end)
-    ring_x = [torch.from_numpy(synth.uniform_vector(A.n, 60 + k)).pin_memory() for k in range(3)]
-    ring_y = [torch.empty(A.n, dtype=torch.float64).pin_memory() for _ in range(3)]
-    for k in range(3):
+    ring_x = [torch.from_numpy(synth.uniform_vector(A.n, 60 + k)).pin_memory() for k in range(4)]
+    ring_y = [torch.empty(A.n, dtype=torch.float64).pin_memory() for _ in range(4)]
+    for k in range(4):
         mh.mhdc_spmv_host_async(H, ring_x[k], ring_y[k])
     mh.mhdc_host_wait(H)
     torch.cuda.synchronize()
@@ -999,7 +999,7 @@ def main():
         dist.barrier()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        mh.mhdc_spmv_host_async(H, ring_x[k % 3], ring_y[k % 3])
+        mh.mhdc_spmv_host_async(H, ring_x[k % 4], ring_y[k % 4])
     mh.mhdc_host_wait(H)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     if dist:

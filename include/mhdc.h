@@ -160,13 +160,13 @@ int mhdc_spmv_host(mhdc_handle A, const void *h_x, void *h_y, void *stream);
 /*
  * mhdc_spmv_host_async -- mhdc_spmv_host without waiting, for a sequence of
  * products on host data: the copy of h_x (pinned host memory, n values of
- * the handle's x dtype) into one of two device slots, the product and the
- * copy of y back to h_y (pinned, n values of the y dtype) are queued on the
- * handle's own streams for copies in, products and copies out, chained by
- * events, so that the copy-in of one call and the copy-out of the previous
+ * the handle's x dtype) into one of three device slots, the product and
+ * the copy of y back to h_y (pinned, n values of the y dtype) are queued on
+ * the handle's own streams for copies in, products and copies out, chained
+ * by events, so that the copy-in of one call and the copy-out of an earlier
  * one overlap the product between them.  When the call returns, the call
- * made two calls earlier has completed: its h_y holds the result and its
- * h_x / h_y may be reused; h_x and h_y of the last two calls must stay
+ * made three calls earlier has completed: its h_y holds the result and its
+ * h_x / h_y may be reused; h_x and h_y of the last three calls must stay
  * untouched until a later call or mhdc_host_wait.  The caller's streams are
  * not used; the product runs the handle's tile shape (mhdc_set_variant).
  *

@@ -336,7 +336,7 @@ def mhdc_spmv(A: Matrix, x, y, stream=None):
 
 
 def mhdc_spmv_host_async(A: Matrix, x, y):
-    """Queue y = A x on pinned host tensors (two calls in flight; see the C
+    """Queue y = A x on pinned host tensors (three calls in flight; see the C
     header for when x and y may be reused).  mhdc_host_wait(A) drains."""
     xt, yt = _xy_types(A)
     for t, dt, nm in ((x, xt, "x"), (y, yt, "y")):

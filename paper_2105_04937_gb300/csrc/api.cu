@@ -110,12 +110,13 @@ int mhdc_spmv_host_async(mhdc_handle A, const void *h_x, void *h_y)
     }
     if (A->n == 0) return MHDC_OK;
     const size_t bx = value_size(A->dtype) * (size_t)A->n, by = y_size(A->dtype) * (size_t)A->n;
-    if (!A->ae_done[1]) {  // first call (or one that failed to set up): make what is missing
+    constexpr int NS = mhdc_matrix::ASYNC_SLOTS;
+    if (!A->ae_done[NS - 1]) {  // first call (or one that failed to set up): make what is missing
         const unsigned fl = cudaStreamNonBlocking;
         if (!A->as_in) MHDC_CUDA_TRY(cudaStreamCreateWithFlags(&A->as_in, fl));
         if (!A->as_comp) MHDC_CUDA_TRY(cudaStreamCreateWithFlags(&A->as_comp, fl));
         if (!A->as_out) MHDC_CUDA_TRY(cudaStreamCreateWithFlags(&A->as_out, fl));
-        for (int k = 0; k < 2; k++) {
+        for (int k = 0; k < NS; k++) {
             if (!A->ax[k]) MHDC_CUDA_TRY(cudaMalloc(&A->ax[k], bx));
             if (!A->ay[k]) MHDC_CUDA_TRY(cudaMalloc(&A->ay[k], by));
             if (!A->ae_in[k]) MHDC_CUDA_TRY(cudaEventCreateWithFlags(&A->ae_in[k], cudaEventDisableTiming));
@@ -125,8 +126,8 @@ int mhdc_spmv_host_async(mhdc_handle A, const void *h_x, void *h_y)
                 MHDC_CUDA_TRY(cudaEventCreateWithFlags(&A->ae_done[k], cudaEventDisableTiming));
         }
     }
-    const int s = (int)(A->a_calls & 1);
-    // the call two back used this slot: its copy-out must be complete
+    const int s = (int)(A->a_calls % NS);
+    // the call NS back used this slot: its copy-out must be complete
     if (A->a_used[s]) MHDC_CUDA_TRY(cudaEventSynchronize(A->ae_done[s]));
     MHDC_CUDA_TRY(cudaMemcpyAsync(A->ax[s], h_x, bx, cudaMemcpyHostToDevice, A->as_in));
     MHDC_CUDA_TRY(cudaEventRecord(A->ae_in[s], A->as_in));
@@ -148,7 +149,7 @@ int mhdc_host_wait(mhdc_handle A)
         set_error_msg("mhdc_host_wait: null handle");
         return MHDC_ERR_INVALID_ARG;
     }
-    for (int k = 0; k < 2; k++)
+    for (int k = 0; k < mhdc_matrix::ASYNC_SLOTS; k++)
         if (A->a_used[k]) MHDC_CUDA_TRY(cudaEventSynchronize(A->ae_done[k]));
     return MHDC_OK;
 }

@@ -994,7 +994,7 @@ void free_matrix(mhdc_matrix *A)
     cudaFree(A->csr_val);
     cudaFree(A->x_stage);
     cudaFree(A->y_stage);
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < mhdc_matrix::ASYNC_SLOTS; k++) {
         if (A->ae_done[k]) cudaEventSynchronize(A->ae_done[k]);
         cudaFree(A->ax[k]);
         cudaFree(A->ay[k]);

@@ -21,13 +21,13 @@ struct mhdc_matrix {
     void *csr_val = nullptr;         // [nnz_rem] of dtype
     void *x_stage = nullptr;         // host-call staging buffers (lazy)
     void *y_stage = nullptr;
-    // pipelined host calls (mhdc_spmv_host_async, lazy): two staging slots,
-    // streams for copies in, products and copies out, and per-slot events
-    void *ax[2] = {nullptr, nullptr}, *ay[2] = {nullptr, nullptr};
+    // pipelined host calls (mhdc_spmv_host_async, lazy): ASYNC_SLOTS staging
+    // slots, streams for copies in, products and copies out, per-slot events
+    static constexpr int ASYNC_SLOTS = 3;
+    void *ax[ASYNC_SLOTS] = {}, *ay[ASYNC_SLOTS] = {};
     cudaStream_t as_in = nullptr, as_comp = nullptr, as_out = nullptr;
-    cudaEvent_t ae_in[2] = {nullptr, nullptr}, ae_comp[2] = {nullptr, nullptr};
-    cudaEvent_t ae_done[2] = {nullptr, nullptr};
-    bool a_used[2] = {false, false};
+    cudaEvent_t ae_in[ASYNC_SLOTS] = {}, ae_comp[ASYNC_SLOTS] = {}, ae_done[ASYNC_SLOTS] = {};
+    bool a_used[ASYNC_SLOTS] = {};
     int64_t a_calls = 0;
     int64_t rem_block_rows = 0;      // rows of blocks whose remainder is nonempty
     int64_t bytes_model = 0;

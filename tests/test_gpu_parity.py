@@ -271,31 +271,32 @@ def test_repeatable_and_host_path(mh):
 
 
 def test_host_async_pipeline(mh):
-    # eight products on host buffers through the pipelined entry point, with
-    # a ring of three buffer pairs (a pair is reused three calls later, after
-    # the call that made it complete has been reported by a later call)
+    # ten products on host buffers through the pipelined entry point, with a
+    # ring of four buffer pairs (a pair is reused four calls later, after the
+    # call that used it has been reported complete by a later call)
     t = torch()
     A = synth.config_matrix("stencil27_128", scale=0.25)
     for dt in DTYPES:
         h = build(mh, A, 4096, 0.6, dt)
-        xs = [x_device(synth.uniform_vector(A.n, 40 + k), dt)[0] for k in range(8)]
+        K, R = 10, 4
+        xs = [x_device(synth.uniform_vector(A.n, 40 + k), dt)[0] for k in range(K)]
         ref = []
         for xd in xs:
             y = y_empty(A.n, dt)
             mh.mhdc_spmv(h, xd, y)
             ref.append(y.cpu())
-        ring_x = [t.empty_like(xs[0], device="cpu").pin_memory() for _ in range(3)]
-        ring_y = [t.empty(A.n, dtype=ref[0].dtype).pin_memory() for _ in range(3)]
-        got = [None] * 8
-        for k in range(8):
-            if k >= 3:
-                got[k - 3] = ring_y[k % 3].clone()   # finished: two calls were queued since
-            ring_x[k % 3].copy_(xs[k].cpu())
-            mh.mhdc_spmv_host_async(h, ring_x[k % 3], ring_y[k % 3])
+        ring_x = [t.empty_like(xs[0], device="cpu").pin_memory() for _ in range(R)]
+        ring_y = [t.empty(A.n, dtype=ref[0].dtype).pin_memory() for _ in range(R)]
+        got = [None] * K
+        for k in range(K):
+            if k >= R:
+                got[k - R] = ring_y[k % R].clone()   # finished: three calls were queued since
+            ring_x[k % R].copy_(xs[k].cpu())
+            mh.mhdc_spmv_host_async(h, ring_x[k % R], ring_y[k % R])
         mh.mhdc_host_wait(h)
-        for k in range(5, 8):
-            got[k] = ring_y[k % 3].clone()
-        for k in range(8):
+        for k in range(K - R, K):
+            got[k] = ring_y[k % R].clone()
+        for k in range(K):
             assert t.equal(got[k], ref[k]), (dt, k)
 
 
