@@ -172,6 +172,8 @@ int mhdc_spmv_host(mhdc_handle A, const void *h_x, void *h_y, void *stream);
  *
  * mhdc_host_wait -- wait until every queued host call of the handle has
  * completed (all h_y written).
+ * Neither call is thread-safe for one handle (calls on different handles are
+ * independent).
  */
 int mhdc_spmv_host_async(mhdc_handle A, const void *h_x, void *h_y);
 int mhdc_host_wait(mhdc_handle A);

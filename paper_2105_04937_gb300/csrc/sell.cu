@@ -76,19 +76,27 @@ __global__ void k_sell_identity(int64_t n, int32_t *perm)
     if (i < n) perm[i] = (int32_t)i;
 }
 
-// rowlen at sorted positions and chunk widths x C (slots per chunk)
+// rowlen at sorted positions and chunk widths x C (slots per chunk); the
+// 64-bit total of all chunks goes to *total (one atomic per warp) so that the
+// host can reject layouts past the int32 slot index before the scan is used
 __global__ void k_sell_chunks(int64_t n, int32_t C, int64_t chunks, const int32_t *__restrict__ perm,
-                              const int32_t *__restrict__ len, int32_t *rowlen, int32_t *slots)
+                              const int32_t *__restrict__ len, int32_t *rowlen, int32_t *slots,
+                              unsigned long long *total)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= chunks) return;
-    int32_t w = 0;
-    for (int64_t r = c * C; r < (c + 1) * C && r < n; r++) {
-        const int32_t l = len[perm[r]];
-        rowlen[r] = l;
-        w = l > w ? l : w;
+    unsigned long long mine = 0;
+    if (c < chunks) {
+        int32_t w = 0;
+        for (int64_t r = c * C; r < (c + 1) * C && r < n; r++) {
+            const int32_t l = len[perm[r]];
+            rowlen[r] = l;
+            w = l > w ? l : w;
+        }
+        mine = (unsigned long long)w * (unsigned long long)C;
+        slots[c] = mine > (unsigned long long)INT32_MAX ? 0 : (int32_t)mine;
     }
-    slots[c] = w * C;
+    for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, d);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(total, mine);
 }
 
 // one thread per (sorted row, entry): slot chunk_ptr[c] + k * C + r; the
@@ -210,19 +218,22 @@ int sell_fill(sell_matrix *S, const int32_t *rp, const int32_t *col, const doubl
     SRC(alloc((void **)&S->chunk_ptr, sizeof(int32_t) * (size_t)(S->chunks + 1)));
     SRC(tmp_alloc(&t.p[1], sizeof(int32_t) * (size_t)S->chunks, st));
     SRC(tmp_alloc(&t.p[2], sizeof(int32_t) * (size_t)scan_scratch_elems(S->chunks), st));
+    SRC(tmp_alloc(&t.p[3], sizeof(unsigned long long), st));
     int32_t *slots = static_cast<int32_t *>(t.p[1]);
-    k_sell_chunks<<<(unsigned)((S->chunks + 255) / 256), 256, 0, st>>>(n, S->C, S->chunks, S->perm,
-                                                                        len, S->rowlen, slots);
+    unsigned long long *total64 = static_cast<unsigned long long *>(t.p[3]);
+    MHDC_CUDA_TRY(cudaMemsetAsync(total64, 0, sizeof(unsigned long long), st));
+    k_sell_chunks<<<(unsigned)((S->chunks + 255) / 256), 256, 0, st>>>(
+        n, S->C, S->chunks, S->perm, len, S->rowlen, slots, total64);
     MHDC_LAUNCH_CHECK("k_sell_chunks");
-    SRC(exclusive_scan_i32(slots, S->chunk_ptr, S->chunks, static_cast<int32_t *>(t.p[2]), st));
-    int32_t total = 0;
-    MHDC_CUDA_TRY(cudaMemcpyAsync(&total, S->chunk_ptr + S->chunks, sizeof(int32_t),
-                                  cudaMemcpyDeviceToHost, st));
+    unsigned long long h_total = 0;
+    MHDC_CUDA_TRY(cudaMemcpyAsync(&h_total, total64, sizeof h_total, cudaMemcpyDeviceToHost, st));
     MHDC_CUDA_TRY(cudaStreamSynchronize(st));
-    if (total < 0) {
+    if (h_total > (unsigned long long)INT32_MAX) {
         set_error_msg("sell_build: more than 2^31 - 1 padded slots");
         return MHDC_ERR_UNSUPPORTED;
     }
+    SRC(exclusive_scan_i32(slots, S->chunk_ptr, S->chunks, static_cast<int32_t *>(t.p[2]), st));
+    const int32_t total = (int32_t)h_total;
     S->slots = total;
     SRC(alloc((void **)&S->col, sizeof(int32_t) * (size_t)total));
     SRC(alloc((void **)&S->val, sizeof(double) * (size_t)total));
