@@ -193,3 +193,12 @@ def test_dia_input_rejects_bad_offsets(mh):
     y = y_empty(n, "f64")
     mh.mhdc_spmv(h, t.ones(n, dtype=t.float64, device="cuda"), y)
     assert t.all(y == 0)
+
+
+def test_dia_input_block_wider_than_matrix_and_single_row(mh):
+    for n, offs in ((1, [0]), (7, [-6, -1, 0, 6]), (300, [-299, -150, 0, 1, 299])):
+        off, val = synth.dia_matrix(n, offs, seed=n, zero_rate=0.2)
+        x = synth.uniform_vector(n, 3)
+        for n_b in (1, n, 4 * n + 3):
+            for dt in ("f64", "bf16"):
+                _dia_case(mh, n, off, val, n_b, 0.5, dt, x)

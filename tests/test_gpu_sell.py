@@ -115,3 +115,13 @@ def test_sell_bad_arguments(mh):
         with pytest.raises(mh.MhdcError) as e:
             mh.sell_build(A.n, rp, col, val, C, sigma)
         assert e.value.code == mh.MHDC_ERR_INVALID_ARG
+
+
+def test_sell_fewer_rows_than_a_chunk(mh):
+    # n < C: one partial chunk; n = 1
+    for n in (1, 5, 31):
+        d = np.zeros((n, n))
+        d[np.arange(n), np.arange(n)] = 2.0
+        d[0, n - 1] = -1.0 if n > 1 else 2.0
+        A = synth.from_dense(d)
+        check_sell(mh, A, 32, 64, synth.uniform_vector(n, n))
