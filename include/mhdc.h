@@ -21,7 +21,10 @@
  *     the ABI.  mhdc_strerror() names a code.
  *   - Value dtype is fixed per handle: F64 handles take FP64 x and write FP64
  *     y; F32 handles take FP32 x and write FP32 y; BF16 handles take BF16 x
- *     and write FP32 y.  Accumulation is FP64 for F64 and FP32 otherwise.
+ *     and write FP32 y.  Accumulation is FP64 for F64 and FP32 otherwise,
+ *     except that a CSR remainder row with more than 64 entries is summed in
+ *     FP64 and rounded once into the FP32 accumulator (every product kernel:
+ *     mhdc_spmv, mhdc_dia_spmv, mhdc_spmm, the batch calls).
  */
 #ifndef MHDC_H
 #define MHDC_H

@@ -305,31 +305,62 @@ FP64_ROW_TOL = 1e-12          # |y_i - y*_i| <= 1e-12 * sum_j |a_ij||x_j|
 U_STORE = {"f64": 0.0, "f32": 2.0 ** -24, "bf16": (1 + 2.0 ** -24) * (1 + 2.0 ** -8) - 1}
 U_ACC = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "bf16": 2.0 ** -24}
 
+# FP32 / BF16 products sum a CSR remainder row (Fig. 13, first loop) with more
+# than REM_LONG entries in FP64 and round that sum once into the FP32
+# accumulator, where it counts as one term; FP64 handles are unaffected.
+REM_LONG = 64
+
 
 def gamma(k, u):
     k = np.asarray(k, dtype=np.float64)
     return k * u / (1.0 - k * u)
 
 
-def bound_vs_exact(absrow, terms, dtype: str) -> np.ndarray:
+def long_remainder(M: dict) -> np.ndarray:
+    """Per row of the converted matrix M: its remainder length L where a
+    reduced-precision product sums the remainder in FP64 (L > REM_LONG),
+    else 0; all zero for FP64 handles."""
+    L = np.diff(np.asarray(M["csr_row_ptr"], dtype=np.int64))
+    if M["dtype"] == "f64":
+        return np.zeros_like(L)
+    return np.where(L > REM_LONG, L, 0)
+
+
+def _acc_factor(terms, dtype: str, long_rem):
+    """(1 + gamma_{k+1}(u_acc)) (1 + gamma_L(2^-53)) - 1 for a row summed as
+    k terms in the accumulator (Higham, Accuracy and Stability of Numerical
+    Algorithms, Sec. 3.1: k FMAs into a sum starting at zero, plus one
+    rounding kept as a margin).  A row with a long remainder (long_rem = L > 0)
+    has k = terms - L + 1: its diagonal terms and the remainder's FP64 sum
+    (error gamma_L(2^-53), products exact in FP64) rounded once."""
+    terms = np.asarray(terms, dtype=np.float64)
+    if long_rem is None:
+        return gamma(terms + 1, U_ACC[dtype])
+    lr = np.asarray(long_rem, dtype=np.float64)
+    k = np.where(lr > 0, terms - lr + 1, terms)
+    g = gamma(k + 1, U_ACC[dtype])
+    return np.where(lr > 0, (1 + g) * (1 + gamma(lr, 2.0 ** -53)) - 1, g)
+
+
+def bound_vs_exact(absrow, terms, dtype: str, long_rem=None) -> np.ndarray:
     """Per-row bound on |y_computed - y_exact| where y_exact uses the
     unrounded FP64 matrix and x: storage rounding of a and x (unit roundoff
-    u_s each) and accumulation of terms + 1 roundings in the accumulator
-    (Higham, Accuracy and Stability of Numerical Algorithms, Sec. 3.1):
-    [(1 + u_s)^2 (1 + gamma_{k+1}) - 1] * sum_j |a_ij x_j|."""
+    u_s each) and the accumulation bound f of _acc_factor:
+    [(1 + u_s)^2 (1 + f) - 1] * sum_j |a_ij x_j|.  long_rem: per-row output
+    of long_remainder (None: every row summed in the accumulator)."""
     if dtype == "f64":
         return FP64_ROW_TOL * np.asarray(absrow)
     us = U_STORE[dtype]
-    g = gamma(np.asarray(terms) + 1, U_ACC[dtype])
-    return ((1 + us) ** 2 * (1 + g) - 1) * np.asarray(absrow)
+    f = _acc_factor(terms, dtype, long_rem)
+    return ((1 + us) ** 2 * (1 + f) - 1) * np.asarray(absrow)
 
 
-def bound_vs_stored(absrow_stored, terms, dtype: str) -> np.ndarray:
+def bound_vs_stored(absrow_stored, terms, dtype: str, long_rem=None) -> np.ndarray:
     """Per-row bound on |y_computed - y_stored| where y_stored is the FP64
-    product of the stored (rounded) values: gamma_{k+1} * sum |a^ x^|."""
+    product of the stored (rounded) values: f * sum |a^ x^| (f of _acc_factor)."""
     if dtype == "f64":
         return FP64_ROW_TOL * np.asarray(absrow_stored)
-    return gamma(np.asarray(terms) + 1, U_ACC[dtype]) * np.asarray(absrow_stored)
+    return _acc_factor(terms, dtype, long_rem) * np.asarray(absrow_stored)
 
 
 # --------------------------------------------------------------------------

@@ -143,6 +143,38 @@ int ensure_dw(mhdc_matrix *A, cudaStream_t st);
 int tune_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream, int32_t *best,
               float *times_us);
 
+// ---- CSR remainder rows (Fig. 13, first loop) of every product kernel
+//
+// FP32 / BF16 handles accumulate in FP32, except a remainder row with more
+// than REM_LONG entries: it is summed in FP64 (each product of two stored
+// FP32 / BF16 values is exact in FP64) and rounded once to FP32, so its error
+// no longer grows with the row's length at FP32's unit roundoff.  The row
+// then enters the FP32 accumulator as one term.  FP64 handles are unchanged.
+constexpr int REM_LONG = 64;
+
+__device__ __forceinline__ double rem_in(double v) { return v; }
+__device__ __forceinline__ float rem_in(float v) { return v; }
+__device__ __forceinline__ float rem_in(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Adds the remainder entries [a, b) of one row to acc (zero on entry in
+// every kernel), in column order.
+template <typename Acc, typename VT, typename X>
+__device__ __forceinline__ void rem_row_add(Acc &acc, int32_t a, int32_t b,
+                                            const int32_t *__restrict__ col,
+                                            const VT *__restrict__ val, const X *__restrict__ x)
+{
+    if constexpr (sizeof(Acc) < sizeof(double)) {
+        if (b - a > REM_LONG) {
+            double s = 0.0;
+            for (int32_t k = a; k < b; k++)
+                s = fma((double)rem_in(val[k]), (double)rem_in(__ldg(x + col[k])), s);
+            acc += (Acc)s;  // rounded to nearest even once; exact while acc is zero
+            return;
+        }
+    }
+    for (int32_t k = a; k < b; k++) acc += rem_in(val[k]) * rem_in(__ldg(x + col[k]));
+}
+
 // Exclusive prefix sum of m int32 values into out[0..m] (out[m] = total);
 // scratch must hold scan_scratch_elems(m) int32.  Defined in scan.cu.
 int64_t scan_scratch_elems(int64_t m);

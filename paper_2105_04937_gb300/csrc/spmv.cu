@@ -156,9 +156,8 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
                     const int32_t t = tl[u] + m;
                     if (t < rows) {
                         const int64_t i = r0 + t;
-                        const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
-                        for (int32_t k = a; k < b; k++)
-                            acc[u][m] += widen(csr_val[k]) * widen(ldg_elem(x + csr_col[k]));
+                        rem_row_add(acc[u][m], csr_row_ptr[i], csr_row_ptr[i + 1], csr_col,
+                                    csr_val, x);
                     }
                 }
         } else if (q0 != q1) {
@@ -168,9 +167,7 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
                 Acc sum = Acc(0);
                 if (tw + rr < rows) {
                     const int64_t i = r0 + tw + rr;
-                    const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
-                    for (int32_t k = a; k < b; k++)
-                        sum += widen(csr_val[k]) * widen(ldg_elem(x + csr_col[k]));
+                    rem_row_add(sum, csr_row_ptr[i], csr_row_ptr[i + 1], csr_col, csr_val, x);
                 }
                 rs[rr] = sum;
             }
@@ -547,7 +544,21 @@ k_mhdc_spmm(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles, int32_t c0, in
                 if (t < rows) {
                     const int64_t i = r0 + t;
                     const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
-                    for (int32_t q = a; q < b; q++) add_row(u, widen(csr_val[q]), csr_col[q]);
+                    if (sizeof(Acc) < sizeof(double) && b - a > REM_LONG) {
+                        // a long row: each column summed in FP64 and rounded
+                        // once, as rem_row_add does for one right-hand side
+#pragma unroll
+                        for (int c = 0; c < KC; c++)
+                            if (c < kc) {
+                                double s = 0.0;
+                                for (int32_t q = a; q < b; q++)
+                                    s = fma((double)widen(csr_val[q]),
+                                            (double)widen(__ldg(Xm + csr_col[q] * ldx + c0 + c)), s);
+                                acc[u][c] = (Acc)s;
+                            }
+                    } else {
+                        for (int32_t q = a; q < b; q++) add_row(u, widen(csr_val[q]), csr_col[q]);
+                    }
                 }
             }
         }
@@ -627,9 +638,8 @@ k_dia_rem(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__
     using Acc = typename Tr<VT>::Acc;
     const int64_t i = (int64_t)blockIdx.x * DIA_THREADS + threadIdx.x;
     if (i >= n) return;
-    const int32_t a = rp[i], b = rp[i + 1];
     Acc s = Acc(0);
-    for (int32_t k = a; k < b; k++) s += widen(val[k]) * widen(ldg_elem(x + col[k]));
+    rem_row_add(s, rp[i], rp[i + 1], col, val, x);
     y[i] = s;
 }
 

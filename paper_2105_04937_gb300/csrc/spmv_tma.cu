@@ -248,9 +248,8 @@ k_mhdc_spmv_tma(int64_t n, int32_t n_b, int32_t upb, int64_t n_units,
                     const int32_t t = tl[k] + m;
                     if (t < ru) {
                         const int64_t i = r0 + t0 + t;
-                        const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
-                        for (int32_t q = a; q < b; q++)
-                            acc[k][m] += wide(csr_val[q]) * wide(__ldg(x + csr_col[q]));
+                        rem_row_add(acc[k][m], csr_row_ptr[i], csr_row_ptr[i + 1], csr_col,
+                                    csr_val, x);
                     }
                 }
         }

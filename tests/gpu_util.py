@@ -79,13 +79,14 @@ def check_spmv(mh, h, M, A, x64, dtype):
     assert np.all(np.isfinite(yg))
     y_st = oracle.mhdc_spmv(M, xs)
     abs_st, terms = oracle.mhdc_absrow(M, xs)
+    lr = oracle.long_remainder(M)
     err = np.abs(yg - y_st)
-    bnd = oracle.bound_vs_stored(abs_st, terms, dtype)
+    bnd = oracle.bound_vs_stored(abs_st, terms, dtype, lr)
     bad = np.nonzero(err > bnd)[0]
     assert bad.size == 0, ("vs stored", dtype, bad[:5], err[bad[:5]], bnd[bad[:5]])
     y_ex = oracle.csr_spmv(A, x64)
     abs_ex = oracle.csr_absrow(A, x64)
-    bnd = oracle.bound_vs_exact(abs_ex, terms, dtype)
+    bnd = oracle.bound_vs_exact(abs_ex, terms, dtype, lr)
     err = np.abs(yg - y_ex)
     bad = np.nonzero(err > bnd)[0]
     assert bad.size == 0, ("vs exact", dtype, bad[:5], err[bad[:5]], bnd[bad[:5]])
@@ -117,11 +118,13 @@ def check_spmm(mh, h, M, A, X64, dtype, pad=0):
     Y = Yfull.double().cpu().numpy()
     if pad:
         assert np.all(np.isnan(Y[:, k:])), "mhdc_spmm wrote outside the k columns"
+    lr = oracle.long_remainder(M)
     for c in range(k):
         yg = Y[:, c]
         y_st = oracle.mhdc_spmv(M, Xw[:, c])
         abs_st, terms = oracle.mhdc_absrow(M, Xw[:, c])
-        assert np.all(np.abs(yg - y_st) <= oracle.bound_vs_stored(abs_st, terms, dtype)), (dtype, k, c)
+        assert np.all(np.abs(yg - y_st) <= oracle.bound_vs_stored(abs_st, terms, dtype, lr)), \
+            (dtype, k, c)
         x64 = np.ascontiguousarray(X64[:, c])
-        bnd = oracle.bound_vs_exact(oracle.csr_absrow(A, x64), terms, dtype)
+        bnd = oracle.bound_vs_exact(oracle.csr_absrow(A, x64), terms, dtype, lr)
         assert np.all(np.abs(yg - oracle.csr_spmv(A, x64)) <= bnd), (dtype, k, c)

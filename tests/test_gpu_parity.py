@@ -541,7 +541,8 @@ def test_batch_matches_oracle_and_graph_replays(mh, dt):
             xs_w = oracle.widen(oracle.store(x, dt), dt)
             ref = oracle.mhdc_spmv(M, xs_w)
             a, terms = oracle.mhdc_absrow(M, xs_w)
-            assert np.all(np.abs(y.double().cpu().numpy() - ref) <= oracle.bound_vs_stored(a, terms, dt))
+            bnd = oracle.bound_vs_stored(a, terms, dt, oracle.long_remainder(M))
+            assert np.all(np.abs(y.double().cpu().numpy() - ref) <= bnd)
     direct = [y.clone() for y in ys]
     for rep in range(3):
         for y in ys:
