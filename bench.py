@@ -322,6 +322,16 @@ def precision_bound(dt: str, terms, abs_row):
     return ((1 + us) ** 2 * (1 + g) - 1) * abs_row
 
 
+def tuner_families(mh, times, dt):
+    """Fastest tuner time (us) of each family of product variants: register
+    tiles (0-5), values by TMA (6-9), values and x windows by TMA (16-19)
+    and, for FP64 handles, emulated FP64 (10-15)."""
+    fam = {"register": range(0, 6), "tma_values": range(6, 10), "tma_values_x": mh.XW_VARIANTS}
+    if dt == "f64":
+        fam["emulated_fp64"] = mh.EMULATED_VARIANTS
+    return {k: round(min(times[v] for v in vs), 2) for k, vs in fam.items()}
+
+
 def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
     """Measurements of the other rows of the hot path beside the headline:
     reduced precision (scattered 4M-row matrix), SpMM (the 128^3 matrix,
@@ -368,7 +378,8 @@ def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
         bnd = precision_bound(dt, terms, abs_ex)
         prec[dt] = {"kernel_us": round(us, 2), "gflops": round(gflops(S.nnz, us / 1e6), 1),
                     "gbs": round(inf["bytes_model"] / us / 1e3, 1), "bytes": inf["bytes_model"],
-                    "variant": best, "P": inf["P"], "beta": round(inf["beta"], 4),
+                    "variant": best, "tuner_best_us": tuner_families(mh, times, dt),
+                    "P": inf["P"], "beta": round(inf["beta"], 4),
                     "max_rel_err": float(np.max(err / np.maximum(abs_ex, 1e-300))),
                     "max_err_over_bound": float(np.max(err / np.maximum(bnd, 1e-300)))}
         Hs.destroy()
@@ -832,7 +843,8 @@ def main():
     kernel_name = ("k_mhdc_spmv<double>" if best_variant < 6 else
                    "k_mhdc_spmv_tma<double>" if best_variant < mh.FIRST_EMULATED_VARIANT else
                    "k_split_x + k_mhdc_spmv_dw" if best_variant < 13 else
-                   "k_split_x + k_mhdc_spmv_tma_dw")
+                   "k_split_x + k_mhdc_spmv_tma_dw" if best_variant < 16 else
+                   "k_mhdc_spmv_xw<double>")
 
     peak, peak_src = measured_peak()
     vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
@@ -1044,6 +1056,8 @@ def main():
             "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "n_b": N_B, "theta": THETA,
                        "P": info["P"], "nnz_rem": info["nnz_rem"],
                        "variant": best_variant, "variant_us": [round(t, 2) for t in variant_us],
+                       "tuner_best_us": (tuner_families(mh, variant_us, "f64") if len(variant_us)
+                                         else None),
                        "alpha": round(info["alpha"], 4), "beta": round(info["beta"], 5),
                        "l2": "inputs larger than L2 (M-HDC arrays "
                              f"{info['bytes_model'] / 1e6:.0f} MB > 129 MB L2); no flush",

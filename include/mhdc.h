@@ -237,7 +237,7 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  * stream dia_val through shared memory with TMA bulk copies (one producer
  * warp, several consumer warps, an mbarrier ring; they need n_b * value size
  * to be a multiple of 16 bytes, else they run variant -1).  Variants 0-9
- * compute the same sums in the same order per row (bit-identical y).
+ * and 16-19 compute the same sums in the same order per row (bit-identical y).
  * Variants 10-15 (FP64 handles only; others run variant -1) emulate the FP64
  * product (10-12 in registers, 13-15 streamed by TMA like 6-9) with pairs of
  * FP32 numbers (values and x split into hi + lo, about
@@ -249,6 +249,11 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  * terms; the handle checks its values at build and each product checks x on
  * the device, and outside that window the product runs the native FP64 path
  * (variant -1's arithmetic) instead.
+ * Variants 16-19 stage both operands in shared memory with TMA bulk copies:
+ * the values as in 6-9 and, per run of nearby diagonals of a block, one
+ * window of x that every diagonal of the run reads (the 27 diagonals of a
+ * 27-point stencil share 3 windows).  They need what 6-9 need and a 16-byte
+ * aligned x (else they run variant -1), and give the same y as 0-9.
  *
  * mhdc_set_variant -- use variant v for this handle (-1: default chosen from n_b).
  *                     The first v in 10-15 on an FP64 handle makes its FP32-pair
@@ -259,7 +264,7 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out);
  *                     times_us is not NULL, each variant's mean time in
  *                     microseconds to times_us[MHDC_NUM_VARIANTS].  Synchronous.
  */
-#define MHDC_NUM_VARIANTS 16
+#define MHDC_NUM_VARIANTS 20
 int mhdc_set_variant(mhdc_handle A, int32_t v);
 int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *best,
               float *times_us);

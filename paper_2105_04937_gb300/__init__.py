@@ -110,13 +110,14 @@ _SIGS = {
     "mhdc_tune": [_P, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
 }
 
-MHDC_NUM_VARIANTS = 16
+MHDC_NUM_VARIANTS = 20
 MHDC_NUM_FEATURES = 64
 MHDC_NUM_CANDIDATES = 45
 MHDC_SELECT_PAPER, MHDC_SELECT_MLP, MHDC_SELECT_AUTOTUNE, MHDC_SELECT_MODEL = 0, 1, 2, 4
 FIRST_EMULATED_VARIANT = 10
 EMULATED_VARIANTS = tuple(range(10, 16))  # FP64 handles: FP32-pair arithmetic
-NATIVE_VARIANTS = tuple(range(0, 10))     # the handle's own arithmetic
+NATIVE_VARIANTS = tuple(range(0, 10)) + tuple(range(16, 20))  # the handle's own arithmetic
+XW_VARIANTS = tuple(range(16, 20))        # values and x staged in shared memory by TMA
 
 
 def lib(build_if_missing: bool = False):

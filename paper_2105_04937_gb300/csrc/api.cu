@@ -235,7 +235,7 @@ int mhdc_set_variant(mhdc_handle A, int32_t v)
         set_error_msg("mhdc_set_variant: invalid argument");
         return MHDC_ERR_INVALID_ARG;
     }
-    if (v >= FIRST_DW_VARIANT) {  // the emulated arrays are made on first use
+    if (v >= FIRST_DW_VARIANT && v < FIRST_XW_VARIANT) {  // emulated arrays: made on first use
         int rc = ensure_dw(A, nullptr);
         if (rc != MHDC_OK) return rc;
         MHDC_CUDA_TRY(cudaStreamSynchronize(nullptr));

@@ -129,6 +129,11 @@ int launch_spmv_tma(const mhdc_matrix *A, int shape, const void *d_x, void *d_y,
 constexpr int NUM_REG_VARIANTS = 6;
 constexpr int FIRST_DW_VARIANT = 10;
 constexpr int FIRST_TMA_DW_VARIANT = 13;
+constexpr int FIRST_XW_VARIANT = 16;
+// variants 16-19: values and x staged in shared memory by TMA (x 16-byte aligned)
+bool xw_supported(const mhdc_matrix *A, const void *d_x);
+int launch_spmv_xw(const mhdc_matrix *A, int shape, const void *d_x, void *d_y,
+                   cudaStream_t stream);
 int launch_spmv_tma_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y,
                        unsigned long long epoch, cudaStream_t stream);
 int launch_split_x(mhdc_matrix *A, const void *d_x, unsigned long long epoch, cudaStream_t stream);
@@ -142,6 +147,25 @@ int prepare_dw(mhdc_matrix *A, cudaStream_t st);
 int ensure_dw(mhdc_matrix *A, cudaStream_t st);
 int tune_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream, int32_t *best,
               float *times_us);
+
+// The 16 bytes starting `sh` bytes (sh < 16, a multiple of the element size)
+// into the 32-byte window (lo, hi): two aligned loads replace V element loads
+// when x[j .. j+V) is not 16-byte aligned.  `sh` is warp-uniform.
+__device__ __forceinline__ uint4 window16(const uint4 &lo, const uint4 &hi, int sh)
+{
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    const int bs = (sh & 3) * 8;
+    uint32_t o[5];
+    switch (sh >> 2) {
+    case 0: o[0] = w[0]; o[1] = w[1]; o[2] = w[2]; o[3] = w[3]; o[4] = w[4]; break;
+    case 1: o[0] = w[1]; o[1] = w[2]; o[2] = w[3]; o[3] = w[4]; o[4] = w[5]; break;
+    case 2: o[0] = w[2]; o[1] = w[3]; o[2] = w[4]; o[3] = w[5]; o[4] = w[6]; break;
+    default: o[0] = w[3]; o[1] = w[4]; o[2] = w[5]; o[3] = w[6]; o[4] = w[7]; break;
+    }
+    if (bs == 0) return make_uint4(o[0], o[1], o[2], o[3]);
+    return make_uint4(__funnelshift_r(o[0], o[1], bs), __funnelshift_r(o[1], o[2], bs),
+                      __funnelshift_r(o[2], o[3], bs), __funnelshift_r(o[3], o[4], bs));
+}
 
 // ---- CSR remainder rows (Fig. 13, first loop) of every product kernel
 //

@@ -82,25 +82,6 @@ __device__ __forceinline__ void load_x(const X *__restrict__ x, int64_t j, bool 
     for (int m = 0; m < V; m++) xv[m] = ldg_elem(x + j + m);
 }
 
-// The 16 bytes starting `sh` bytes (sh < 16, a multiple of the element size)
-// into the 32-byte window (lo, hi): two aligned loads replace V element loads
-// when x[j .. j+V) is not 16-byte aligned.  `sh` is warp-uniform.
-__device__ __forceinline__ uint4 window16(const uint4 &lo, const uint4 &hi, int sh)
-{
-    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-    const int bs = (sh & 3) * 8;
-    uint32_t o[5];
-    switch (sh >> 2) {
-    case 0: o[0] = w[0]; o[1] = w[1]; o[2] = w[2]; o[3] = w[3]; o[4] = w[4]; break;
-    case 1: o[0] = w[1]; o[1] = w[2]; o[2] = w[3]; o[3] = w[4]; o[4] = w[5]; break;
-    case 2: o[0] = w[2]; o[1] = w[3]; o[2] = w[4]; o[3] = w[5]; o[4] = w[6]; break;
-    default: o[0] = w[3]; o[1] = w[4]; o[2] = w[5]; o[3] = w[6]; o[4] = w[7]; break;
-    }
-    if (bs == 0) return make_uint4(o[0], o[1], o[2], o[3]);
-    return make_uint4(__funnelshift_r(o[0], o[1], bs), __funnelshift_r(o[1], o[2], bs),
-                      __funnelshift_r(o[2], o[3], bs), __funnelshift_r(o[3], o[4], bs));
-}
-
 // One warp = one tile of RW = 32 * V * U consecutive rows of one row block.
 // The block's diagonals are taken D at a time: the D * U 16-byte value loads
 // of a group are issued first, then the x loads, then the FMAs, so a warp
@@ -853,7 +834,10 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
 
 int launch_variant(mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStream_t stream)
 {
-    if (id >= FIRST_DW_VARIANT) {
+    if (id >= FIRST_XW_VARIANT) {
+        if (xw_supported(A, d_x)) return launch_spmv_xw(A, id - FIRST_XW_VARIANT, d_x, d_y, stream);
+        id = -1;
+    } else if (id >= FIRST_DW_VARIANT) {
         if (A->dw_ok && A->dtype == MHDC_F64 && (A->n_b % 2) == 0) {
             if (id < FIRST_TMA_DW_VARIANT) return launch_dw(A, id - FIRST_DW_VARIANT, d_x, d_y, stream);
             const unsigned long long epoch = ++A->dw_epoch;

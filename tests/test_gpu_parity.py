@@ -253,6 +253,39 @@ def test_misaligned_x_gives_identical_result(mh):
         mh.mhdc_check(h)
 
 
+def test_staged_x_variants_edge_cases(mh):
+    # variants 16-19 (values and x windows in shared memory): bit-identical to
+    # the register kernel on small and ragged shapes -- n not a multiple of
+    # the 16-byte vector, n_b below and above the unit size, windows reaching
+    # outside [0, n), diagonals far apart (one window each), global selection
+    t = torch()
+    cases = []
+    for seed in range(4):
+        rng = synth.Rng(seed, 41)
+        n = int(rng.integers(1, 1, 3000)[0])
+        A = synth.random_sparse(n, 0.01, seed=200 + seed, diag_bias=0.7)
+        cases += [(A, n_b, th, mode) for n_b in (8, 64, 1024, 3 * n + 8)
+                  for th, mode in ((0.0, "block"), (0.02, "block"), (0.5, "global"))]
+    cases += [(synth.paper_stencil(50001, d), n_b, 0.0, "block") for d in (1, 3) for n_b in (16, 4096)]
+    cases.append((synth.config_matrix("stencil27_128", 0.25), 4096, 0.6, "block"))
+    cases.append((synth.config_matrix("scattered_4m", 1 / 128), 2048, 0.6, "block"))
+    for A, n_b, th, mode in cases:
+        for dt in DTYPES:
+            h, M = check_build(mh, A, n_b, th, dt, mode)
+            xd, _ = x_device(synth.loguniform_vector(A.n, 3), dt)
+            mh.mhdc_set_variant(h, 1)
+            y0 = y_empty(A.n, dt)
+            mh.mhdc_spmv(h, xd, y0)
+            for v in mh.XW_VARIANTS:
+                mh.mhdc_set_variant(h, v)
+                y = y_empty(A.n, dt)
+                mh.mhdc_spmv(h, xd, y)
+                t.cuda.synchronize()
+                mh.mhdc_check(h)
+                assert t.equal(y, y0), (A.n, n_b, th, mode, dt, v)
+            check_spmv(mh, h, M, A, synth.uniform_vector(A.n, 4), dt)
+
+
 def test_repeatable_and_host_path(mh):
     A = synth.config_matrix("stencil27_128", scale=0.25)
     t = torch()
