@@ -8,8 +8,8 @@
 // 16 bytes of dia_val per diagonal (coalesced, 512 B per warp, no L1
 // allocation since every value is read once) and the matching x values
 // (L1/L2-cached: consecutive diagonals of a block hit the same x window), and
-// accumulates in registers; y is written once.  A persistent grid of
-// (SMs x resident CTAs) walks the tiles.
+// accumulates in registers; y is written once.  One warp per tile, a grid
+// of 8-warp CTAs covering every tile.
 #include <cstring>
 #include <type_traits>
 
