@@ -153,17 +153,33 @@ def fp64_peak_tflops():
     return 2 * 2 * sms * mhz * 1e6 / 1e12
 
 
-def profiled_traffic(variant):
-    """DRAM bytes per launch from the committed ncu summary of the tuned
-    kernel, if that summary covers this variant and spmv.cu is unchanged
-    since the capture; else None."""
+# the sources of the product kernels: a capture counts only while all of them
+# are unchanged
+KERNEL_SOURCES = ("spmv.cu", "spmv_tma.cu", "mhdc_internal.cuh", "dw_arith.cuh")
+
+
+def kernel_source_sha(root=None) -> str | None:
+    """sha1[:16] of the product kernels' sources, concatenated in order."""
     import hashlib
+    h = hashlib.sha1()
     try:
-        md = open(os.path.join(ROOT, "profiles", "mhdc_spmv_f64_stencil27_128.md")).read()
-        src = open(os.path.join(ROOT, "paper_2105_04937_gb300", "csrc", "spmv.cu"), "rb").read()
+        for name in KERNEL_SOURCES:
+            with open(os.path.join(root or ROOT, "paper_2105_04937_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
     except OSError:
         return None
-    sha = hashlib.sha1(src).hexdigest()[:16]
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(variant):
+    """DRAM bytes per launch from the committed ncu summary of the tuned
+    kernel, if that summary covers this variant and the kernel sources are
+    unchanged since the capture; else None."""
+    try:
+        md = open(os.path.join(ROOT, "profiles", "mhdc_spmv_f64_stencil27_128.md")).read()
+    except OSError:
+        return None
+    sha = kernel_source_sha()
     for line in md.splitlines():
         # "traffic: <variant> <bytes> <source sha1 prefix>"
         parts = line.split()

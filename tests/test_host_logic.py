@@ -38,15 +38,20 @@ def test_profiled_traffic_matches_source_hash(tmp_path, monkeypatch):
     root = tmp_path
     (root / "profiles").mkdir()
     (root / "paper_2105_04937_gb300" / "csrc").mkdir(parents=True)
-    src = b"// kernel source\n"
-    (root / "paper_2105_04937_gb300" / "csrc" / "spmv.cu").write_bytes(src)
-    sha = hashlib.sha1(src).hexdigest()[:16]
+    h = hashlib.sha1()
+    for name in bench.KERNEL_SOURCES:
+        src = f"// {name}\n".encode()
+        (root / "paper_2105_04937_gb300" / "csrc" / name).write_bytes(src)
+        h.update(src)
+    sha = h.hexdigest()[:16]
     (root / "profiles" / "mhdc_spmv_f64_stencil27_128.md").write_text(
         f"text\ntraffic: 1 350833152 {sha}\ntraffic: 5 350264832 0000000000000000\n")
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.profiled_traffic(1) == 350833152
     assert bench.profiled_traffic(5) is None      # captured for another source
     assert bench.profiled_traffic(3) is None      # not captured
+    (root / "paper_2105_04937_gb300" / "csrc" / "spmv_tma.cu").write_bytes(b"// changed\n")
+    assert bench.profiled_traffic(1) is None      # a kernel source changed since
 
 
 def test_bench_parses_sweep_options(monkeypatch):
