@@ -203,26 +203,22 @@ def gflops(nnz, sec):
 
 
 def time_launches(fn, steps, warmup, stream, torch):
-    """K back-to-back launches: total time over the region and the mean of
-    per-launch event durations (both on the launching stream)."""
+    """K back-to-back launches bracketed by two events on the launching
+    stream: (total ms, mean ms per launch = total / K).  No events between
+    the launches: a timed event between two kernels waits for the first to
+    drain before the second starts, which added 2-7 us per launch here."""
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
     t0.record(stream)
-    for a, b in ev:
-        a.record(stream)
+    for _ in range(steps):
         fn()
-        b.record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
     total_ms = t0.elapsed_time(t1)
-    per = [a.elapsed_time(b) for a, b in ev]
-    return total_ms, float(np.mean(per)), float(np.median(per))
+    return total_ms, total_ms / steps
 
 
 def cpu_baseline(A, budget_s, log):
@@ -320,7 +316,7 @@ def run_reference(args):
 
 
 def _mean_launch_us(fn, steps, warmup, stream, torch):
-    tot, mean, _ = time_launches(fn, steps, warmup, stream, torch)
+    tot, mean = time_launches(fn, steps, warmup, stream, torch)
     return mean * 1e3
 
 
@@ -408,6 +404,45 @@ def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
     out["a7_reduced_precision"] = prec
     log(f"reduced precision: {json.dumps(prec)[:300]}")
     del srp, scol, sval
+    # -- reduced precision on the headline matrix (n_b = 4096, theta = 0.6):
+    # FP32 / BF16 storage makes the product HBM-bound; its bandwidth against
+    # the measured copy peak, and the error against this library's FP64
+    # product of the unrounded data
+    peak, peak_src = measured_peak()
+    xh = synth.uniform_vector(A.n, 12)
+    xh_d = torch.from_numpy(xh).cuda()
+    yh = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    absh = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    mh.csr_spmv(A.n, rp, col, val, xh_d, yh, stream)
+    mh.csr_spmv(A.n, rp, col, val.abs(), xh_d.abs(), absh, stream)
+    torch.cuda.synchronize()
+    yh_ex, absh_ex = yh.cpu().numpy(), absh.cpu().numpy()
+    terms_h = np.diff(A.row_ptr).astype(np.float64)
+    hp = {"workload": "stencil27_128 (the headline matrix), n_b=4096, theta=0.6",
+          "peak_gbs": peak, "peak_source": peak_src,
+          "error_reference": "FP64 CSR product of the unrounded data (GPU)"}
+    for dt in ("f32", "bf16"):
+        Hh = mh.mhdc_build(A.n, rp, col, val, 4096, 0.6, dt)
+        inf = Hh.info
+        xd = xh_d.float() if dt == "f32" else xh_d.float().to(torch.bfloat16)
+        yd = torch.empty(A.n, dtype=torch.float32, device="cuda")
+        _, times = mh.mhdc_tune(Hh, xd, yd)
+        best = min(mh.NATIVE_VARIANTS, key=lambda v: times[v])
+        mh.mhdc_set_variant(Hh, best)
+        us = _mean_launch_us(lambda: mh.mhdc_spmv(Hh, xd, yd, stream), steps, 5, stream, torch)
+        mh.mhdc_spmv(Hh, xd, yd, stream)
+        torch.cuda.synchronize()
+        err = np.abs(yd.double().cpu().numpy() - yh_ex)
+        bnd = precision_bound(dt, terms_h, absh_ex)
+        gbs = inf["bytes_model"] / us / 1e3
+        hp[dt] = {"kernel_us": round(us, 2), "gflops": round(gflops(A.nnz, us / 1e6), 1),
+                  "gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4), "bytes": inf["bytes_model"],
+                  "variant": best, "tuner_best_us": tuner_families(mh, times, dt),
+                  "max_err_over_bound": float(np.max(err / np.maximum(bnd, 1e-300)))}
+        Hh.destroy()
+        del yd
+    out["a7_headline_matrix"] = hp
+    log(f"reduced precision, headline matrix: {json.dumps(hp)[:300]}")
     # -- SpMM on the headline matrix in FP32
     H32 = mh.mhdc_build(A.n, rp, col, val, 4096, 0.6, "f32")
     mm = {"workload": "stencil27_128, FP32 values and X, Y row-major n x k"}
@@ -446,7 +481,7 @@ def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
     for nm_, fn in (("separate_launches", separate),
                     ("persistent_launch", lambda: mh.mhdc_batch_spmv(B, XP, YP, stream)),
                     ("graph_replay", lambda: mh.mhdc_batch_spmv_graph(B, XP, YP, stream))):
-        tot, mean, _ = time_launches(fn, 30, 3, stream, torch)
+        tot, mean = time_launches(fn, 30, 3, stream, torch)
         bt[nm_] = {"us": round(mean * 1e3, 1), "gflops": round(gflops(nnz_b, mean / 1e3), 1)}
     B.destroy()
     for h in hs:
@@ -882,14 +917,10 @@ def main():
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
     sampler.mark("t0")
     ev0.record(stream)
-    for a, b in evs:
-        a.record(stream)
+    for _ in range(args.steps):
         step()
-        b.record(stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     sampler.mark("t1")
@@ -897,7 +928,11 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     total_ms = ev0.elapsed_time(ev1)
-    kern_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    # the region holds the K launches of the product kernel and nothing else
+    # (one per step, back to back, no events between them: a timed event
+    # between two kernels drains the device and added 2-4 us per step), so
+    # the kernel's average launch duration is the region's time over K
+    kern_ms = total_ms / args.steps
     if dist:
         total_ms = max_over_ranks(total_ms, dist, torch.device("cuda", local))
     clocks = sampler.stop() if rank == 0 else None
@@ -917,7 +952,7 @@ def main():
         # plain FP64 CSR on the same matrix and GPU (Fig. 2)
         def csr_step():
             mh.csr_spmv(A.n, rp, col, val, x, y, stream)
-        tot, mean, _ = time_launches(csr_step, min(args.steps, 5000), args.warmup, stream, torch)
+        tot, mean = time_launches(csr_step, min(args.steps, 5000), args.warmup, stream, torch)
         csr_bytes = 12 * A.nnz + 4 * (A.n + 1) + 16 * A.n
         extra["csr_fp64"] = {"gflops": round(gflops(A.nnz, mean / 1e3), 2),
                              "gbs": round(csr_bytes / (mean / 1e3) / 1e9, 1),
@@ -928,7 +963,7 @@ def main():
         for sigma in (1, 256):
             Ss = mh.sell_build(A.n, rp, col, val, 32, sigma)
             si = Ss.info
-            tot, mean_s, _ = time_launches(lambda: mh.sell_spmv(Ss, x, y, stream),
+            tot, mean_s = time_launches(lambda: mh.sell_spmv(Ss, x, y, stream),
                                            min(args.steps, 5000), args.warmup, stream, torch)
             sell_bytes = 12 * si["slots"] + 8 * A.n * 3 + 4 * (si["chunks"] + 1)
             extra[f"sell_c32_s{sigma}_fp64"] = {
@@ -943,7 +978,7 @@ def main():
 
         def hdc_step():
             mh.mhdc_spmv(Hh, x, y, stream)
-        tot, mean, _ = time_launches(hdc_step, min(args.steps, 5000), args.warmup, stream, torch)
+        tot, mean = time_launches(hdc_step, min(args.steps, 5000), args.warmup, stream, torch)
         extra["hdc_fp64"] = {"gflops": round(gflops(A.nnz, mean / 1e3), 2),
                              "gbs": round(ih["bytes_model"] / (mean / 1e3) / 1e9, 1),
                              "kernel_us": round(mean * 1e3, 2), "bytes": ih["bytes_model"],
@@ -957,7 +992,7 @@ def main():
 
             def cusp_step():
                 torch.mv(Acsr, x)
-            tot, mean, _ = time_launches(cusp_step, min(args.steps, 1000), args.warmup, stream, torch)
+            tot, mean = time_launches(cusp_step, min(args.steps, 1000), args.warmup, stream, torch)
             extra["csr_cusparse_ref"] = {"gflops": round(gflops(A.nnz, mean / 1e3), 2),
                                          "gbs": round(csr_bytes / (mean / 1e3) / 1e9, 1),
                                          "step_us": round(mean * 1e3, 2),
@@ -974,12 +1009,12 @@ def main():
         Im = torch.arange(Nm, dtype=torch.int32, device="cuda")
         wm = {}
         for nm_, ind, per in (("direct", False, 32), ("indirect", True, 36)):
-            tot, mean, _ = time_launches(lambda: mh.mhdc_stream_bench(Am, Bm, Im, Cm, ind, stream),
+            tot, mean = time_launches(lambda: mh.mhdc_stream_bench(Am, Bm, Im, Cm, ind, stream),
                                          20, 3, stream, torch)
             wm[nm_] = round(per * Nm / (mean / 1e3) / 1e9, 1)
         ro = torch.empty(mh.mhdc_read_bench_ctas(), dtype=torch.int64, device="cuda")
         big = torch.cat([Am, Bm])
-        tot, mean, _ = time_launches(lambda: mh.mhdc_read_bench(big, ro, stream), 20, 3, stream, torch)
+        tot, mean = time_launches(lambda: mh.mhdc_read_bench(big, ro, stream), 20, 3, stream, torch)
         wm["read_only"] = round(8 * big.numel() / (mean / 1e3) / 1e9, 1)
         extra["w_mem_gbs"] = wm
         del Am, Bm, Cm, Im, big
@@ -989,7 +1024,7 @@ def main():
         for fp64, nm_, iters in ((True, "fp64_tflops", 512), (False, "fp32_tflops", 8192)):
             ob = torch.empty(ctas * 256, dtype=torch.float64 if fp64 else torch.float32,
                              device="cuda")
-            tot, mean, _ = time_launches(lambda: mh.mhdc_fma_bench(fp64, iters, ob, stream),
+            tot, mean = time_launches(lambda: mh.mhdc_fma_bench(fp64, iters, ob, stream),
                                          5, 2, stream, torch)
             fr[nm_] = round(2.0 * ctas * 256 * 8 * iters / (mean / 1e3) / 1e12, 4)
         extra["fma_measured"] = fr
