@@ -231,6 +231,16 @@ int mhdc_export(mhdc_handle A, int32_t *h_dia_ptr, int32_t *h_dia_offset, void *
 int mhdc_info(mhdc_handle A, mhdc_info_t *out);
 
 /*
+ * mhdc_stats -- the statistics of the performance model (Sec. 5.3): alpha,
+ * the filling rate of the stored diagonals (entries / (P * n_b)); beta, the
+ * share of the nonzeros left in the CSR remainder; P, the stored partial
+ * diagonals; bytes, the model's main-memory bytes of one product
+ * (mhdc_info_t.bytes_model).  Any output pointer may be NULL.  Host call,
+ * no device work; MHDC_ERR_INVALID_ARG for a NULL handle.
+ */
+int mhdc_stats(mhdc_handle A, double *alpha, double *beta, int64_t *P, int64_t *bytes);
+
+/*
  * Tile shapes of the M-HDC product (no counterpart in the paper, whose kernel
  * is a CPU loop nest): variants 0-5 load dia_val into registers (a warp owns
  * 32 x 16 B x U rows and loads D diagonals before accumulating); variants 6-9

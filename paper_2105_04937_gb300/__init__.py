@@ -23,7 +23,7 @@ __all__ = [
     "MHDC_F64", "MHDC_F32", "MHDC_BF16", "MhdcError", "Matrix", "lib", "mhdc_build",
     "hdc_build", "mhdc_build_dia", "mhdc_dia_spmv", "mhdc_spmv_host_async", "mhdc_host_wait", "Sell", "sell_build", "sell_spmv",
     "sell_info", "sell_export", "sell_destroy", "mhdc_spmv", "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
-    "mhdc_info", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
+    "mhdc_info", "mhdc_stats", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
     "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "mhdc_check",
     "mhdc_read_bench", "mhdc_read_bench_ctas", "mhdc_build_noalloc",
     "mhdc_fma_bench", "Batch", "mhdc_batch_create", "mhdc_batch_spmv", "mhdc_batch_spmv_graph",
@@ -79,6 +79,8 @@ _SIGS = {
     "csr_spmv": [_I64, _P, _P, _P, _P, _P, _P],
     "mhdc_export": [_P, _P, _P, _P, _P, _P, _P],
     "mhdc_info": [_P, C.POINTER(_Info)],
+    "mhdc_stats": [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                   C.POINTER(C.c_int64)],
     "mhdc_destroy": [_P],
     "mhdc_strerror": [C.c_int],
     "mhdc_last_error": [],
@@ -398,6 +400,15 @@ def csr_spmv(n, row_ptr, col, val, x, y, stream=None):
     _check(lib().csr_spmv(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(x), _ptr(y),
                           _stream(stream)), "csr_spmv")
     return y
+
+
+def mhdc_stats(A: Matrix) -> dict:
+    """alpha, beta, P and the model bytes of one product (Sec. 5.3)."""
+    a, b = C.c_double(), C.c_double()
+    p, by = C.c_int64(), C.c_int64()
+    _check(lib().mhdc_stats(C.c_void_p(A.handle), C.byref(a), C.byref(b), C.byref(p), C.byref(by)),
+           "mhdc_stats")
+    return {"alpha": a.value, "beta": b.value, "P": p.value, "bytes": by.value}
 
 
 def mhdc_info(A: Matrix) -> dict:

@@ -229,6 +229,18 @@ int mhdc_info(mhdc_handle A, mhdc_info_t *out)
     return MHDC_OK;
 }
 
+int mhdc_stats(mhdc_handle A, double *alpha, double *beta, int64_t *P, int64_t *bytes)
+{
+    mhdc_info_t inf;
+    const int rc = mhdc_info(A, &inf);
+    if (rc != MHDC_OK) return rc;
+    if (alpha) *alpha = inf.alpha;
+    if (beta) *beta = inf.beta;
+    if (P) *P = inf.P;
+    if (bytes) *bytes = inf.bytes_model;
+    return MHDC_OK;
+}
+
 int mhdc_set_variant(mhdc_handle A, int32_t v)
 {
     if (!A || v < -1 || v >= MHDC_NUM_VARIANTS) {

@@ -52,6 +52,8 @@ def test_status_codes_and_strerror(built_lib):
         txt = built_lib.mhdc_strerror(code).decode()
         assert txt and txt != "unknown status", name
     assert built_lib.mhdc_strerror(12345).decode() == "unknown status"
+    # host-only calls reject a missing handle without touching a device
+    assert built_lib.mhdc_stats(None, None, None, None, None) == codes["MHDC_ERR_INVALID_ARG"]
     import paper_2105_04937_gb300 as m
     for name, code in codes.items():
         assert getattr(m, name) == code, name

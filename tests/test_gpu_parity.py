@@ -41,6 +41,12 @@ def test_example_matches_fig12_on_gpu(mh):
     assert E["csr_val"].tolist() == g["csr_val"]
     assert E["csr_col"].tolist() == g["csr_col_ind"]
     assert E["csr_row_ptr"].tolist() == g["csr_row_ptr"]
+    # the model statistics of this example (Sec. 5.3): P = 5 partial diagonals
+    # of 4 slots, alpha = stored entries / slots, beta = remainder share
+    st = mh.mhdc_stats(h)
+    P, rem = len(g["dia_col_offset"]), len(g["csr_val"])
+    assert st["P"] == P and st["alpha"] == (A.nnz - rem) / (P * 4) and st["beta"] == rem / A.nnz
+    assert st["bytes"] == h.info["bytes_model"]
 
 
 @pytest.mark.parametrize("mode", ["block", "global"])
