@@ -392,9 +392,12 @@ def mhdc_spmm(A: Matrix, X, Y, stream=None):
 
 
 def csr_spmv(n, row_ptr, col, val, x, y, stream=None):
-    """The plain FP64 CSR kernel (Fig. 2) on device tensors."""
+    """The plain FP64 CSR kernel (Fig. 2) on device tensors (the CSR is not
+    validated: pass arrays that mhdc_build would accept)."""
     import torch
     _check_dev(row_ptr, torch.int32, n + 1, "row_ptr")
+    _check_dev(col, torch.int32, None, "col")
+    _check_dev(val, torch.float64, None, "val")
     _check_dev(x, torch.float64, n, "x")
     _check_dev(y, torch.float64, n, "y")
     _check(lib().csr_spmv(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(x), _ptr(y),
