@@ -21,10 +21,12 @@ from .build import SO, build as _build_library  # noqa: F401  (re-exported for b
 
 __all__ = [
     "MHDC_F64", "MHDC_F32", "MHDC_BF16", "MhdcError", "Matrix", "lib", "mhdc_build",
-    "hdc_build", "mhdc_build_dia", "mhdc_dia_spmv", "mhdc_spmv_host_async", "mhdc_host_wait", "Sell", "sell_build", "sell_spmv",
-    "sell_info", "sell_export", "sell_destroy", "mhdc_spmv", "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
+    "hdc_build", "mhdc_build_dia", "mhdc_dia_spmv", "mhdc_spmv_host_async", "mhdc_host_wait",
+    "Sell", "sell_build", "sell_spmv", "sell_info", "sell_export", "sell_destroy", "mhdc_spmv",
+    "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
     "mhdc_info", "mhdc_stats", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
-    "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "mhdc_check",
+    "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "NATIVE_VARIANTS",
+    "EMULATED_VARIANTS", "XW_VARIANTS", "FIRST_EMULATED_VARIANT", "mhdc_check",
     "mhdc_read_bench", "mhdc_read_bench_ctas", "mhdc_build_noalloc",
     "mhdc_fma_bench", "Batch", "mhdc_batch_create", "mhdc_batch_spmv", "mhdc_batch_spmv_graph",
     "mhdc_batch_destroy", "pointer_array", "MHDC_NUM_FEATURES", "MHDC_NUM_CANDIDATES",
