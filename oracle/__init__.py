@@ -58,7 +58,6 @@ def _declare(L):
     sig = {
         "orc_csr_check": (C.c_int, [I64, P, P]),
         "orc_csr_spmv": (None, [I64, P, P, P, P, P, C.c_int]),
-        "orc_csr_spmv_rows": (None, [P, P, P, P, I64, P, P, P]),
         "orc_csr_absrow": (None, [I64, P, P, P, P, P, C.c_int]),
         "orc_round_f32": (None, [I64, P, P]),
         "orc_round_bf16": (None, [I64, P, P]),
@@ -118,15 +117,6 @@ def csr_spmv(A, x, nthreads: int = 0) -> np.ndarray:
     lib().orc_csr_spmv(A.n, _p(_i32(A.row_ptr)), _p(_i32(A.col)), _p(_f64(A.val)), _p(x), _p(y),
                        nthreads)
     return y
-
-
-def csr_spmv_rows(A, x, rows) -> tuple[np.ndarray, np.ndarray]:
-    rows = np.ascontiguousarray(rows, dtype=np.int64)
-    y = np.empty(rows.size)
-    a = np.empty(rows.size)
-    lib().orc_csr_spmv_rows(_p(_i32(A.row_ptr)), _p(_i32(A.col)), _p(_f64(A.val)), _p(_f64(x)),
-                            rows.size, _p(rows), _p(y), _p(a))
-    return y, a
 
 
 def csr_absrow(A, x, nthreads: int = 0) -> np.ndarray:

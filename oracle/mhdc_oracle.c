@@ -77,24 +77,6 @@ void orc_csr_spmv(int64_t n, const int32_t *row_ptr, const int32_t *col,
     }
 }
 
-/* The same product for a list of rows only, plus sum_j |a_ij| |x_j| of each
- * of those rows (the scale the FP64 tolerance is relative to). */
-void orc_csr_spmv_rows(const int32_t *row_ptr, const int32_t *col, const double *val,
-                       const double *x, int64_t m, const int64_t *rows,
-                       double *y_out, double *abs_out)
-{
-    for (int64_t r = 0; r < m; r++) {
-        int64_t i = rows[r];
-        double s = 0.0, a = 0.0;
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
-            s += val[k] * x[col[k]];
-            a += fabs(val[k]) * fabs(x[col[k]]);
-        }
-        y_out[r] = s;
-        abs_out[r] = a;
-    }
-}
-
 /* sum_j |a_ij| |x_j| for every row. */
 void orc_csr_absrow(int64_t n, const int32_t *row_ptr, const int32_t *col,
                     const double *val, const double *x, double *out, int nthreads)

@@ -205,6 +205,69 @@ def test_spmv_matches_dense_matvec(seed):
             assert np.allclose(a, scale, rtol=1e-13, atol=0)
 
 
+def check_csr_absrow():
+    """sum_j |a_ij| |x_j| per row (the scale of every per-row tolerance, Sec.
+    3.1's y = A x) against the dense |A| |x|.  Integer values and x of both
+    signs make the dense product exact, so the comparison is equality: a
+    doubled scale, a dropped absolute value or a missed entry all fail."""
+    for seed in range(4):
+        n = 30 + 11 * seed
+        A = synth.random_sparse(n, 0.15, seed=200 + seed, diag_bias=0.4)
+        rng = synth.Rng(300 + seed, 1)
+        A.val = np.round(rng.uniform(A.nnz, -9, 9)) + np.where(rng.unit(A.nnz) < 0.5, 0.5, -0.5)
+        x = np.round(rng.uniform(n, -7, 7)) - 0.25
+        dense = np.zeros((n, n))
+        dense[A.rows(), A.col] = A.val
+        assert np.array_equal(oracle.csr_absrow(A, x), np.abs(dense) @ np.abs(x)), seed
+    # float data: the same within rounding of the two summation orders
+    A = synth.config_matrix("stencil7_32", scale=0.25)
+    x = synth.uniform_vector(A.n, 9)
+    dense_rows = np.zeros(A.n)
+    np.add.at(dense_rows, A.rows(), np.abs(A.val) * np.abs(x[A.col]))
+    assert np.allclose(oracle.csr_absrow(A, x), dense_rows, rtol=1e-14, atol=0)
+
+
+def test_csr_absrow_matches_dense():
+    check_csr_absrow()
+
+
+def check_mhdc_absrow_terms():
+    """Terms per row of an M-HDC structure, the k of the gamma_k bounds: every
+    remainder entry of the row plus one per selected diagonal of its block,
+    out-of-range positions included (Fig. 13 runs the diagonal loop over the
+    whole block; the kernels add 0 * 0 there).  The selection and the
+    remainder come from the dense brute-force re-derivation, and |A||x| from
+    the dense matrix, so neither side reuses the oracle's conversion."""
+    for seed in range(5):
+        rng = synth.Rng(seed, 77)
+        n = int(rng.integers(1, 8, 40)[0])
+        A = synth.random_sparse(n, 0.2, seed=50 + seed, diag_bias=0.6)
+        dense = np.zeros((n, n))
+        dense[A.rows(), A.col] = A.val
+        x = synth.uniform_vector(n, 40 + seed)
+        clipped_terms = 0
+        for bl in sorted({1, 3, 7, n // 2 + 1, n, n + 2}):
+            for theta in (0.2, 0.5, 0.9):
+                E = dense_convert(dense, bl, theta, "block")
+                M = oracle.convert(A, bl, theta)
+                a, t = oracle.mhdc_absrow(M, x)
+                want = np.zeros(n, dtype=np.int64)
+                for i in range(n):
+                    ib = i // bl
+                    sel = E["dia_offset"][E["dia_ptr"][ib]:E["dia_ptr"][ib + 1]]
+                    rem = sum(1 for j in range(n) if dense[i, j] != 0 and (j - i) not in sel)
+                    want[i] = rem + len(sel)
+                    clipped_terms += sum(1 for d in sel if not 0 <= i + d < n)
+                assert t.tolist() == want.tolist(), (seed, n, bl, theta)
+                assert np.allclose(a, np.abs(dense) @ np.abs(x), rtol=1e-13, atol=0)
+        # the cases above include diagonals that leave the matrix
+        assert clipped_terms > 0
+
+
+def test_mhdc_absrow_terms_match_dense_count():
+    check_mhdc_absrow_terms()
+
+
 # ---------------------------------------------------------------- invariants
 
 def _nonzero_set(A):
@@ -335,7 +398,12 @@ def test_round_f32_matches_numpy_cast():
 def test_round_bf16_matches_torch():
     torch = pytest.importorskip("torch")
     rng = synth.Rng(8, 1)
-    x = np.concatenate([_edge_doubles(), rng.uniform(20000, -1, 1) * 10.0 ** rng.uniform(20000, -30, 30)])
+    # exact BF16 ties (the 16 bits dropped are 0x8000) below and above an
+    # even and an odd kept significand, both signs: nearest-even decides them
+    ties = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8, 3 + 2 ** -7, 3 + 3 * 2 ** -7, 2 ** -100 * (1 + 2 ** -8),
+                     2 ** 100 * (1 + 5 * 2 ** -8)])
+    x = np.concatenate([_edge_doubles(), ties, -ties,
+                        rng.uniform(20000, -1, 1) * 10.0 ** rng.uniform(20000, -30, 30)])
     ours = oracle.round_bf16(x)
     f32 = torch.from_numpy(x.astype(np.float32))
     ref = f32.to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
