@@ -442,9 +442,11 @@ int mhdc_fma_bench(int32_t fp64, int32_t iters, void *d_out, void *stream);
  * Limits: n <= 262144 rows and nnz <= 262144 stored entries; larger inputs
  * return MHDC_ERR_INVALID_ARG with a message saying so.  All temporaries live
  * in one file-scope device array of about 14 MB, which every GPU that loads
- * this library holds until the process exits.  The first call on a device
- * looks that array's address up (cudaGetSymbolAddress) with the device
- * current; make the first call on each device before any stream capture.
+ * this library holds until the process exits.  Every call looks that
+ * array's address up (cudaGetSymbolAddress) with the calling thread's device
+ * current, so a device reset between calls is harmless; the first call on a
+ * device also loads the library's conversion kernels there, so make it before
+ * any stream capture.
  * Every call shares the array and it keeps the last call's contents: calls
  * that overlap on the GPU (other streams, other threads) race and must not be
  * issued; the call clears what must start at zero itself.

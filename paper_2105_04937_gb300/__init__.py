@@ -501,32 +501,69 @@ def mhdc_read_bench(A, out, stream=None):
     return out
 
 
+def _noalloc_check(n, nnz, row_ptr, col, val, n_b, dtype, dia_ptr, dia_offset, dia_val,
+                   csr_row_ptr, csr_col, csr_val):
+    """Argument checks of mhdc_build_noalloc, done before anything runs on the
+    GPU: the C layer receives raw pointers and cannot check lengths or
+    placement, and a short or host-side array would be written out of bounds.
+    nnz = row_ptr[n] (read by the caller)."""
+    import torch
+    if n < 1 or n_b < 1:
+        raise ValueError("n and n_b must be >= 1")
+    if nnz < 0:
+        raise ValueError("row_ptr[n] must be >= 0")
+    store = {MHDC_F64: (torch.float64,), MHDC_F32: (torch.float32,),
+             MHDC_BF16: (torch.bfloat16, torch.int16)}[dtype]
+    nb = (n + n_b - 1) // n_b
+    _check_dev(row_ptr, torch.int32, n + 1, "row_ptr")
+    _check_dev(col, torch.int32, nnz, "col")
+    _check_dev(val, torch.float64, nnz, "val")
+    _check_dev(dia_ptr, torch.int32, nb + 1, "dia_ptr")
+    _check_dev(dia_offset, torch.int32, None, "dia_offset")
+    _check_dev(csr_row_ptr, torch.int32, n + 1, "csr_row_ptr")
+    _check_dev(csr_col, torch.int32, None, "csr_col")
+    for t, nm in ((dia_val, "dia_val"), (csr_val, "csr_val")):
+        if t.dtype not in store:
+            raise TypeError(f"{nm} must be {' or '.join(map(str, store))} for this dtype, "
+                            f"got {t.dtype}")
+        _check_dev(t, t.dtype, None, nm)
+    cap_P = dia_offset.numel()
+    if dia_val.numel() < cap_P * n_b:
+        raise ValueError("dia_val must hold dia_offset.numel() * n_b values")
+    dev = row_ptr.device
+    for t, nm in ((col, "col"), (val, "val"), (dia_ptr, "dia_ptr"), (dia_offset, "dia_offset"),
+                  (dia_val, "dia_val"), (csr_row_ptr, "csr_row_ptr"), (csr_col, "csr_col"),
+                  (csr_val, "csr_val")):
+        if t.device != dev:
+            raise ValueError(f"{nm} is on {t.device}, row_ptr on {dev}")
+    return cap_P, min(csr_col.numel(), csr_val.numel())
+
+
 def mhdc_build_noalloc(n, row_ptr, col, val, n_b, theta, dtype, dia_ptr, dia_offset, dia_val,
                        csr_row_ptr, csr_col, csr_val, stream=None):
-    """mhdc_build into caller-owned device tensors, allocating nothing.
+    """mhdc_build into caller-owned device tensors, allocating no device memory.
 
     Output tensors: dia_ptr int32[ceil(n/n_b)+1], dia_offset int32[cap_P],
-    dia_val (float64 / float32 / int16 bits for bf16)[cap_P * n_b],
-    csr_row_ptr int32[n+1], csr_col int32[cap_rem], csr_val[cap_rem].
-    Returns (P, nnz_rem).  Limits and sharing rules: see include/mhdc.h."""
+    dia_val (float64 / float32 / bfloat16 or int16 bits)[cap_P * n_b],
+    csr_row_ptr int32[n+1], csr_col int32[cap_rem], csr_val[cap_rem]; every
+    tensor on row_ptr's device.  Returns (P, nnz_rem).  Limits and sharing
+    rules: see include/mhdc.h."""
     import torch
     if isinstance(dtype, str):
         dtype = DTYPES[dtype]
     _check_dev(row_ptr, torch.int32, n + 1, "row_ptr")
-    vsz = {MHDC_F64: 8, MHDC_F32: 4, MHDC_BF16: 2}[dtype]
-    for t, nm in ((dia_val, "dia_val"), (csr_val, "csr_val")):
-        if not t.is_cuda or t.element_size() != vsz or not t.is_contiguous():
-            raise ValueError(f"{nm} must be a contiguous CUDA tensor of {vsz}-byte elements")
-    cap_P = dia_offset.numel()
-    if dia_val.numel() < cap_P * n_b:
-        raise ValueError("dia_val must hold dia_offset.numel() * n_b values")
-    cap_rem = min(csr_col.numel(), csr_val.numel())
+    with torch.cuda.device(row_ptr.device):
+        nnz = int(row_ptr[n].item()) if n >= 1 else 0
+    cap_P, cap_rem = _noalloc_check(n, nnz, row_ptr, col, val, int(n_b), dtype, dia_ptr,
+                                    dia_offset, dia_val, csr_row_ptr, csr_col, csr_val)
     P = C.c_int64(0)
     R = C.c_int64(0)
-    rc = lib().mhdc_build_noalloc(n, _ptr(row_ptr), _ptr(col), _ptr(val), int(n_b), float(theta),
-                                  int(dtype), _ptr(dia_ptr), _ptr(dia_offset), _ptr(dia_val), cap_P,
-                                  _ptr(csr_row_ptr), _ptr(csr_col), _ptr(csr_val), cap_rem,
-                                  C.byref(P), C.byref(R), _stream(stream))
+    with torch.cuda.device(row_ptr.device):
+        rc = lib().mhdc_build_noalloc(n, _ptr(row_ptr), _ptr(col), _ptr(val), int(n_b),
+                                      float(theta), int(dtype), _ptr(dia_ptr), _ptr(dia_offset),
+                                      _ptr(dia_val), cap_P, _ptr(csr_row_ptr), _ptr(csr_col),
+                                      _ptr(csr_val), cap_rem, C.byref(P), C.byref(R),
+                                      _stream(stream))
     _check(rc, "mhdc_build_noalloc")
     return P.value, R.value
 

@@ -1563,30 +1563,19 @@ constexpr int64_t NA_WORDS = NA_BASE + 2 * NA_MAX_OVF;
 
 static __device__ __align__(256) int32_t g_noalloc_scratch[NA_WORDS];
 
-std::mutex g_noalloc_mu;
-int32_t *g_noalloc_ptr[64] = {};
-
-// The device address of g_noalloc_scratch on the current device (looked up
-// once per device; host code cannot use the symbol itself as a pointer).
+// The device address of g_noalloc_scratch on the current device.  Host code
+// cannot use the symbol itself as a pointer (in host code it names a host-side
+// stand-in), so every call looks the address up with its device current:
+// after a device reset the module, and with it the array, may sit elsewhere.
 int noalloc_scratch(int32_t **out)
 {
-    int dev = 0;
-    MHDC_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) {
-        set_error_msg("mhdc_build_noalloc: device index out of range");
-        return MHDC_ERR_UNSUPPORTED;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error("cudaGetSymbolAddress(g_noalloc_scratch)", e);
+        return MHDC_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("cudaGetSymbolAddress(g_noalloc_scratch)", e);
-            return MHDC_ERR_CUDA;
-        }
-        g_noalloc_ptr[dev] = static_cast<int32_t *>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<int32_t *>(p);
     return MHDC_OK;
 }
 
@@ -1711,6 +1700,14 @@ int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double
             n, n_b, rp, col, theta, S + NA_IDS, 0, 0, S + NA_KEYS, S + NA_CNT, base, S + NA_LG,
             S + NA_SEL, S + NA_SELCNT, S + NA_OVF);
         MHDC_LAUNCH_CHECK("k_count_select<global>");
+        // a global table holds at least twice its block's entries and cannot
+        // overflow; the flags are read back anyway, as mhdc_build does
+        RC(exclusive_scan_i32(S + NA_OVF, S + NA_OVFPOS, nb, S + NA_SCANS, st));
+        RC(read_i32(S + NA_OVFPOS + nb, &novf, st));
+        if (novf != 0) {
+            set_error_msg("k_count_select: global table overflow");
+            return MHDC_ERR_DEVICE_CHECK;
+        }
     }
     // 3. dia_ptr (caller's array) and the number of partial diagonals
     RC(exclusive_scan_i32(S + NA_SELCNT, dia_ptr, nb, S + NA_SCANS, st));

@@ -7,9 +7,10 @@ that may only hand over buffers it already owns.  They call
 mhdc_build_noalloc with output arrays of their own; its temporaries live in a
 fixed device array inside the library.  Its results must equal what
 mhdc_build + mhdc_export give for the same input, bit for bit (the tolerance
-every conversion test here uses).  Two calls in a row, on different matrices
-and dtypes, check that what one call leaves in the shared device array does
-not leak into the next.  This file is collected last on purpose.
+every conversion test here uses).  Three calls in a row, on different matrices
+and dtypes (the last two through the conversion's global-table path), check
+that what one call leaves in the shared device array does not leak into the
+next.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -66,17 +67,37 @@ def convert_both(mh, A, n_b, theta, dtype):
     return P, R
 
 
-def test_noalloc_matches_mhdc_build_on_two_calls_in_a_row(mh):
+def distinct_offsets_per_block(A, n_b):
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    off = A.col.astype(np.int64) - rows
+    blk = rows // n_b
+    return [np.unique(off[blk == b]).size for b in range((A.n + n_b - 1) // n_b)]
+
+
+# a row block with more distinct offsets than this overflows the largest
+# shared-memory table and is counted in a table inside the device array
+SHARED_TABLE_LIMIT = 12288
+
+
+def test_noalloc_matches_mhdc_build_on_calls_in_a_row(mh):
     # call 1: 7-point stencil on 32^3 (223,232 entries), FP64
     A = synth.config_matrix("stencil7_32")
     P1, R1 = convert_both(mh, A, 1024, 0.6, "f64")
     assert P1 == 222 and R1 == 0
     # call 2: scattered diagonals (232,355 entries, rows with random entries;
-    # two 8192-row blocks with > 12288 distinct offsets each, so both take the
-    # global-table path), BF16
+    # both 8192-row blocks take the global-table path), BF16
     B = synth.config_matrix("scattered_4m", scale=1 / 256)
+    assert min(distinct_offsets_per_block(B, 8192)) > SHARED_TABLE_LIMIT
     P2, R2 = convert_both(mh, B, 8192, 0.6, "bf16")
     assert P2 > 0 and R2 > 0
+    # call 3: another scattered matrix (14,980 rows, a ragged last block) whose
+    # first block also takes the global-table path, FP32: the tables,
+    # overflow list and remainder flags that call 2 left behind must not leak
+    C_ = synth.config_matrix("scattered_4m", scale=1 / 280)
+    assert C_.n == 14980 and C_.nnz <= LIMIT
+    assert distinct_offsets_per_block(C_, 8192)[0] > SHARED_TABLE_LIMIT
+    P3, R3 = convert_both(mh, C_, 8192, 0.6, "f32")
+    assert P3 > 0 and R3 > 0 and (P3, R3) != (P2, R2)
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit(mh):
