@@ -315,6 +315,31 @@ def run_reference(args):
         dist.destroy_process_group()
 
 
+def _graph_launch_us(fn, torch, per_graph=200, replays=10):
+    """Mean device time of fn() (launching on the current stream) for kernels
+    too short to time launch by launch from Python: per_graph back-to-back
+    launches captured in one CUDA graph, the graph replayed between two
+    events."""
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(per_graph):
+            fn()
+    g.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    e0.record(st)
+    for _ in range(replays):
+        g.replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / (replays * per_graph)
+
+
 def _mean_launch_us(fn, steps, warmup, stream, torch):
     tot, mean = time_launches(fn, steps, warmup, stream, torch)
     return mean * 1e3
@@ -353,6 +378,30 @@ def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
     import synth
     out = {}
     steps = max(10, min(args.steps, 400))
+    # -- the 7-point stencil on 32^3 (FP64, n_b = 1024, theta = 0.6) against the
+    # FP64 CSR kernel: its whole working set (about 2.5 MB) stays in L2, so
+    # this is an in-cache figure, not an HBM one
+    S1 = synth.config_matrix("stencil7_32")
+    r1, c1, v1 = (torch.from_numpy(a).cuda() for a in (S1.row_ptr, S1.col, S1.val))
+    x1 = torch.from_numpy(synth.uniform_vector(S1.n, 0)).cuda()
+    y1 = torch.empty_like(x1)
+    H1 = mh.mhdc_build(S1.n, r1, c1, v1, 1024, 0.6, "f64")
+    _, t1 = mh.mhdc_tune(H1, x1, y1)
+    mh.mhdc_set_variant(H1, min(mh.NATIVE_VARIANTS, key=lambda v: t1[v]))
+    us_m = _graph_launch_us(lambda: mh.mhdc_spmv(H1, x1, y1), torch)
+    us_c = _graph_launch_us(lambda: mh.csr_spmv(S1.n, r1, c1, v1, x1, y1), torch)
+    i1 = H1.info
+    out["cfg1_stencil7_32"] = {
+        "workload": "7-point FDM stencil on 32^3 (32,768 rows, 223,232 nnz), FP64, n_b=1024, "
+                    "theta=0.6; in-cache (working set in L2); 200 launches per CUDA graph, "
+                    "replayed 10 times",
+        "mhdc_us": round(us_m, 3), "mhdc_gflops": round(gflops(S1.nnz, us_m / 1e6), 1),
+        "csr_us": round(us_c, 3), "csr_gflops": round(gflops(S1.nnz, us_c / 1e6), 1),
+        "mhdc_vs_csr": round(us_c / us_m, 3), "P": i1["P"], "alpha": round(i1["alpha"], 4),
+        "bytes_model": i1["bytes_model"], "gbs_from_l2": round(i1["bytes_model"] / us_m / 1e3, 1)}
+    H1.destroy()
+    del r1, c1, v1, x1, y1
+    log(f"cfg1: {json.dumps(out['cfg1_stencil7_32'])}")
     # -- reduced precision: FP64 / FP32 / BF16 storage, n_b = 2048, theta = 0.6
     S = synth.config_matrix("scattered_4m")
     srp = torch.from_numpy(S.row_ptr).cuda()
@@ -445,15 +494,22 @@ def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
     log(f"reduced precision, headline matrix: {json.dumps(hp)[:300]}")
     # -- SpMM on the headline matrix in FP32
     H32 = mh.mhdc_build(A.n, rp, col, val, 4096, 0.6, "f32")
-    mm = {"workload": "stencil27_128, FP32 values and X, Y row-major n x k"}
+    mm = {"workload": "stencil27_128, FP32 values and X, Y row-major n x k",
+          "bytes_model": "V_A + 8 k n (X read once, Y written once, FP32)"}
+    peak, _ = measured_peak()
     for k in (1, 4, 8, 16):
         X = torch.rand((A.n, k), dtype=torch.float32, device="cuda")
         Y = torch.empty((A.n, k), dtype=torch.float32, device="cuda")
+        shape = None
+        if k > 1:   # the library's own tuner picks the tile shape for this k
+            shape, shape_us = mh.mhdc_spmm_tune(H32, X, Y)
         us = _mean_launch_us(lambda: mh.mhdc_spmm(H32, X, Y, stream), min(steps, 200), 3,
                              stream, torch)
         bytes_ = H32.info["bytes_model"] + (k - 1) * A.n * 8
         mm[f"k{k}"] = {"kernel_us": round(us, 2), "gflops": round(gflops(A.nnz * k, us / 1e6), 1),
-                       "gbs": round(bytes_ / us / 1e3, 1)}
+                       "gbs": round(bytes_ / us / 1e3, 1), "hbm_frac": round(bytes_ / us / 1e3 / peak, 4),
+                       "bytes": bytes_, "shape": shape,
+                       "shape_us": None if shape is None else [round(t, 1) for t in shape_us]}
         del X, Y
     H32.destroy()
     out["a8_spmm_fp32"] = mm
@@ -886,7 +942,8 @@ def main():
         torch.cuda.synchronize()
         rel = float(((y_emu - y_nat).abs() / absr.clamp_min(1e-300)).max())
         accuracy = {"variant": acc_variant, "max_row_err_vs_native_over_sum_abs": rel,
-                    "tolerance": 1e-12, "bound": 7e-13, "within": rel <= 1e-12}
+                    "tolerance": 1e-12, "bound": "(5.2 k + 18) 2^-48, k <= 48: < 9.6e-13",
+                    "within": rel <= 1e-12}
         log(f"accuracy of emulated variant {acc_variant}: {accuracy}")
         del y_emu, y_nat, absr
         if emulated:

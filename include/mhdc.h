@@ -183,15 +183,31 @@ int mhdc_host_wait(mhdc_handle A);
 
 /*
  * mhdc_spmm -- Y = A X for k right-hand sides (the M-HDC kernel of Fig. 13
- * applied to k vectors at once, reading A once).
+ * applied to k vectors at once, reading A once per pass of up to 16 columns).
  *
  *   k        number of right-hand sides, 1 <= k <= 64
  *   d_X      row-major n x k block of x dtype, leading dimension ldx >= k
  *   d_Y      row-major n x k block of y dtype, leading dimension ldy >= k
+ * Each (row, column) is summed as mhdc_spmv sums a row: the CSR remainder in
+ * column order, then the diagonals in ascending order.  X and Y rows are
+ * moved in 16-byte slices when X + column, Y + column and the leading
+ * dimensions are aligned to the slice (else element by element).
  * Asynchronous on `stream`.
+ *
+ * mhdc_spmm_set_variant -- SpMM tile shape v (0..MHDC_NUM_SPMM_VARIANTS-1:
+ *   (rows per lane, diagonals per load group) = (1,4), (2,2), (2,4), (4,2);
+ *   -1: the default, 2).  Every shape gives the same Y.
+ * mhdc_spmm_tune -- time every shape on (d_X, d_Y) with k columns (Y is
+ *   overwritten), keep the fastest in the handle, write its id to *best and,
+ *   if times_us is not NULL, each shape's mean time in microseconds to
+ *   times_us[MHDC_NUM_SPMM_VARIANTS].  Synchronous.
  */
+#define MHDC_NUM_SPMM_VARIANTS 4
 int mhdc_spmm(mhdc_handle A, int32_t k, const void *d_X, int64_t ldx, void *d_Y, int64_t ldy,
               void *stream);
+int mhdc_spmm_set_variant(mhdc_handle A, int32_t v);
+int mhdc_spmm_tune(mhdc_handle A, int32_t k, const void *d_X, int64_t ldx, void *d_Y,
+                   int64_t ldy, void *stream, int32_t *best, float *times_us);
 
 /*
  * mhdc_dia_spmv -- y = A x in the unblocked DIA order (Sec. 3.3, Fig. 5) for a
@@ -254,8 +270,9 @@ int mhdc_stats(mhdc_handle A, double *alpha, double *beta, int64_t *P, int64_t *
  * 49 significant bits; products and sums by error-free transformations): on
  * GB300 the FP64 pipe is about 64x slower than FP32, and these variants move
  * the arithmetic to the FP32 pipe.  Their per-row error stays below
- * 7e-13 * sum_j |a_ij||x_j| (inside the FP64 tolerance 1e-12) as long as every
- * nonzero |a_ij| and |x_j| lies in [2^-51, 2^60] and a row has at most 64
+ * (5.2 k + 18) 2^-48 sum_j |a_ij||x_j| for a row of k terms, under 9.6e-13 *
+ * sum_j |a_ij||x_j| (inside the FP64 tolerance 1e-12), as long as every
+ * nonzero |a_ij| and |x_j| lies in [2^-45, 2^60] and a row has at most 48
  * terms; the handle checks its values at build and each product checks x on
  * the device, and outside that window the product runs the native FP64 path
  * (variant -1's arithmetic) instead.
@@ -268,8 +285,12 @@ int mhdc_stats(mhdc_handle A, double *alpha, double *beta, int64_t *P, int64_t *
  * mhdc_set_variant -- use variant v for this handle (-1: default chosen from n_b).
  *                     The first v in 10-15 on an FP64 handle makes its FP32-pair
  *                     arrays (device memory as large as dia_val and csr_val)
- *                     on the legacy default stream and waits for them.
- * mhdc_tune        -- time every variant on (d_x, d_y) (overwriting d_y), keep
+ *                     on the legacy default stream and waits for them; if they
+ *                     cannot be allocated it returns MHDC_ERR_OOM, keeps no part
+ *                     of them and leaves the variant unchanged.
+ * mhdc_tune        -- (makes the FP32-pair arrays of an FP64 handle first, as
+ *                     mhdc_set_variant does, with the same MHDC_ERR_OOM rule)
+ *                     time every variant on (d_x, d_y) (overwriting d_y), keep
  *                     the fastest in the handle, write its id to *best and, if
  *                     times_us is not NULL, each variant's mean time in
  *                     microseconds to times_us[MHDC_NUM_VARIANTS].  Synchronous.
@@ -399,6 +420,25 @@ const char *mhdc_strerror(int code);
 /* mhdc_last_error -- details of the last failed call on this host thread
  * (which call or kernel, and the CUDA error text); "" if none yet. */
 const char *mhdc_last_error(void);
+
+/*
+ * Allocation-failure injection, for testing the cleanup paths of every call
+ * (the paper has no counterpart).  Every device allocation of the library
+ * (cudaMalloc and its stream-ordered pool) passes one host-side counter.
+ *
+ * mhdc_debug_fail_alloc -- from now on, the n-th allocation attempt fails as
+ *   if the device were out of memory (nothing is allocated and no CUDA call
+ *   is made; the calling entry point returns MHDC_ERR_OOM after releasing
+ *   what it had allocated).  n = 0 disarms.  Resets the attempt counter.
+ *   Setting the environment variable MHDC_FAULT_ALLOC=n arms the same hook
+ *   for the whole process at its first allocation.  Not thread-safe against
+ *   concurrent library calls that allocate.
+ * mhdc_debug_alloc_stats -- allocation attempts since the last arming, and
+ *   allocations made and not yet freed by the library (any pointer may be
+ *   NULL).  Host-only; always MHDC_OK.
+ */
+int mhdc_debug_fail_alloc(int64_t n);
+int mhdc_debug_alloc_stats(int64_t *attempts, int64_t *live);
 
 /*
  * mhdc_stream_bench -- the paper's memory benchmarks (Sec. 6.2, Figs. 19-20)

@@ -23,7 +23,8 @@ __all__ = [
     "MHDC_F64", "MHDC_F32", "MHDC_BF16", "MhdcError", "Matrix", "lib", "mhdc_build",
     "hdc_build", "mhdc_build_dia", "mhdc_dia_spmv", "mhdc_spmv_host_async", "mhdc_host_wait",
     "Sell", "sell_build", "sell_spmv", "sell_info", "sell_export", "sell_destroy", "mhdc_spmv",
-    "mhdc_spmv_host", "mhdc_spmm", "csr_spmv", "mhdc_export",
+    "mhdc_spmv_host", "mhdc_spmm", "mhdc_spmm_set_variant", "mhdc_spmm_tune",
+    "MHDC_NUM_SPMM_VARIANTS", "csr_spmv", "mhdc_export",
     "mhdc_info", "mhdc_stats", "mhdc_destroy", "mhdc_strerror", "mhdc_stream_bench", "DTYPES",
     "mhdc_set_variant", "mhdc_tune", "MHDC_NUM_VARIANTS", "NATIVE_VARIANTS",
     "EMULATED_VARIANTS", "XW_VARIANTS", "FIRST_EMULATED_VARIANT", "mhdc_check",
@@ -34,7 +35,7 @@ __all__ = [
     "mhdc_candidate", "mhdc_features", "mhdc_autotune", "mhdc_select", "Mlp",
     "mhdc_mlp_create", "mhdc_mlp_forward", "mhdc_mlp_grad", "mhdc_mlp_train_step",
     "mhdc_mlp_get_params", "mhdc_mlp_set_params", "mhdc_mlp_destroy", "mhdc_num_candidates",
-    "mhdc_mlp_num_params",
+    "mhdc_mlp_num_params", "mhdc_debug_fail_alloc", "mhdc_debug_alloc_stats",
 ]
 
 MHDC_F64, MHDC_F32, MHDC_BF16 = 0, 1, 2
@@ -78,6 +79,9 @@ _SIGS = {
     "mhdc_host_wait": [_P],
     "mhdc_dia_spmv": [_P, _P, _P, _P],
     "mhdc_spmm": [_P, _I32, _P, _I64, _P, _I64, _P],
+    "mhdc_spmm_set_variant": [_P, _I32],
+    "mhdc_spmm_tune": [_P, _I32, _P, _I64, _P, _I64, _P, C.POINTER(C.c_int32),
+                       C.POINTER(C.c_float)],
     "csr_spmv": [_I64, _P, _P, _P, _P, _P, _P],
     "mhdc_export": [_P, _P, _P, _P, _P, _P, _P],
     "mhdc_info": [_P, C.POINTER(_Info)],
@@ -112,9 +116,12 @@ _SIGS = {
     "mhdc_build_noalloc": [_I64, _P, _P, _P, _I32, _D, _I32, _P, _P, _P, _I64, _P, _P, _P, _I64,
                            C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P],
     "mhdc_tune": [_P, _P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)],
+    "mhdc_debug_fail_alloc": [_I64],
+    "mhdc_debug_alloc_stats": [C.POINTER(_I64), C.POINTER(_I64)],
 }
 
 MHDC_NUM_VARIANTS = 20
+MHDC_NUM_SPMM_VARIANTS = 4
 MHDC_NUM_FEATURES = 64
 MHDC_NUM_CANDIDATES = 45
 MHDC_SELECT_PAPER, MHDC_SELECT_MLP, MHDC_SELECT_AUTOTUNE, MHDC_SELECT_MODEL = 0, 1, 2, 4
@@ -377,8 +384,7 @@ def mhdc_spmv_host(A: Matrix, x, y, stream=None):
     return y
 
 
-def mhdc_spmm(A: Matrix, X, Y, stream=None):
-    """Y = A X for row-major n x k device tensors X and Y."""
+def _spmm_args(A: Matrix, X, Y):
     xt, yt = _xy_types(A)
     for t, dt, nm in ((X, xt, "X"), (Y, yt, "Y")):
         if not t.is_cuda or t.dtype != dt:
@@ -387,10 +393,32 @@ def mhdc_spmm(A: Matrix, X, Y, stream=None):
             raise ValueError(f"{nm} must be n x k with unit column stride")
     if X.shape[1] != Y.shape[1]:
         raise ValueError("X and Y must have the same number of columns")
-    k = X.shape[1]
+    return X.shape[1]
+
+
+def mhdc_spmm(A: Matrix, X, Y, stream=None):
+    """Y = A X for row-major n x k device tensors X and Y."""
+    k = _spmm_args(A, X, Y)
     _check(lib().mhdc_spmm(C.c_void_p(A.handle), k, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0),
                            _stream(stream)), "mhdc_spmm")
     return Y
+
+
+def mhdc_spmm_set_variant(A: Matrix, v: int):
+    """SpMM tile shape v (0..MHDC_NUM_SPMM_VARIANTS-1, -1: default)."""
+    _check(lib().mhdc_spmm_set_variant(C.c_void_p(A.handle), int(v)), "mhdc_spmm_set_variant")
+
+
+def mhdc_spmm_tune(A: Matrix, X, Y, stream=None):
+    """Time every SpMM tile shape on (X, Y); keep the fastest.  Returns
+    (best, per-shape microseconds)."""
+    k = _spmm_args(A, X, Y)
+    best = C.c_int32(-1)
+    times = (C.c_float * MHDC_NUM_SPMM_VARIANTS)()
+    _check(lib().mhdc_spmm_tune(C.c_void_p(A.handle), k, _ptr(X), X.stride(0), _ptr(Y),
+                                Y.stride(0), _stream(stream), C.byref(best), times),
+           "mhdc_spmm_tune")
+    return best.value, list(times)
 
 
 def csr_spmv(n, row_ptr, col, val, x, y, stream=None):
@@ -566,6 +594,19 @@ def mhdc_build_noalloc(n, row_ptr, col, val, n_b, theta, dtype, dia_ptr, dia_off
                                       _stream(stream))
     _check(rc, "mhdc_build_noalloc")
     return P.value, R.value
+
+
+def mhdc_debug_fail_alloc(n: int):
+    """Make the library's n-th device allocation attempt from now on fail as
+    out of memory (host-side injection; 0 disarms)."""
+    _check(lib().mhdc_debug_fail_alloc(int(n)), "mhdc_debug_fail_alloc")
+
+
+def mhdc_debug_alloc_stats() -> tuple[int, int]:
+    """(allocation attempts since the last arming, live allocations)."""
+    a, l_ = C.c_int64(0), C.c_int64(0)
+    lib().mhdc_debug_alloc_stats(C.byref(a), C.byref(l_))
+    return a.value, l_.value
 
 
 def mhdc_fma_bench(fp64: bool, iters: int, out, stream=None):

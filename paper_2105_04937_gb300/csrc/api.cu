@@ -79,8 +79,8 @@ int mhdc_spmv_host(mhdc_handle A, const void *h_x, void *h_y, void *stream)
     }
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bx = value_size(A->dtype) * (size_t)A->n, by = y_size(A->dtype) * (size_t)A->n;
-    if (!A->x_stage) MHDC_CUDA_TRY(cudaMalloc(&A->x_stage, bx ? bx : 16));
-    if (!A->y_stage) MHDC_CUDA_TRY(cudaMalloc(&A->y_stage, by ? by : 16));
+    if (!A->x_stage) MHDC_CUDA_TRY(dmalloc(&A->x_stage, bx ? bx : 16));
+    if (!A->y_stage) MHDC_CUDA_TRY(dmalloc(&A->y_stage, by ? by : 16));
     MHDC_CUDA_TRY(cudaMemcpyAsync(A->x_stage, h_x, bx, cudaMemcpyHostToDevice, st));
     int rc = launch_spmv(A, A->x_stage, A->y_stage, st);
     if (rc != MHDC_OK) return rc;
@@ -117,8 +117,8 @@ int mhdc_spmv_host_async(mhdc_handle A, const void *h_x, void *h_y)
         if (!A->as_comp) MHDC_CUDA_TRY(cudaStreamCreateWithFlags(&A->as_comp, fl));
         if (!A->as_out) MHDC_CUDA_TRY(cudaStreamCreateWithFlags(&A->as_out, fl));
         for (int k = 0; k < NS; k++) {
-            if (!A->ax[k]) MHDC_CUDA_TRY(cudaMalloc(&A->ax[k], bx));
-            if (!A->ay[k]) MHDC_CUDA_TRY(cudaMalloc(&A->ay[k], by));
+            if (!A->ax[k]) MHDC_CUDA_TRY(dmalloc(&A->ax[k], bx));
+            if (!A->ay[k]) MHDC_CUDA_TRY(dmalloc(&A->ay[k], by));
             if (!A->ae_in[k]) MHDC_CUDA_TRY(cudaEventCreateWithFlags(&A->ae_in[k], cudaEventDisableTiming));
             if (!A->ae_comp[k])
                 MHDC_CUDA_TRY(cudaEventCreateWithFlags(&A->ae_comp[k], cudaEventDisableTiming));
@@ -162,6 +162,26 @@ int mhdc_spmm(mhdc_handle A, int32_t k, const void *d_X, int64_t ldx, void *d_Y,
         return MHDC_ERR_INVALID_ARG;
     }
     return launch_spmm(A, k, d_X, ldx, d_Y, ldy, (cudaStream_t)stream);
+}
+
+int mhdc_spmm_set_variant(mhdc_handle A, int32_t v)
+{
+    if (!A || v < -1 || v >= MHDC_NUM_SPMM_VARIANTS) {
+        set_error_msg("mhdc_spmm_set_variant: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    A->spmm_variant = v;
+    return MHDC_OK;
+}
+
+int mhdc_spmm_tune(mhdc_handle A, int32_t k, const void *d_X, int64_t ldx, void *d_Y,
+                   int64_t ldy, void *stream, int32_t *best, float *times_us)
+{
+    if (!A || k < 1 || k > 64 || ldx < k || ldy < k || (A->n > 0 && (!d_X || !d_Y))) {
+        set_error_msg("mhdc_spmm_tune: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    return tune_spmm(A, k, d_X, ldx, d_Y, ldy, (cudaStream_t)stream, best, times_us);
 }
 
 int csr_spmv(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const double *d_val,
@@ -325,8 +345,8 @@ int mhdc_batch_create(int32_t m, const mhdc_handle *mats, mhdc_batch_handle *out
     B->total_tiles = tiles;
     B->total_nnz = nnz;
     cudaGetDevice(&B->device);
-    cudaError_t e = cudaMalloc((void **)&B->d_mats, sizeof(BatchMat) * (size_t)m);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&B->d_ctr, 2 * sizeof(unsigned long long));
+    cudaError_t e = dmalloc((void **)&B->d_mats, sizeof(BatchMat) * (size_t)m);
+    if (e == cudaSuccess) e = dmalloc((void **)&B->d_ctr, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess)
         e = cudaMemcpy(B->d_mats, h.data(), sizeof(BatchMat) * (size_t)m, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(B->d_ctr, 0, 2 * sizeof(unsigned long long));
@@ -393,8 +413,8 @@ int mhdc_batch_destroy(mhdc_batch_handle B)
     if (!B) return MHDC_OK;
     if (B->graph) cudaGraphExecDestroy(B->graph);
     if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
-    cudaFree(B->d_mats);
-    cudaFree(B->d_ctr);
+    dfree(B->d_mats);
+    dfree(B->d_ctr);
     delete B;
     return MHDC_OK;
 }

@@ -688,7 +688,7 @@ struct Buf {
     cudaStream_t st = nullptr;
     ~Buf()
     {
-        if (p) cudaFreeAsync(p, st);
+        if (p) dfree_async(p, st);
     }
     template <typename T>
     T *as() const { return static_cast<T *>(p); }
@@ -700,7 +700,7 @@ int dalloc(Buf &b, size_t bytes, cudaStream_t st)
     cudaMemPool_t pool;
     int rc = build_pool(&pool);
     if (rc != MHDC_OK) return rc;
-    cudaError_t e = cudaMallocFromPoolAsync(&b.p, bytes, pool, st);
+    cudaError_t e = dmalloc_pool(&b.p, bytes, pool, st);
     if (e != cudaSuccess) {
         b.p = nullptr;
         set_error("cudaMallocFromPoolAsync", e);
@@ -713,7 +713,7 @@ int dalloc(Buf &b, size_t bytes, cudaStream_t st)
 int dalloc_raw(void **p, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = dmalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
         set_error("cudaMalloc", e);
@@ -986,18 +986,18 @@ int feature_hist(int64_t n, const int32_t *rp, const int32_t *col, int32_t n_b,
 void free_matrix(mhdc_matrix *A)
 {
     if (!A) return;
-    cudaFree(A->dia_ptr);
-    cudaFree(A->dia_offset);
-    cudaFree(A->dia_val);
-    cudaFree(A->csr_row_ptr);
-    cudaFree(A->csr_col);
-    cudaFree(A->csr_val);
-    cudaFree(A->x_stage);
-    cudaFree(A->y_stage);
+    dfree(A->dia_ptr);
+    dfree(A->dia_offset);
+    dfree(A->dia_val);
+    dfree(A->csr_row_ptr);
+    dfree(A->csr_col);
+    dfree(A->csr_val);
+    dfree(A->x_stage);
+    dfree(A->y_stage);
     for (int k = 0; k < mhdc_matrix::ASYNC_SLOTS; k++) {
         if (A->ae_done[k]) cudaEventSynchronize(A->ae_done[k]);
-        cudaFree(A->ax[k]);
-        cudaFree(A->ay[k]);
+        dfree(A->ax[k]);
+        dfree(A->ay[k]);
         if (A->ae_in[k]) cudaEventDestroy(A->ae_in[k]);
         if (A->ae_comp[k]) cudaEventDestroy(A->ae_comp[k]);
         if (A->ae_done[k]) cudaEventDestroy(A->ae_done[k]);
@@ -1005,11 +1005,11 @@ void free_matrix(mhdc_matrix *A)
     if (A->as_in) cudaStreamDestroy(A->as_in);
     if (A->as_comp) cudaStreamDestroy(A->as_comp);
     if (A->as_out) cudaStreamDestroy(A->as_out);
-    cudaFree(A->status);
-    cudaFree(A->dia_dw);
-    cudaFree(A->csr_dw);
-    cudaFree(A->x_dw);
-    cudaFree(A->dw_flag);
+    dfree(A->status);
+    dfree(A->dia_dw);
+    dfree(A->csr_dw);
+    dfree(A->x_dw);
+    dfree(A->dw_flag);
     delete A;
 }
 
@@ -1053,25 +1053,26 @@ __global__ void k_max_diff(int64_t m, const int32_t *__restrict__ ptr, int *out)
 
 // Split an FP64 handle's values into FP32 pairs and decide whether the
 // emulated product may be used.  Lack of memory only disables emulation.
-int prepare_dw(mhdc_matrix *A, cudaStream_t st)
+static void free_dw(mhdc_matrix *A)
 {
-    A->dw_ok = false;
-    if (A->dtype != MHDC_F64 || A->n == 0) return MHDC_OK;
+    dfree(A->dia_dw);
+    dfree(A->csr_dw);
+    dfree(A->x_dw);
+    dfree(A->dw_flag);
+    A->dia_dw = A->csr_dw = A->x_dw = nullptr;
+    A->dw_flag = nullptr;
+}
+
+// The FP32-pair arrays of the emulated FP64 variants.  On any failure they
+// are released again (the handle keeps its native variants) and the error is
+// returned.
+static int prepare_dw_arrays(mhdc_matrix *A, cudaStream_t st)
+{
     const int64_t nd = A->P * (int64_t)A->n_b;
-    if (cudaMalloc((void **)&A->dia_dw, sizeof(float2) * (size_t)(nd ? nd : 1)) != cudaSuccess ||
-        cudaMalloc((void **)&A->csr_dw, sizeof(float2) * (size_t)(A->nnz_rem ? A->nnz_rem : 1)) !=
-            cudaSuccess ||
-        cudaMalloc((void **)&A->x_dw, sizeof(float2) * (size_t)A->n) != cudaSuccess ||
-        cudaMalloc((void **)&A->dw_flag, sizeof(unsigned long long)) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(A->dia_dw);
-        cudaFree(A->csr_dw);
-        cudaFree(A->x_dw);
-        cudaFree(A->dw_flag);
-        A->dia_dw = A->csr_dw = A->x_dw = nullptr;
-        A->dw_flag = nullptr;
-        return MHDC_OK;
-    }
+    MHDC_CUDA_TRY(dmalloc((void **)&A->dia_dw, sizeof(float2) * (size_t)(nd ? nd : 1)));
+    MHDC_CUDA_TRY(dmalloc((void **)&A->csr_dw, sizeof(float2) * (size_t)(A->nnz_rem ? A->nnz_rem : 1)));
+    MHDC_CUDA_TRY(dmalloc((void **)&A->x_dw, sizeof(float2) * (size_t)A->n));
+    MHDC_CUDA_TRY(dmalloc((void **)&A->dw_flag, sizeof(unsigned long long)));
     MHDC_CUDA_TRY(cudaMemsetAsync(A->dw_flag, 0, sizeof(unsigned long long), st));
     Buf w;
     RC(dalloc(w, 2 * sizeof(int), st));
@@ -1100,6 +1101,19 @@ int prepare_dw(mhdc_matrix *A, cudaStream_t st)
     A->dw_ok = h[0] == 0 && (h[1] + h[2]) <= DW_MAX_TERMS;
     A->bytes_device += (int64_t)sizeof(float2) * (nd + A->nnz_rem + A->n);
     return MHDC_OK;
+}
+
+int prepare_dw(mhdc_matrix *A, cudaStream_t st)
+{
+    A->dw_ok = false;
+    if (A->dtype != MHDC_F64 || A->n == 0) return MHDC_OK;
+    const int rc = prepare_dw_arrays(A, st);
+    if (rc != MHDC_OK) {
+        cudaStreamSynchronize(st);  // kernels that write the arrays are done
+        free_dw(A);
+        A->dw_ok = false;
+    }
+    return rc;
 }
 
 int ensure_dw(mhdc_matrix *A, cudaStream_t st)
@@ -1491,7 +1505,7 @@ int tmp_alloc(void **p, size_t bytes, cudaStream_t st)
 
 void tmp_free(void *p, cudaStream_t st)
 {
-    if (p) cudaFreeAsync(p, st);
+    if (p) dfree_async(p, st);
 }
 
 int build_matrix_dia(int64_t n, int32_t nd, const int32_t *d_offset, const double *d_val,

@@ -34,6 +34,7 @@ struct mhdc_matrix {
     int64_t bytes_device = 0;
     int spmv_grid = 0;               // CTAs of the SpMV launch
     int variant = -1;                // SpMV tile shape (-1: chosen from n_b)
+    int spmm_variant = -1;           // SpMM tile shape (-1: default)
     int *status = nullptr;           // device word: bit 0 = a bounded wait gave up
     // FP64 handles: values split into FP32 (hi, lo) pairs for the emulated product
     float2 *dia_dw = nullptr;        // [P * n_b]
@@ -80,6 +81,14 @@ inline size_t value_size(int dtype)
 }
 inline size_t y_size(int dtype) { return dtype == MHDC_F64 ? 8 : 4; }
 
+// Every device allocation and free of the library (alloc.cu): cudaMalloc /
+// cudaFree / stream-ordered pool calls, with a live count and the host-side
+// allocation-failure hook of mhdc_debug_fail_alloc.
+cudaError_t dmalloc(void **p, size_t bytes);
+void dfree(void *p);
+cudaError_t dmalloc_pool(void **p, size_t bytes, cudaMemPool_t pool, cudaStream_t st);
+void dfree_async(void *p, cudaStream_t st);
+
 // Record the details of the last failure of this thread (mhdc_last_error).
 void set_error(const char *where, cudaError_t e);
 void set_error_msg(const char *msg);
@@ -109,8 +118,6 @@ int build_noalloc(int64_t n, const int32_t *rp, const int32_t *col, const double
 
 // Products; defined in spmv.cu.
 int launch_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream);
-int launch_spmm(mhdc_matrix *A, int k, const void *d_X, int64_t ldx, void *d_Y,
-                int64_t ldy, cudaStream_t stream);
 int launch_dia(const mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream);
 int launch_csr(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                const double *x, double *y, cudaStream_t stream);
@@ -139,14 +146,20 @@ int launch_spmv_tma_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y,
 int launch_split_x(mhdc_matrix *A, const void *d_x, unsigned long long epoch, cudaStream_t stream);
 // Emulated FP64 (FP32 pairs): nonzero |a|, |x| must lie in [2^DW_EMIN, 2^DW_EMAX]
 // and a row may have at most DW_MAX_TERMS terms (error bound, see spmv.cu).
-constexpr int DW_EMIN = -51;
+constexpr int DW_EMIN = -45;
 constexpr int DW_EMAX = 60;
-constexpr int DW_MAX_TERMS = 64;
+constexpr int DW_MAX_TERMS = 48;
 int prepare_dw(mhdc_matrix *A, cudaStream_t st);
 // prepare_dw once per handle (the emulated variants and the tuner call it).
 int ensure_dw(mhdc_matrix *A, cudaStream_t st);
 int tune_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream, int32_t *best,
               float *times_us);
+
+// SpMM; defined in spmm.cu.
+int launch_spmm(mhdc_matrix *A, int k, const void *d_X, int64_t ldx, void *d_Y,
+                int64_t ldy, cudaStream_t stream);
+int tune_spmm(mhdc_matrix *A, int k, const void *d_X, int64_t ldx, void *d_Y, int64_t ldy,
+              cudaStream_t stream, int32_t *best, float *times_us);
 
 // The 16 bytes starting `sh` bytes (sh < 16, a multiple of the element size)
 // into the 32-byte window (lo, hi): two aligned loads replace V element loads
@@ -179,9 +192,11 @@ constexpr int REM_LONG = 64;
 __device__ __forceinline__ double rem_in(double v) { return v; }
 __device__ __forceinline__ float rem_in(float v) { return v; }
 __device__ __forceinline__ float rem_in(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double rem_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rem_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 // Adds the remainder entries [a, b) of one row to acc (zero on entry in
-// every kernel), in column order.
+// every kernel), in column order, one FMA per entry.
 template <typename Acc, typename VT, typename X>
 __device__ __forceinline__ void rem_row_add(Acc &acc, int32_t a, int32_t b,
                                             const int32_t *__restrict__ col,
@@ -196,7 +211,58 @@ __device__ __forceinline__ void rem_row_add(Acc &acc, int32_t a, int32_t b,
             return;
         }
     }
-    for (int32_t k = a; k < b; k++) acc += rem_in(val[k]) * rem_in(__ldg(x + col[k]));
+    for (int32_t k = a; k < b; k++) acc = rem_fma(rem_in(val[k]), rem_in(__ldg(x + col[k])), acc);
+}
+
+// The remainder rows of one lane, R at a time, with the operations of
+// rem_row_add (each row from zero in s[r], column order, one FMA per entry,
+// rows longer than REM_LONG through its FP64 path) but with the loads of all
+// R rows in flight together: each round loads the next E entries of every
+// row -- columns and values, then the gathers of x, all independent --
+// before the FMAs of the round (rem_row_add walks the rows one after the
+// other).  Row r holds the entries [a[r], b[r]); a[r] >= b[r] is an empty row.
+template <int R, int E, typename Acc, typename VT, typename X>
+__device__ __forceinline__ void rem_rows_add(Acc (&s)[R], int32_t (&a)[R], const int32_t (&b)[R],
+                                             const int32_t *__restrict__ col,
+                                             const VT *__restrict__ val,
+                                             const X *__restrict__ x)
+{
+    if constexpr (sizeof(Acc) < sizeof(double)) {
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            if (b[r] - a[r] > REM_LONG) {
+                rem_row_add(s[r], a[r], b[r], col, val, x);
+                a[r] = b[r];
+            }
+    }
+    for (;;) {
+        bool more = false;
+#pragma unroll
+        for (int r = 0; r < R; r++) more |= a[r] < b[r];
+        if (!more) break;
+        int32_t c[R][E];
+        VT v[R][E];
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const bool in = e < b[r] - a[r];
+                c[r][e] = in ? col[a[r] + e] : 0;
+                v[r][e] = in ? val[a[r] + e] : VT(0);
+            }
+        X xv[R][E];
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+            for (int e = 0; e < E; e++) xv[r][e] = e < b[r] - a[r] ? __ldg(x + c[r][e]) : X(0);
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+            for (int e = 0; e < E; e++)
+                if (e < b[r] - a[r]) s[r] = rem_fma(rem_in(v[r][e]), rem_in(xv[r][e]), s[r]);
+#pragma unroll
+        for (int r = 0; r < R; r++) a[r] = b[r] - a[r] > E ? a[r] + E : b[r];
+    }
 }
 
 // Exclusive prefix sum of m int32 values into out[0..m] (out[m] = total);

@@ -164,10 +164,10 @@ Views views(const mhdc_mlp *M, float *base)
 int ensure_work(mhdc_mlp *M, int B)
 {
     if (M->work && M->work_batch >= B) return MHDC_OK;
-    cudaFree(M->work);
+    dfree(M->work);
     M->work = nullptr;
     const int64_t words = (int64_t)B * (6 * M->H + 2 * M->O);
-    MHDC_CUDA_TRY(cudaMalloc((void **)&M->work, sizeof(float) * (size_t)words));
+    MHDC_CUDA_TRY(dmalloc((void **)&M->work, sizeof(float) * (size_t)words));
     M->work_batch = B;
     return MHDC_OK;
 }
@@ -300,10 +300,10 @@ int mhdc_autotune(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, con
     }
     cudaStream_t st = (cudaStream_t)stream;
     void *x = nullptr, *y = nullptr;
-    MHDC_CUDA_TRY(cudaMalloc(&x, 8 * (size_t)n));
-    cudaError_t e = cudaMalloc(&y, 8 * (size_t)n);
+    MHDC_CUDA_TRY(dmalloc(&x, 8 * (size_t)n));
+    cudaError_t e = dmalloc(&y, 8 * (size_t)n);
     if (e != cudaSuccess) {
-        cudaFree(x);
+        dfree(x);
         set_error("cudaMalloc", e);
         return cuda_status(e);
     }
@@ -334,8 +334,8 @@ int mhdc_autotune(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, con
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(x);
-    cudaFree(y);
+    dfree(x);
+    dfree(y);
     return rc;
 }
 
@@ -365,11 +365,11 @@ int mhdc_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed
     fill(v.W2, (int64_t)M->H * M->H, M->H);
     fill(v.W3, (int64_t)M->O * M->H, M->H);
     const size_t bytes = sizeof(float) * (size_t)M->P;
-    cudaError_t e = cudaMalloc((void **)&M->params, bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&M->grads, bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&M->m, bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&M->v, bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&M->loss, sizeof(float));
+    cudaError_t e = dmalloc((void **)&M->params, bytes);
+    if (e == cudaSuccess) e = dmalloc((void **)&M->grads, bytes);
+    if (e == cudaSuccess) e = dmalloc((void **)&M->m, bytes);
+    if (e == cudaSuccess) e = dmalloc((void **)&M->v, bytes);
+    if (e == cudaSuccess) e = dmalloc((void **)&M->loss, sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(M->params, h.data(), bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(M->m, 0, bytes);
     if (e == cudaSuccess) e = cudaMemset(M->v, 0, bytes);
@@ -459,12 +459,12 @@ int mhdc_mlp_train_step(mhdc_mlp_handle M, int32_t batch, const float *d_X, cons
 int mhdc_mlp_destroy(mhdc_mlp_handle M)
 {
     if (!M) return MHDC_OK;
-    cudaFree(M->params);
-    cudaFree(M->grads);
-    cudaFree(M->m);
-    cudaFree(M->v);
-    cudaFree(M->work);
-    cudaFree(M->loss);
+    dfree(M->params);
+    dfree(M->grads);
+    dfree(M->m);
+    dfree(M->v);
+    dfree(M->work);
+    dfree(M->loss);
     delete M;
     return MHDC_OK;
 }
@@ -500,13 +500,13 @@ int mhdc_select(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col, const
         int rc = compute_features(n, d_row_ptr, d_col, st, f);
         if (rc != MHDC_OK) return rc;
         float *d = nullptr;
-        MHDC_CUDA_TRY(cudaMalloc((void **)&d, sizeof(float) * (MHDC_NUM_FEATURES + MHDC_NUM_CANDIDATES)));
+        MHDC_CUDA_TRY(dmalloc((void **)&d, sizeof(float) * (MHDC_NUM_FEATURES + MHDC_NUM_CANDIDATES)));
         cudaMemcpyAsync(d, f, sizeof f, cudaMemcpyHostToDevice, st);
         rc = mhdc_mlp_forward(mlp, 1, d, d + MHDC_NUM_FEATURES, stream);
         if (rc == MHDC_OK)
             cudaMemcpyAsync(pred, d + MHDC_NUM_FEATURES, sizeof pred, cudaMemcpyDeviceToHost, st);
         cudaStreamSynchronize(st);
-        cudaFree(d);
+        dfree(d);
         if (rc != MHDC_OK) return rc;
         for (int k = 0; k < MHDC_NUM_CANDIDATES; k++)
             if (ok(k) && (best < 0 || pred[k] < pred[best])) best = k;

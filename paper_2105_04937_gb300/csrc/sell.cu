@@ -155,17 +155,17 @@ k_sell_spmv(int64_t n, int32_t C, const int32_t *__restrict__ perm,
 void free_sell(sell_matrix *S)
 {
     if (!S) return;
-    cudaFree(S->perm);
-    cudaFree(S->rowlen);
-    cudaFree(S->chunk_ptr);
-    cudaFree(S->col);
-    cudaFree(S->val);
+    dfree(S->perm);
+    dfree(S->rowlen);
+    dfree(S->chunk_ptr);
+    dfree(S->col);
+    dfree(S->val);
     delete S;
 }
 
 int alloc(void **p, size_t bytes)
 {
-    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    cudaError_t e = dmalloc(p, bytes ? bytes : 16);
     if (e != cudaSuccess) {
         *p = nullptr;
         set_error("cudaMalloc", e);

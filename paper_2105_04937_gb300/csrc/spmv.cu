@@ -65,6 +65,15 @@ __device__ __forceinline__ T ldg_elem(const T *p)
 
 constexpr int SPMV_THREADS = 256;
 constexpr int SPMV_WARPS = SPMV_THREADS / 32;
+// Resident CTAs per SM the register tiles are compiled for, i.e. their
+// register budget (5 CTAs of 256 threads: 48 registers a thread, 4: 64).
+// The kernels wait on memory, so the smallest tiles keep 40 warps per SM (32
+// for BF16, whose 8 remainder rows per lane need more); larger tiles need
+// more registers for their loads in flight.
+constexpr int spmv_min_blocks(int U, int D, int vsize)
+{
+    return U * D <= 2 ? (vsize == 2 ? 4 : 5) : U * D <= 4 ? 3 : 2;
+}
 
 // x[j .. j+V) into xv: one 16-byte load when j is 16-byte aligned, else V
 // element loads (all in bounds: the caller checked 0 <= j, j + V <= n).
@@ -86,7 +95,7 @@ __device__ __forceinline__ void load_x(const X *__restrict__ x, int64_t j, bool 
 // The block's diagonals are taken D at a time: the D * U 16-byte value loads
 // of a group are issued first, then the x loads, then the FMAs, so a warp
 // keeps D * U * 512 bytes of dia_val in flight.
-template <typename VT, int U, int D, bool VEC>
+template <typename VT, int U, int D, bool VEC, bool PF = false>
 __device__ __forceinline__ void
 reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restrict__ dia_ptr,
          const int32_t *__restrict__ dia_offset, const VT *__restrict__ dia_val,
@@ -113,6 +122,20 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
 
     // the block's diagonal range, loaded with the remainder bounds below (independent)
     const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
+    if constexpr (VEC && PF) {
+        // every diagonal's values of this tile into L2 ahead of their loads:
+        // one bulk prefetch per diagonal (lane d takes diagonal p0 + d), the
+        // tile's slice clipped to the block's n_b slots (16-byte multiples).
+        // Used by the batched kernel, whose warps walk several tiles in turn;
+        // it slowed the one-tile-per-warp grid down.
+        const int32_t nv = (n_b - tw < RW) ? n_b - tw : RW;
+        const uint32_t bytes = (uint32_t)(nv * (int32_t)sizeof(VT));
+        for (int32_t q = p0 + lane; q < p1; q += 32) {
+            const VT *src = dia_val + (int64_t)q * n_b + tw;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes)
+                         : "memory");
+        }
+    }
 
     Acc acc[U][V];
 #pragma unroll
@@ -120,38 +143,51 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
 #pragma unroll
         for (int m = 0; m < V; m++) acc[u][m] = Acc(0);
 
-    // CSR remainder rows of the tile (Fig. 13, first loop).  With V >= 4 rows
-    // per lane (FP32, BF16) each lane instead sums whole rows (row tw + rr for
-    // rr = lane, lane + 32, ...), in column order from zero, and the sums reach
-    // their owners through shared memory: the same operations as summing into
-    // acc directly, with one row per lane instead of V in sequence.
+    // CSR remainder rows of the tile (Fig. 13, first loop), summed by
+    // rem_rows_add: every row from zero in column order, with the next
+    // entries of all the lane's rows loaded together.  With V >= 4 rows per
+    // lane (FP32, BF16) each lane instead sums whole rows tw + rr (rr = lane,
+    // lane + 32, ..., coalesced row bounds), and the sums reach their owners
+    // through shared memory: the same operations as summing into acc
+    // directly.
     {
         const int32_t tend = full ? tw + RW : rows;
         const int32_t q0 = csr_row_ptr[r0 + tw], q1 = csr_row_ptr[r0 + tend];
         if (q0 != q1 && V < 4) {
-            // two rows per lane (FP64): sum them in place
+            // V rows per vector (FP64: 2), U vectors per lane
+            constexpr int R = U * V;
+            Acc s[R];
+            int32_t a[R], b[R];
 #pragma unroll
             for (int u = 0; u < U; u++)
 #pragma unroll
                 for (int m = 0; m < V; m++) {
                     const int32_t t = tl[u] + m;
-                    if (t < rows) {
-                        const int64_t i = r0 + t;
-                        rem_row_add(acc[u][m], csr_row_ptr[i], csr_row_ptr[i + 1], csr_col,
-                                    csr_val, x);
-                    }
+                    s[u * V + m] = Acc(0);
+                    a[u * V + m] = t < rows ? csr_row_ptr[r0 + t] : 0;
+                    b[u * V + m] = t < rows ? csr_row_ptr[r0 + t + 1] : 0;
                 }
+            rem_rows_add<R, 1>(s, a, b, csr_col, csr_val, x);
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int m = 0; m < V; m++) acc[u][m] = s[u * V + m];
         } else if (q0 != q1) {
+            constexpr int R = RW / 32;
             __shared__ Acc rsum[SPMV_WARPS][RW];
             Acc *rs = rsum[threadIdx.x >> 5];
-            for (int rr = lane; rr < RW; rr += 32) {
-                Acc sum = Acc(0);
-                if (tw + rr < rows) {
-                    const int64_t i = r0 + tw + rr;
-                    rem_row_add(sum, csr_row_ptr[i], csr_row_ptr[i + 1], csr_col, csr_val, x);
-                }
-                rs[rr] = sum;
+            Acc s[R];
+            int32_t a[R], b[R];
+#pragma unroll
+            for (int j = 0; j < R; j++) {
+                const int32_t t = tw + lane + 32 * j;
+                s[j] = Acc(0);
+                a[j] = t < rows ? csr_row_ptr[r0 + t] : 0;
+                b[j] = t < rows ? csr_row_ptr[r0 + t + 1] : 0;
             }
+            rem_rows_add<R, 1>(s, a, b, csr_col, csr_val, x);
+#pragma unroll
+            for (int j = 0; j < R; j++) rs[lane + 32 * j] = s[j];
             __syncwarp();
 #pragma unroll
             for (int u = 0; u < U; u++)
@@ -243,7 +279,7 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
 }
 
 template <typename VT, int U, int D, bool VEC>
-__global__ void __launch_bounds__(SPMV_THREADS)
+__global__ void __launch_bounds__(SPMV_THREADS, spmv_min_blocks(U, D, sizeof(VT)))
 k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
             const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
             const VT *__restrict__ dia_val, const int32_t *__restrict__ csr_row_ptr,
@@ -265,15 +301,13 @@ k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
 // 2^-48 relative error (the split of the values is done once at build, that
 // of x by k_split_x with integer operations only), and each row accumulates
 //   s += a * x
-// as an FP32 pair: the product by TwoProduct (an FMA gives the exact error of
-// hi * hi) plus the two cross terms, normalised by Fast2Sum; the sum by the
-// accurate double-word addition (Joldes, Muller, Popescu, "Tight and rigorous
-// error bounds for basic building blocks of double-word arithmetic", ACM TOMS
-// 2017, Alg. 6: relative error <= 3u^2 / (1 - 4u), u = 2^-24).
-// Error per row, k terms, every nonzero |a|, |x| in [2^-51, 2^60] (so every
-// intermediate is a normal FP32 number): inputs 2 * 2^-48, product 3 * 2^-48,
-// sum 3 * 2^-48 per step, all relative to sum_j |a_ij x_j|, plus the final
-// rounding to FP64: at most (5 + 3k) * 2^-48 + 2^-53 < 7e-13 for k <= 64.
+// as an FP32 pair (dw::dw_fma): the high product enters the high word by
+// TwoSum, and the product's exact error, the two cross products and the
+// TwoSum error are added into the low word, renormalised by Fast2Sum (15 FP32
+// operations a term).  Error per row of k terms, every nonzero |a|, |x| in
+// [2^-45, 2^60] and k <= 48: at most (5.2 k + 18) * 2^-48 * sum_j |a_ij x_j|
+// including the final rounding to FP64, i.e. below 9.6e-13 (the derivation
+// is in dw_arith.cuh).
 // Outside the window the same launch runs the native FP64 tile instead.
 // ---------------------------------------------------------------------------
 // x_dw[i] = FP32 pair of x[i] (integer operations only): hi = x rounded to 24
@@ -327,7 +361,7 @@ k_split_x(int64_t n, const double *__restrict__ x, float2 *__restrict__ x_dw,
 }
 
 template <int U, int D>
-__global__ void __launch_bounds__(SPMV_THREADS)
+__global__ void __launch_bounds__(SPMV_THREADS, U * D <= 2 ? 5 : 4)
 k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
                const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
                const float2 *__restrict__ dia_dw, const int32_t *__restrict__ csr_row_ptr,
@@ -361,6 +395,7 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
     for (int u = 0; u < U; u++)
 #pragma unroll
         for (int m = 0; m < V; m++) sh[u][m] = sl[u][m] = 0.f;
+    const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
 
     {
         const int32_t tend = full ? tw + RW : rows;
@@ -381,7 +416,6 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
         }
     }
 
-    const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
     const int64_t xrow0 = r0 + tw;
     int32_t p = p0;
     auto group = [&](auto Dc) {
@@ -448,125 +482,6 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
 #pragma unroll
         for (int m = 0; m < V; m++)
             if (tl[u] + m < rows) y[r0 + tl[u] + m] = dw::f32_to_f64(sh[u][m]) + dw::f32_to_f64(sl[u][m]);
-}
-
-// ---------------------------------------------------------------------------
-// SpMM: Y = A X for k right-hand sides (row-major X, Y), the M-HDC kernel of
-// Fig. 13 with each scalar x_j replaced by row j of X.  A lane owns U rows
-// (r, r + 32, ...) of a warp tile and KC columns [c0, c0 + KC) of Y; per
-// diagonal it loads one value per row (coalesced across the warp) and the KC
-// contiguous entries of X's row j = i + off (16-byte vectors when aligned),
-// so a warp reads 32 consecutive rows of X per diagonal.
-// ---------------------------------------------------------------------------
-template <typename X, int KC>
-__device__ __forceinline__ void load_row(const X *__restrict__ p, bool vec, X (&v)[KC])
-{
-    if constexpr ((KC * sizeof(X)) % 16 == 0) {
-        if (vec) {
-#pragma unroll
-            for (int q = 0; q < (int)(KC * sizeof(X) / 16); q++) {
-                const uint4 r = __ldg(reinterpret_cast<const uint4 *>(p) + q);
-                memcpy(reinterpret_cast<char *>(v) + 16 * q, &r, 16);
-            }
-            return;
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < KC; c++) v[c] = __ldg(p + c);
-}
-
-template <typename VT, int KC, int U>
-__global__ void __launch_bounds__(SPMV_THREADS)
-k_mhdc_spmm(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles, int32_t c0, int32_t k,
-            const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
-            const VT *__restrict__ dia_val, const int32_t *__restrict__ csr_row_ptr,
-            const int32_t *__restrict__ csr_col, const VT *__restrict__ csr_val,
-            const typename Tr<VT>::X *__restrict__ Xm, int64_t ldx,
-            typename Tr<VT>::Y *__restrict__ Ym, int64_t ldy)
-{
-    using Acc = typename Tr<VT>::Acc;
-    using X = typename Tr<VT>::X;
-    constexpr int RW = 32 * U;
-    const int lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5);
-    if (w >= n_tiles) return;
-    const int64_t ib = w / tpb;
-    const int32_t tw = (int32_t)(w - ib * tpb) * RW;
-    const int64_t r0 = ib * (int64_t)n_b;
-    const int32_t rows = (int32_t)((n - r0 < n_b) ? (n - r0) : n_b);
-    if (tw >= rows) return;
-    const int kc = (k - c0 < KC) ? k - c0 : KC;  // columns of this pass (ragged last pass)
-    const bool vec = kc == KC && (reinterpret_cast<uintptr_t>(Xm + c0) & 15) == 0 &&
-                     ((ldx * (int64_t)sizeof(X)) & 15) == 0;
-    Acc acc[U][KC];
-#pragma unroll
-    for (int u = 0; u < U; u++)
-#pragma unroll
-        for (int c = 0; c < KC; c++) acc[u][c] = Acc(0);
-    auto add_row = [&](int u, Acc a, int64_t j) {
-        X xv[KC];
-        const X *xp = Xm + j * ldx + c0;
-        if (kc == KC) {
-            load_row<X, KC>(xp, vec, xv);
-        } else {
-#pragma unroll
-            for (int c = 0; c < KC; c++) xv[c] = c < kc ? __ldg(xp + c) : X(0);
-        }
-#pragma unroll
-        for (int c = 0; c < KC; c++) acc[u][c] += a * widen(xv[c]);
-    };
-    // CSR remainder rows (Fig. 13, first loop)
-    {
-        const int32_t tend = (tw + RW < rows) ? tw + RW : rows;
-        if (csr_row_ptr[r0 + tw] != csr_row_ptr[r0 + tend]) {
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                const int32_t t = tw + u * 32 + lane;
-                if (t < rows) {
-                    const int64_t i = r0 + t;
-                    const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
-                    if (sizeof(Acc) < sizeof(double) && b - a > REM_LONG) {
-                        // a long row: each column summed in FP64 and rounded
-                        // once, as rem_row_add does for one right-hand side
-#pragma unroll
-                        for (int c = 0; c < KC; c++)
-                            if (c < kc) {
-                                double s = 0.0;
-                                for (int32_t q = a; q < b; q++)
-                                    s = fma((double)widen(csr_val[q]),
-                                            (double)widen(__ldg(Xm + csr_col[q] * ldx + c0 + c)), s);
-                                acc[u][c] = (Acc)s;
-                            }
-                    } else {
-                        for (int32_t q = a; q < b; q++) add_row(u, widen(csr_val[q]), csr_col[q]);
-                    }
-                }
-            }
-        }
-    }
-    // diagonals (Fig. 13, second loop)
-    const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
-#pragma unroll 2
-    for (int32_t p = p0; p < p1; p++) {
-        const int64_t off = dia_offset[p];
-        const VT *vp = dia_val + (int64_t)p * n_b;
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int32_t t = tw + u * 32 + lane;
-            const int64_t j = r0 + t + off;
-            if (t < rows && j >= 0 && j < n) add_row(u, widen(vp[t]), j);
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-        const int32_t t = tw + u * 32 + lane;
-        if (t < rows) {
-            typename Tr<VT>::Y *yp = Ym + (r0 + t) * ldy + c0;
-#pragma unroll
-            for (int c = 0; c < KC; c++)
-                if (c < kc) yp[c] = acc[u][c];
-        }
-    }
 }
 
 // Plain CSR (Fig. 2), one thread per row: s = fma(val[k], x[col_ind[k]], s)
@@ -962,53 +877,6 @@ int launch_fma_probe(int fp64, int iters, void *out, cudaStream_t stream)
     return MHDC_OK;
 }
 
-template <typename VT, int KC>
-int spmm_pass(const mhdc_matrix *A, int32_t c0, int32_t k, const void *X, int64_t ldx, void *Y,
-              int64_t ldy, cudaStream_t st)
-{
-    constexpr int U = KC >= 8 ? 1 : 2;
-    constexpr int RW = 32 * U;
-    const int32_t tpb = (int32_t)((A->n_b + RW - 1) / RW);
-    const int64_t tiles = (int64_t)tpb * A->n_blocks;
-    const int64_t grid = (tiles + SPMV_WARPS - 1) / SPMV_WARPS;
-    k_mhdc_spmm<VT, KC, U><<<(unsigned)grid, SPMV_THREADS, 0, st>>>(
-        A->n, A->n_b, tpb, tiles, c0, k, A->dia_ptr, A->dia_offset,
-        static_cast<const VT *>(A->dia_val), A->csr_row_ptr, A->csr_col,
-        static_cast<const VT *>(A->csr_val), static_cast<const typename Tr<VT>::X *>(X), ldx,
-        static_cast<typename Tr<VT>::Y *>(Y), ldy);
-    MHDC_LAUNCH_CHECK("k_mhdc_spmm");
-    return MHDC_OK;
-}
-
-template <typename VT>
-int spmm_typed(const mhdc_matrix *A, int k, const void *X, int64_t ldx, void *Y, int64_t ldy,
-               cudaStream_t st)
-{
-    // column passes of at most 16; the pass width follows k
-    for (int32_t c0 = 0; c0 < k; c0 += 16) {
-        const int kc = (k - c0 < 16) ? k - c0 : 16;
-        int rc;
-        if (kc > 8) rc = spmm_pass<VT, 16>(A, c0, k, X, ldx, Y, ldy, st);
-        else if (kc > 4) rc = spmm_pass<VT, 8>(A, c0, k, X, ldx, Y, ldy, st);
-        else if (kc > 2) rc = spmm_pass<VT, 4>(A, c0, k, X, ldx, Y, ldy, st);
-        else rc = spmm_pass<VT, 2>(A, c0, k, X, ldx, Y, ldy, st);
-        if (rc != MHDC_OK) return rc;
-    }
-    return MHDC_OK;
-}
-
-int launch_spmm(mhdc_matrix *A, int k, const void *d_X, int64_t ldx, void *d_Y, int64_t ldy,
-                cudaStream_t stream)
-{
-    if (A->n == 0) return MHDC_OK;
-    if (k == 1 && ldx == 1 && ldy == 1) return launch_spmv(A, d_X, d_Y, stream);
-    switch (A->dtype) {
-    case MHDC_F64: return spmm_typed<double>(A, k, d_X, ldx, d_Y, ldy, stream);
-    case MHDC_F32: return spmm_typed<float>(A, k, d_X, ldx, d_Y, ldy, stream);
-    default: return spmm_typed<__nv_bfloat16>(A, k, d_X, ldx, d_Y, ldy, stream);
-    }
-}
-
 int launch_stream_bench(int64_t N, const double *A, const double *B, const int32_t *I, double *C,
                         int indirect, cudaStream_t stream)
 {
@@ -1036,7 +904,7 @@ namespace {
 constexpr int BATCH_CHUNK = 4;
 
 template <typename VT>
-__global__ void __launch_bounds__(SPMV_THREADS)
+__global__ void __launch_bounds__(SPMV_THREADS, 4)
 k_batch_spmv(int32_t m, const BatchMat *__restrict__ mats, int64_t total_tiles,
              const void *const *__restrict__ xs, void *const *__restrict__ ys,
              unsigned long long *__restrict__ ctr)
@@ -1061,7 +929,7 @@ k_batch_spmv(int32_t m, const BatchMat *__restrict__ mats, int64_t total_tiles,
             using X = typename Tr<VT>::X;
             using Y = typename Tr<VT>::Y;
             if (M.vec)
-                reg_tile<VT, 1, 2, true>(w, M.n, M.n_b, M.tpb, M.dia_ptr, M.dia_offset,
+                reg_tile<VT, 1, 2, true, true>(w, M.n, M.n_b, M.tpb, M.dia_ptr, M.dia_offset,
                                          static_cast<const VT *>(M.dia_val), M.csr_row_ptr,
                                          M.csr_col, static_cast<const VT *>(M.csr_val),
                                          static_cast<const X *>(xs[lo]), static_cast<Y *>(ys[lo]));

@@ -541,6 +541,39 @@ def test_spmm_full_size_fp32_k16(mh):
     check_spmm(mh, h, M, A, X, "f32")
 
 
+@pytest.mark.parametrize("dt", DTYPES)
+def test_spmm_every_tile_shape(mh, dt):
+    # every SpMM tile shape sums each (row, column) in the same order: the
+    # shapes agree bit for bit, and each meets the column-wise bounds; X and Y
+    # with a padded leading dimension take the element-by-element path
+    t = torch()
+    cases = [(synth.config_matrix("stencil27_128", scale=0.2), 1000),
+             (synth.random_sparse(301, 0.04, seed=8, diag_bias=0.6), 37),
+             (synth.config_matrix("scattered_4m", scale=1 / 512), 2048)]
+    for A, n_b in cases:
+        h, M = check_build(mh, A, n_b, 0.6, dt)
+        for k in (2, 4, 8, 12, 16, 20):
+            X = synth.uniform_vector(A.n * k, 90 + k).reshape(A.n, k)
+            Ys = []
+            for v in range(mh.MHDC_NUM_SPMM_VARIANTS):
+                mh.mhdc_spmm_set_variant(h, v)
+                check_spmm(mh, h, M, A, X, dt, pad=1 if k == 12 else 0)
+                xd, _ = x_device(X.ravel(), dt)
+                Xd = xd.view(A.n, k)
+                Y = t.empty((A.n, k), dtype=t.float64 if dt == "f64" else t.float32,
+                            device="cuda")
+                mh.mhdc_spmm(h, Xd, Y)
+                Ys.append(Y)
+            t.cuda.synchronize()
+            for v in range(1, len(Ys)):
+                assert t.equal(Ys[v], Ys[0]), (n_b, k, v)
+        best, times = mh.mhdc_spmm_tune(h, Xd, Ys[0])
+        assert 0 <= best < mh.MHDC_NUM_SPMM_VARIANTS and all(tm > 0 for tm in times)
+        mh.mhdc_spmm_set_variant(h, -1)
+        with pytest.raises(mh.MhdcError):
+            mh.mhdc_spmm_set_variant(h, mh.MHDC_NUM_SPMM_VARIANTS)
+
+
 def test_spmm_k64_and_bad_args(mh):
     t = torch()
     A = synth.config_matrix("stencil7_32", scale=0.25)
