@@ -302,11 +302,23 @@ int mhdc_tune(mhdc_handle A, const void *d_x, void *d_y, void *stream, int32_t *
 
 /*
  * mhdc_check -- read and clear the handle's device status word: returns
- * MHDC_ERR_TIMEOUT if a bounded device-side wait of an earlier product on
- * this handle gave up (its y is then incomplete), else MHDC_OK.
+ * MHDC_ERR_DEVICE_CHECK if a bounds check of a checked product (below)
+ * failed, else MHDC_ERR_TIMEOUT if a bounded device-side wait of an earlier
+ * product on this handle gave up (its y is then incomplete), else MHDC_OK.
  * Synchronizes the device.
+ *
+ * mhdc_set_checked -- on = 1: from now on mhdc_spmv and mhdc_spmv_host(_async)
+ * on this handle run a bounds-checked product (the default tile shape,
+ * whatever mhdc_set_variant chose): before every access the index into
+ * dia_ptr, dia_offset, dia_val, csr_row_ptr, csr_col, csr_val, x and y is
+ * compared with that array's extent; a failed check skips the access (the
+ * term counts as 0, a y row is not written) and mhdc_check reports it.  An
+ * in-bounds product gives the same y as the unchecked default.  A debugging
+ * aid, slower than the tuned kernels; the other products (SpMM, DIA order,
+ * batch) are not affected.  on = 0 switches it off.  Host-only.
  */
 int mhdc_check(mhdc_handle A);
+int mhdc_set_checked(mhdc_handle A, int32_t on);
 
 /*
  * Batched product: y_i = A_i x_i for m handles in one persistent launch (no

@@ -35,7 +35,7 @@ __all__ = [
     "mhdc_candidate", "mhdc_features", "mhdc_autotune", "mhdc_select", "Mlp",
     "mhdc_mlp_create", "mhdc_mlp_forward", "mhdc_mlp_grad", "mhdc_mlp_train_step",
     "mhdc_mlp_get_params", "mhdc_mlp_set_params", "mhdc_mlp_destroy", "mhdc_num_candidates",
-    "mhdc_mlp_num_params", "mhdc_debug_fail_alloc", "mhdc_debug_alloc_stats",
+    "mhdc_mlp_num_params", "mhdc_debug_fail_alloc", "mhdc_debug_alloc_stats", "mhdc_set_checked",
 ]
 
 MHDC_F64, MHDC_F32, MHDC_BF16 = 0, 1, 2
@@ -93,6 +93,7 @@ _SIGS = {
     "mhdc_stream_bench": [_I64, _P, _P, _P, _P, _I32, _P],
     "mhdc_set_variant": [_P, _I32],
     "mhdc_check": [_P],
+    "mhdc_set_checked": [_P, _I32],
     "mhdc_read_bench": [_I64, _P, _P, _P],
     "mhdc_read_bench_ctas": [],
     "mhdc_fma_bench": [_I32, _I32, _P, _P],
@@ -508,6 +509,11 @@ def mhdc_tune(A: Matrix, x, y, stream=None):
                            C.byref(best), times), "mhdc_tune")
     A._info = None
     return best.value, [float(t) for t in times]
+
+
+def mhdc_set_checked(A: Matrix, on: bool = True):
+    """Products of this handle run the bounds-checked kernel (see mhdc.h)."""
+    _check(lib().mhdc_set_checked(C.c_void_p(A.handle), 1 if on else 0), "mhdc_set_checked")
 
 
 def mhdc_check(A: Matrix):

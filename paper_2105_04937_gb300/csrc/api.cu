@@ -299,9 +299,23 @@ int mhdc_check(mhdc_handle A)
     MHDC_CUDA_TRY(cudaMemcpy(&h, A->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (h) {
         MHDC_CUDA_TRY(cudaMemset(A->status, 0, sizeof(int)));
+        if (h & STATUS_BOUNDS) {
+            set_error_msg("a bounds check of a checked product failed (the access was skipped)");
+            return MHDC_ERR_DEVICE_CHECK;
+        }
         set_error_msg("a bounded device-side wait gave up");
         return MHDC_ERR_TIMEOUT;
     }
+    return MHDC_OK;
+}
+
+int mhdc_set_checked(mhdc_handle A, int32_t on)
+{
+    if (!A || (on != 0 && on != 1)) {
+        set_error_msg("mhdc_set_checked: invalid argument");
+        return MHDC_ERR_INVALID_ARG;
+    }
+    A->checked = on != 0;
     return MHDC_OK;
 }
 

@@ -35,7 +35,9 @@ struct mhdc_matrix {
     int spmv_grid = 0;               // CTAs of the SpMV launch
     int variant = -1;                // SpMV tile shape (-1: chosen from n_b)
     int spmm_variant = -1;           // SpMM tile shape (-1: default)
-    int *status = nullptr;           // device word: bit 0 = a bounded wait gave up
+    int *status = nullptr;           // device word: bit 0 = a bounded wait gave up,
+                                     // bit 1 = a bounds check of a checked product failed
+    bool checked = false;            // products run the bounds-checked kernel
     // FP64 handles: values split into FP32 (hi, lo) pairs for the emulated product
     float2 *dia_dw = nullptr;        // [P * n_b]
     float2 *csr_dw = nullptr;        // [nnz_rem]
@@ -263,6 +265,49 @@ __device__ __forceinline__ void rem_rows_add(Acc (&s)[R], int32_t (&a)[R], const
 #pragma unroll
         for (int r = 0; r < R; r++) a[r] = b[r] - a[r] > E ? a[r] + E : b[r];
     }
+}
+
+// Bounds-checked products (mhdc_set_checked): the extents of a handle's
+// arrays and its status word.  ck_in(ck, lo, hi, ext) is true when the
+// index range [lo, hi) lies inside [0, ext); otherwise it sets bit 1 of the
+// status word (mhdc_check then reports MHDC_ERR_DEVICE_CHECK) and the caller
+// skips the access.
+struct BoundsCheck {
+    int64_t n_blocks, P, dia_slots, nnz_rem;
+    int *status;
+};
+constexpr int STATUS_BOUNDS = 2;
+
+__device__ __forceinline__ bool ck_in(const BoundsCheck &ck, int64_t lo, int64_t hi, int64_t ext)
+{
+    if (lo >= 0 && lo <= hi && hi <= ext) return true;
+    atomicOr(ck.status, STATUS_BOUNDS);
+    return false;
+}
+
+// rem_row_add with every index checked: the entry range against the
+// remainder's extent, each column against [0, n).  An access that fails is
+// skipped (the entry counts as 0).
+template <typename Acc, typename VT, typename X>
+__device__ __forceinline__ void rem_row_add_ck(Acc &acc, int32_t a, int32_t b,
+                                               const int32_t *__restrict__ col,
+                                               const VT *__restrict__ val, const X *__restrict__ x,
+                                               int64_t n, const BoundsCheck &ck)
+{
+    if (!ck_in(ck, a, b, ck.nnz_rem)) return;
+    auto xat = [&](int32_t k) -> X {
+        const int32_t c = col[k];
+        return ck_in(ck, c, (int64_t)c + 1, n) ? __ldg(x + c) : X(0);
+    };
+    if constexpr (sizeof(Acc) < sizeof(double)) {
+        if (b - a > REM_LONG) {
+            double s = 0.0;
+            for (int32_t k = a; k < b; k++) s = fma((double)rem_in(val[k]), (double)rem_in(xat(k)), s);
+            acc += (Acc)s;
+            return;
+        }
+    }
+    for (int32_t k = a; k < b; k++) acc = rem_fma(rem_in(val[k]), rem_in(xat(k)), acc);
 }
 
 // Exclusive prefix sum of m int32 values into out[0..m] (out[m] = total);

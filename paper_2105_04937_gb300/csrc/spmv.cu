@@ -66,13 +66,14 @@ __device__ __forceinline__ T ldg_elem(const T *p)
 constexpr int SPMV_THREADS = 256;
 constexpr int SPMV_WARPS = SPMV_THREADS / 32;
 // Resident CTAs per SM the register tiles are compiled for, i.e. their
-// register budget (5 CTAs of 256 threads: 48 registers a thread, 4: 64).
-// The kernels wait on memory, so the smallest tiles keep 40 warps per SM (32
-// for BF16, whose 8 remainder rows per lane need more); larger tiles need
-// more registers for their loads in flight.
+// register budget (5 CTAs of 256 threads: 48 registers a thread, 4: 64, 2:
+// 128).  The kernels wait on memory, so the small tiles keep 40 warps per SM
+// (32 for BF16, whose 8 remainder rows per lane need more, and for tiles of
+// 4 loads per group); the largest tiles need more registers for their loads
+// in flight.
 constexpr int spmv_min_blocks(int U, int D, int vsize)
 {
-    return U * D <= 2 ? (vsize == 2 ? 4 : 5) : U * D <= 4 ? 3 : 2;
+    return U * D <= 2 ? (vsize == 2 ? 4 : 5) : U * D <= 4 ? (vsize == 2 && U > 1 ? 3 : 4) : 2;
 }
 
 // x[j .. j+V) into xv: one 16-byte load when j is 16-byte aligned, else V
@@ -95,13 +96,18 @@ __device__ __forceinline__ void load_x(const X *__restrict__ x, int64_t j, bool 
 // The block's diagonals are taken D at a time: the D * U 16-byte value loads
 // of a group are issued first, then the x loads, then the FMAs, so a warp
 // keeps D * U * 512 bytes of dia_val in flight.
-template <typename VT, int U, int D, bool VEC, bool PF = false>
+//
+// CK (mhdc_set_checked): every index into the handle's arrays, x and y is
+// compared with the array's extent first; a failed check skips the access
+// (0 is used) and marks the status word.  The operations are otherwise those
+// of the unchecked tile, so an in-bounds product gives the same y.
+template <typename VT, int U, int D, bool VEC, bool PF = false, bool CK = false>
 __device__ __forceinline__ void
 reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restrict__ dia_ptr,
          const int32_t *__restrict__ dia_offset, const VT *__restrict__ dia_val,
          const int32_t *__restrict__ csr_row_ptr, const int32_t *__restrict__ csr_col,
          const VT *__restrict__ csr_val, const typename Tr<VT>::X *__restrict__ x,
-         typename Tr<VT>::Y *__restrict__ y)
+         typename Tr<VT>::Y *__restrict__ y, BoundsCheck ck = BoundsCheck{})
 {
     using Acc = typename Tr<VT>::Acc;
     using X = typename Tr<VT>::X;
@@ -121,7 +127,17 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
     for (int u = 0; u < U; u++) tl[u] = tw + (u * 32 + lane) * V;
 
     // the block's diagonal range, loaded with the remainder bounds below (independent)
-    const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
+    int32_t p0 = 0, p1 = 0;
+    if constexpr (CK) {
+        if (ck_in(ck, ib, ib + 2, ck.n_blocks + 1)) {
+            p0 = dia_ptr[ib];
+            p1 = dia_ptr[ib + 1];
+            if (!ck_in(ck, p0, p1, ck.P)) p0 = p1 = 0;
+        }
+    } else {
+        p0 = dia_ptr[ib];
+        p1 = dia_ptr[ib + 1];
+    }
     if constexpr (VEC && PF) {
         // every diagonal's values of this tile into L2 ahead of their loads:
         // one bulk prefetch per diagonal (lane d takes diagonal p0 + d), the
@@ -152,8 +168,22 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
     // directly.
     {
         const int32_t tend = full ? tw + RW : rows;
+        if constexpr (CK) {
+            if (!ck_in(ck, r0 + tw, r0 + tend + 1, n + 1)) return;
+        }
         const int32_t q0 = csr_row_ptr[r0 + tw], q1 = csr_row_ptr[r0 + tend];
-        if (q0 != q1 && V < 4) {
+        if (q0 != q1 && CK) {
+            // checked: each lane sums its own rows (tl[u] + m) row by row
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int m = 0; m < V; m++) {
+                    const int32_t t = tl[u] + m;
+                    if (t < rows)
+                        rem_row_add_ck(acc[u][m], csr_row_ptr[r0 + t], csr_row_ptr[r0 + t + 1],
+                                       csr_col, csr_val, x, n, ck);
+                }
+        } else if (q0 != q1 && V < 4) {
             // V rows per vector (FP64: 2), U vectors per lane
             constexpr int R = U * V;
             Acc s[R];
@@ -185,7 +215,56 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
                 a[j] = t < rows ? csr_row_ptr[r0 + t] : 0;
                 b[j] = t < rows ? csr_row_ptr[r0 + t + 1] : 0;
             }
-            rem_rows_add<R, 1>(s, a, b, csr_col, csr_val, x);
+            if constexpr (sizeof(VT) == 2) {
+                // BF16: the tile's remainder entries are gathered by the whole
+                // warp, RSG per lane at a time (columns and values coalesced,
+                // then the x gathers), into shared memory as (value, x) FP32
+                // pairs; each lane then runs its rows' FMA chains from there
+                // in column order.  The same operations as rem_rows_add
+                // without its registers for 8 rows of loads per lane.
+                constexpr int RSG = 4;
+                constexpr int CAP = 32 * RSG;
+                __shared__ float2 rst[SPMV_WARPS][CAP];
+                float2 *st = rst[threadIdx.x >> 5];
+                bool lng[R];
+#pragma unroll
+                for (int j = 0; j < R; j++) lng[j] = sizeof(Acc) < sizeof(double) && b[j] - a[j] > REM_LONG;
+                for (int32_t c0 = q0; c0 < q1; c0 += CAP) {
+                    const int32_t c1 = (q1 - c0 < CAP) ? q1 : c0 + CAP;
+                    int32_t cc[RSG];
+                    VT vv[RSG];
+                    X xx[RSG];
+#pragma unroll
+                    for (int m = 0; m < RSG; m++) {
+                        const int32_t e = c0 + lane + 32 * m;
+                        cc[m] = e < c1 ? csr_col[e] : 0;
+                        vv[m] = e < c1 ? csr_val[e] : VT(0);
+                    }
+#pragma unroll
+                    for (int m = 0; m < RSG; m++)
+                        xx[m] = c0 + lane + 32 * m < c1 ? __ldg(x + cc[m]) : X(0);
+#pragma unroll
+                    for (int m = 0; m < RSG; m++)
+                        if (c0 + lane + 32 * m < c1)
+                            st[lane + 32 * m] = make_float2(rem_in(vv[m]), rem_in(xx[m]));
+                    __syncwarp();
+#pragma unroll
+                    for (int j = 0; j < R; j++) {
+                        if (lng[j]) continue;
+                        const int32_t k0 = a[j] > c0 ? a[j] : c0, k1 = b[j] < c1 ? b[j] : c1;
+                        for (int32_t k = k0; k < k1; k++) {
+                            const float2 pv = st[k - c0];
+                            s[j] = rem_fma(pv.x, pv.y, s[j]);
+                        }
+                    }
+                    __syncwarp();
+                }
+#pragma unroll
+                for (int j = 0; j < R; j++)
+                    if (lng[j]) rem_row_add(s[j], a[j], b[j], csr_col, csr_val, x);
+            } else {
+                rem_rows_add<R, 1>(s, a, b, csr_col, csr_val, x);
+            }
 #pragma unroll
             for (int j = 0; j < R; j++) rs[lane + 32 * j] = s[j];
             __syncwarp();
@@ -211,7 +290,8 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
             const VT *vp = dia_val + (int64_t)(p + d) * n_b;
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                if (full || tl[u] < rows) {
+                const int64_t vi = (int64_t)(p + d) * n_b + tl[u];
+                if ((full || tl[u] < rows) && (!CK || ck_in(ck, vi, vi + V, ck.dia_slots))) {
                     if constexpr (VEC) {
                         const uint4 r = ld_stream16(vp + tl[u]);
                         memcpy(v[d][u], &r, 16);
@@ -236,7 +316,13 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
                         // two aligned 16-byte loads and a byte shift per vector
 #pragma unroll
                         for (int u = 0; u < U; u++) {
-                            const X *a = x + (jw - r) + (tl[u] - tw);
+                            const int64_t ja = (jw - r) + (tl[u] - tw);
+                            if (CK && !ck_in(ck, ja, ja + 2 * V, n)) {
+#pragma unroll
+                                for (int m = 0; m < V; m++) xv[d][u][m] = X(0);
+                                continue;
+                            }
+                            const X *a = x + ja;
                             const uint4 lo = __ldg(reinterpret_cast<const uint4 *>(a));
                             const uint4 hi = __ldg(reinterpret_cast<const uint4 *>(a + V));
                             const uint4 q = window16(lo, hi, (int)(r * sizeof(X)));
@@ -247,7 +333,15 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
                 }
                 const bool al = x_al && r == 0;
 #pragma unroll
-                for (int u = 0; u < U; u++) load_x<X, V>(x, jw + (tl[u] - tw), al, xv[d][u]);
+                for (int u = 0; u < U; u++) {
+                    const int64_t j0 = jw + (tl[u] - tw);
+                    if (CK && !ck_in(ck, j0, j0 + V, n)) {
+#pragma unroll
+                        for (int m = 0; m < V; m++) xv[d][u][m] = X(0);
+                        continue;
+                    }
+                    load_x<X, V>(x, j0, al, xv[d][u]);
+                }
             } else {
 #pragma unroll
                 for (int u = 0; u < U; u++)
@@ -274,7 +368,8 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
     for (int u = 0; u < U; u++) {
 #pragma unroll
         for (int m = 0; m < V; m++)
-            if (tl[u] + m < rows) y[r0 + tl[u] + m] = acc[u][m];
+            if (tl[u] + m < rows && (!CK || ck_in(ck, r0 + tl[u] + m, r0 + tl[u] + m + 1, n)))
+                y[r0 + tl[u] + m] = acc[u][m];
     }
 }
 
@@ -286,10 +381,27 @@ k_mhdc_spmv(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
             const int32_t *__restrict__ csr_col, const VT *__restrict__ csr_val,
             const typename Tr<VT>::X *__restrict__ x, typename Tr<VT>::Y *__restrict__ y)
 {
-    const int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5);
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= n_tiles) return;
     reg_tile<VT, U, D, VEC>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_val, csr_row_ptr, csr_col,
                             csr_val, x, y);
+}
+
+// The bounds-checked product of mhdc_set_checked: the default tile shapes
+// (U = 1; D = 2 with 16-byte vectors, D = 4 without), every access checked.
+template <typename VT, bool VEC>
+__global__ void __launch_bounds__(SPMV_THREADS)
+k_mhdc_spmv_ck(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
+               const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
+               const VT *__restrict__ dia_val, const int32_t *__restrict__ csr_row_ptr,
+               const int32_t *__restrict__ csr_col, const VT *__restrict__ csr_val,
+               const typename Tr<VT>::X *__restrict__ x, typename Tr<VT>::Y *__restrict__ y,
+               BoundsCheck ck)
+{
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= n_tiles) return;
+    reg_tile<VT, 1, VEC ? 2 : 4, VEC, false, true>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_val,
+                                                   csr_row_ptr, csr_col, csr_val, x, y, ck);
 }
 
 // ---------------------------------------------------------------------------
@@ -360,26 +472,18 @@ k_split_x(int64_t n, const double *__restrict__ x, float2 *__restrict__ x_dw,
     x_dw[i] = o;
 }
 
+// One warp tile of the emulated product: the rows and tile geometry of
+// reg_tile<double, U, D, true> (RW = 64 U rows), FP32-pair arithmetic.
 template <int U, int D>
-__global__ void __launch_bounds__(SPMV_THREADS, U * D <= 2 ? 5 : 4)
-k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
-               const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
-               const float2 *__restrict__ dia_dw, const int32_t *__restrict__ csr_row_ptr,
-               const int32_t *__restrict__ csr_col, const float2 *__restrict__ csr_dw,
-               const float2 *__restrict__ x_dw, const unsigned long long *__restrict__ flag,
-               unsigned long long epoch, const double *__restrict__ dia_val,
-               const double *__restrict__ csr_val, const double *__restrict__ x,
-               double *__restrict__ y)
+__device__ __forceinline__ void
+dw_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restrict__ dia_ptr,
+        const int32_t *__restrict__ dia_offset, const float2 *__restrict__ dia_dw,
+        const int32_t *__restrict__ csr_row_ptr, const int32_t *__restrict__ csr_col,
+        const float2 *__restrict__ csr_dw, const float2 *__restrict__ x_dw,
+        double *__restrict__ y)
 {
     constexpr int V = 2;  // float2 slots per 16-byte load
     constexpr int RW = 32 * V * U;
-    const int64_t w = (int64_t)blockIdx.x * SPMV_WARPS + (threadIdx.x >> 5);
-    if (w >= n_tiles) return;
-    if (*flag != (epoch << 1)) {  // x outside the window: native FP64 tile
-        reg_tile<double, U, D, true>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_val, csr_row_ptr,
-                                     csr_col, csr_val, x, y);
-        return;
-    }
     const int lane = threadIdx.x & 31;
     const int64_t ib = w / tpb;
     const int32_t tw = (int32_t)(w - ib * tpb) * RW;
@@ -400,19 +504,40 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
     {
         const int32_t tend = full ? tw + RW : rows;
         if (csr_row_ptr[r0 + tw] != csr_row_ptr[r0 + tend]) {
+            // the lane's rows, each in column order; every round loads the
+            // next entry of every row (values, then the gathers of x) before
+            // its steps, so the rows' loads are in flight together
+            constexpr int R = U * V;
+            int32_t a[R], b[R];
 #pragma unroll
             for (int u = 0; u < U; u++)
 #pragma unroll
                 for (int m = 0; m < V; m++) {
                     const int32_t t = tl[u] + m;
-                    if (t < rows) {
-                        const int64_t i = r0 + t;
-                        const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
-                        for (int32_t k = a; k < b; k++)
-                            dw::dw_fma(sh[u][m], sl[u][m], __ldg(csr_dw + k),
-                                   __ldg(x_dw + __ldg(csr_col + k)));
-                    }
+                    a[u * V + m] = t < rows ? csr_row_ptr[r0 + t] : 0;
+                    b[u * V + m] = t < rows ? csr_row_ptr[r0 + t + 1] : 0;
                 }
+            for (;;) {
+                bool more = false;
+#pragma unroll
+                for (int r = 0; r < R; r++) more |= a[r] < b[r];
+                if (!more) break;
+                float2 av[R], xv[R];
+                int32_t c[R];
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    c[r] = a[r] < b[r] ? __ldg(csr_col + a[r]) : 0;
+                    av[r] = a[r] < b[r] ? __ldg(csr_dw + a[r]) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int r = 0; r < R; r++) xv[r] = a[r] < b[r] ? __ldg(x_dw + c[r]) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                    if (a[r] < b[r]) {
+                        dw::dw_fma(sh[r / V][r % V], sl[r / V][r % V], av[r], xv[r]);
+                        a[r]++;
+                    }
+            }
         }
     }
 
@@ -483,6 +608,29 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
         for (int m = 0; m < V; m++)
             if (tl[u] + m < rows) y[r0 + tl[u] + m] = dw::f32_to_f64(sh[u][m]) + dw::f32_to_f64(sl[u][m]);
 }
+
+template <int U, int D>
+__global__ void __launch_bounds__(SPMV_THREADS, U * D <= 2 ? 5 : 4)
+k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
+               const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
+               const float2 *__restrict__ dia_dw, const int32_t *__restrict__ csr_row_ptr,
+               const int32_t *__restrict__ csr_col, const float2 *__restrict__ csr_dw,
+               const float2 *__restrict__ x_dw, const unsigned long long *__restrict__ flag,
+               unsigned long long epoch, const double *__restrict__ dia_val,
+               const double *__restrict__ csr_val, const double *__restrict__ x,
+               double *__restrict__ y)
+{
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= n_tiles) return;
+    if (*flag != (epoch << 1)) {  // x outside the window: native FP64 tile
+        reg_tile<double, U, D, true>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_val, csr_row_ptr,
+                                     csr_col, csr_val, x, y);
+        return;
+    }
+    dw_tile<U, D>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_dw, csr_row_ptr, csr_col, csr_dw, x_dw,
+                  y);
+}
+
 
 // Plain CSR (Fig. 2), one thread per row: s = fma(val[k], x[col_ind[k]], s)
 // over the row, four entries per step.  One FP64 FMA per nonzero and no
@@ -727,13 +875,14 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
     const int rw = RWs[shape];
     int32_t tpb = (int32_t)((A->n_b + rw - 1) / rw);
     int64_t tiles = (int64_t)tpb * A->n_blocks;
-    const int64_t grid = (tiles + SPMV_WARPS - 1) / SPMV_WARPS;
+    const int threads = tiles < 2 * SPMV_WARPS * (int64_t)num_sms() ? 32 : SPMV_THREADS;
+    const int64_t grid = (tiles + threads / 32 - 1) / (threads / 32);
     const unsigned long long epoch = ++A->dw_epoch;
     k_split_x<<<(unsigned)((A->n + 255) / 256), 256, 0, stream>>>(
         A->n, (const double *)d_x, A->x_dw, A->dw_flag, epoch);
     MHDC_LAUNCH_CHECK("k_split_x");
     auto args = [&](auto kern) {
-        kern<<<(unsigned)grid, SPMV_THREADS, 0, stream>>>(
+        kern<<<(unsigned)grid, threads, 0, stream>>>(
             A->n, A->n_b, tpb, tiles, A->dia_ptr, A->dia_offset, A->dia_dw, A->csr_row_ptr,
             A->csr_col, A->csr_dw, A->x_dw, A->dw_flag, epoch, (const double *)A->dia_val,
             (const double *)A->csr_val, (const double *)d_x, (double *)d_y);
@@ -747,13 +896,50 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
     return MHDC_OK;
 }
 
+bool emulation_possible(const mhdc_matrix *A)
+{
+    return A->dw_ok && A->dtype == MHDC_F64 && (A->n_b % 2) == 0;
+}
+
+template <typename VT>
+int launch_checked_typed(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream)
+{
+    using X = typename Tr<VT>::X;
+    using Y = typename Tr<VT>::Y;
+    const bool vec = (A->n_b % Tr<VT>::V) == 0;
+    const int rw = vec ? 32 * Tr<VT>::V : 32;
+    const int32_t tpb = (int32_t)((A->n_b + rw - 1) / rw);
+    const int64_t tiles = (int64_t)tpb * A->n_blocks;
+    const int64_t grid = (tiles + SPMV_WARPS - 1) / SPMV_WARPS;
+    const BoundsCheck ck{A->n_blocks, A->P, A->P * (int64_t)A->n_b, A->nnz_rem, A->status};
+    auto go = [&](auto kern) {
+        kern<<<(unsigned)grid, SPMV_THREADS, 0, stream>>>(
+            A->n, A->n_b, tpb, tiles, A->dia_ptr, A->dia_offset, static_cast<const VT *>(A->dia_val),
+            A->csr_row_ptr, A->csr_col, static_cast<const VT *>(A->csr_val),
+            static_cast<const X *>(d_x), static_cast<Y *>(d_y), ck);
+    };
+    if (vec) go(k_mhdc_spmv_ck<VT, true>);
+    else go(k_mhdc_spmv_ck<VT, false>);
+    MHDC_LAUNCH_CHECK("k_mhdc_spmv_ck");
+    return MHDC_OK;
+}
+
+int launch_checked(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream)
+{
+    switch (A->dtype) {
+    case MHDC_F64: return launch_checked_typed<double>(A, d_x, d_y, stream);
+    case MHDC_F32: return launch_checked_typed<float>(A, d_x, d_y, stream);
+    default: return launch_checked_typed<__nv_bfloat16>(A, d_x, d_y, stream);
+    }
+}
+
 int launch_variant(mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStream_t stream)
 {
     if (id >= FIRST_XW_VARIANT) {
         if (xw_supported(A, d_x)) return launch_spmv_xw(A, id - FIRST_XW_VARIANT, d_x, d_y, stream);
         id = -1;
     } else if (id >= FIRST_DW_VARIANT) {
-        if (A->dw_ok && A->dtype == MHDC_F64 && (A->n_b % 2) == 0) {
+        if (emulation_possible(A)) {
             if (id < FIRST_TMA_DW_VARIANT) return launch_dw(A, id - FIRST_DW_VARIANT, d_x, d_y, stream);
             const unsigned long long epoch = ++A->dw_epoch;
             k_split_x<<<(unsigned)((A->n + 255) / 256), 256, 0, stream>>>(
@@ -770,14 +956,17 @@ int launch_variant(mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStrea
     const Variant v = variant_for(A, id);
     int32_t tpb = (int32_t)((A->n_b + v.rw - 1) / v.rw);
     int64_t tiles = (int64_t)tpb * A->n_blocks;
-    const int64_t grid = (tiles + SPMV_WARPS - 1) / SPMV_WARPS;
+    // a matrix with fewer tiles than two 8-warp CTAs per SM would leave SMs
+    // idle: one-warp CTAs spread its tiles over every SM
+    const int threads = tiles < 2 * SPMV_WARPS * (int64_t)num_sms() ? 32 : SPMV_THREADS;
+    const int64_t grid = (tiles + threads / 32 - 1) / (threads / 32);
     int64_t n = A->n;
     int32_t n_b = A->n_b;
     const void *dv = A->dia_val, *cv = A->csr_val;
     const int32_t *dp = A->dia_ptr, *doff = A->dia_offset, *crp = A->csr_row_ptr, *cc = A->csr_col;
     void *args[] = {&n, &n_b, &tpb, &tiles, (void *)&dp, (void *)&doff, (void *)&dv, (void *)&crp,
                     (void *)&cc, (void *)&cv, (void *)&d_x, &d_y};
-    MHDC_CUDA_TRY(cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(SPMV_THREADS), args, 0, stream));
+    MHDC_CUDA_TRY(cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(threads), args, 0, stream));
     return MHDC_OK;
 }
 
@@ -794,6 +983,7 @@ int spmv_grid_for(const mhdc_matrix *A)
 int launch_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream)
 {
     if (A->n == 0) return MHDC_OK;
+    if (A->checked) return launch_checked(A, d_x, d_y, stream);
     return launch_variant(A, A->variant, d_x, d_y, stream);
 }
 
@@ -810,21 +1000,27 @@ int tune_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream, i
     int best_id = -1;
     float best_t = 0.f;
     const int reps = 20;
-    for (int id = 0; id < MHDC_NUM_VARIANTS; id++) {
+    auto time_id = [&](int id, float *us_out) -> int {
         int rc = MHDC_OK;
         for (int r = 0; r < 3 && rc == MHDC_OK; r++) rc = launch_variant(A, id, d_x, d_y, stream);
         cudaEventRecord(e0, stream);
         for (int r = 0; r < reps && rc == MHDC_OK; r++) rc = launch_variant(A, id, d_x, d_y, stream);
         cudaEventRecord(e1, stream);
+        if (rc != MHDC_OK) return rc;
+        MHDC_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *us_out = ms * 1e3f / reps;
+        return MHDC_OK;
+    };
+    for (int id = 0; id < MHDC_NUM_VARIANTS; id++) {
+        float us = 0.f;
+        const int rc = time_id(id, &us);
         if (rc != MHDC_OK) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             return rc;
         }
-        MHDC_CUDA_TRY(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const float us = ms * 1e3f / reps;
         if (times_us) times_us[id] = us;
         if (best_id < 0 || us < best_t) {
             best_id = id;
