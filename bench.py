@@ -39,6 +39,16 @@ N_B, THETA = 4096, 0.6
 FALLBACK_HBM_GBS = 6800.0
 
 
+# --kernel cases: (workload, n_b, dtype, right-hand sides; 0 = SpMV)
+KERNEL_CASES = {
+    "head-f64": ("stencil27_128", 4096, "f64", 0), "head-f32": ("stencil27_128", 4096, "f32", 0),
+    "head-bf16": ("stencil27_128", 4096, "bf16", 0), "scat-f64": ("scattered_4m", 2048, "f64", 0),
+    "scat-f32": ("scattered_4m", 2048, "f32", 0), "scat-bf16": ("scattered_4m", 2048, "bf16", 0),
+    "spmm4": ("stencil27_128", 4096, "f32", 4), "spmm8": ("stencil27_128", 4096, "f32", 8),
+    "spmm16": ("stencil27_128", 4096, "f32", 16), "batch": ("batch64", 4096, "f64", 0),
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -56,6 +66,10 @@ def parse():
                          "(CSR / DIA / B-DIA / M-HDC over n, plus an n_b sweep) or the "
                          "model-accuracy grid of Sec. 6.4.3; JSON lines to --out")
     ap.add_argument("--out", default=None, help="file for the sweep's JSON lines")
+    ap.add_argument("--kernel", default=None, choices=sorted(KERNEL_CASES),
+                    help="instead of the headline line: launch one product kernel of a bench "
+                         "row (--variant fixes the SpMV variant or SpMM shape) warmup + steps "
+                         "times and print its mean time; for profiling runs")
     ap.add_argument("--sizes", default="1e4,3e4,1e5,3e5,1e6,3e6,1e7,2e7,5e7",
                     help="matrix sizes n of the stencil sweep")
     ap.add_argument("--nb-n", type=float, default=1e7,
@@ -857,6 +871,47 @@ def sweep_model(args, mh, torch, log):
     log(f"clocks: {clk}")
 
 
+def run_kernel_case(args, mh, torch, stream):
+    """One product kernel of a bench row, warmup + steps launches back to back
+    (for ncu captures of that kernel); prints its mean time per launch."""
+    import synth
+    name, n_b, dt, k = KERNEL_CASES[args.kernel]
+    if name == "batch64":
+        mats = synth.batch_matrices(64, 16, 96, seed=3)
+        hs, xs, ys = [], [], []
+        for Am in mats:
+            r_, c_, v_ = (torch.from_numpy(a).cuda() for a in (Am.row_ptr, Am.col, Am.val))
+            hs.append(mh.mhdc_build(Am.n, r_, c_, v_, n_b, THETA, dt))
+            mh.mhdc_set_variant(hs[-1], 5 if args.variant is None else args.variant)
+            xs.append(torch.rand(Am.n, dtype=torch.float64, device="cuda"))
+            ys.append(torch.empty(Am.n, dtype=torch.float64, device="cuda"))
+        B = mh.mhdc_batch_create(hs)
+        XP, YP = mh.pointer_array(xs), mh.pointer_array(ys)
+        fn = lambda: mh.mhdc_batch_spmv(B, XP, YP, stream)  # noqa: E731
+    else:
+        A = synth.config_matrix(name)
+        rp, col, val = (torch.from_numpy(a).cuda() for a in (A.row_ptr, A.col, A.val))
+        H = mh.mhdc_build(A.n, rp, col, val, n_b, THETA, dt)
+        x64 = torch.from_numpy(synth.loguniform_vector(A.n, 2) if name == "scattered_4m"
+                               else synth.uniform_vector(A.n, 12)).cuda()
+        yt = torch.float64 if dt == "f64" else torch.float32
+        if k == 0:
+            xd = x64 if dt == "f64" else x64.float() if dt == "f32" else x64.float().to(torch.bfloat16)
+            yd = torch.empty(A.n, dtype=yt, device="cuda")
+            if args.variant is not None:
+                mh.mhdc_set_variant(H, args.variant)
+            fn = lambda: mh.mhdc_spmv(H, xd, yd, stream)  # noqa: E731
+        else:
+            X = torch.rand((A.n, k), dtype=torch.float32, device="cuda")
+            Y = torch.empty((A.n, k), dtype=torch.float32, device="cuda")
+            if args.variant is not None:
+                mh.mhdc_spmm_set_variant(H, args.variant)
+            fn = lambda: mh.mhdc_spmm(H, X, Y, stream)  # noqa: E731
+    tot, mean = time_launches(fn, args.steps, args.warmup, stream, torch)
+    print(json.dumps({"kernel_case": args.kernel, "variant": args.variant, "steps": args.steps,
+                      "mean_us": round(mean * 1e3, 3)}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -881,6 +936,8 @@ def main():
     stream = torch.cuda.current_stream()
     if args.sweep:
         return (sweep_stencil if args.sweep == "stencil" else sweep_model)(args, mh, torch, log)
+    if args.kernel:
+        return run_kernel_case(args, mh, torch, stream)
 
     A = synth.config_matrix("stencil27_128")
     rp = torch.from_numpy(A.row_ptr).cuda()
