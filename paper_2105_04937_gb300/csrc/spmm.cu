@@ -206,10 +206,10 @@ k_mhdc_spmm(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles, int32_t c0, in
     }
 
     // the block's partial diagonals (Fig. 13, second loop), D at a time.
-    // Addresses: the lane's X row pointers and value offsets are set once;
-    // per diagonal only off * ldx (warp-uniform) is added.  A group whose
-    // diagonals keep the whole tile inside [0, n) (and a full tile) takes a
-    // path without per-row checks.
+    // Addresses: the lane's X row pointers are set once; per diagonal only
+    // off * ldx (warp-uniform) is added.  Tiles at the matrix edge (a row of
+    // the tile outside the matrix, or an X row outside [0, n) for some
+    // diagonal) check every row of every group.
     const X *__restrict__ xr[U];
 #pragma unroll
     for (int u = 0; u < U; u++) xr[u] = xs + (r0 + t[u]) * ldx;
@@ -219,46 +219,27 @@ k_mhdc_spmm(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles, int32_t c0, in
     auto group = [&](auto Dc) {
         constexpr int DD = decltype(Dc)::value;
         int64_t off[DD];
-        bool inside = full;
 #pragma unroll
-        for (int d = 0; d < DD; d++) {
-            off[d] = dia_offset[p + d];
-            inside = inside && jlo + off[d] >= 0 && jhi + off[d] <= n;
-        }
+        for (int d = 0; d < DD; d++) off[d] = dia_offset[p + d];
         Acc v[DD][U];
         X xv[DD][U][QV];
-        if (inside && xvec) {  // warp-uniform
 #pragma unroll
-            for (int d = 0; d < DD; d++) {
-                const VT *vp = dia_val + (int64_t)(p + d) * n_b + tw + g;
+        for (int d = 0; d < DD; d++)
 #pragma unroll
-                for (int u = 0; u < U; u++) v[d][u] = wd(vp[G * u]);
-            }
+            for (int u = 0; u < U; u++)
+                v[d][u] = t[u] < rows ? wd(dia_val[(int64_t)(p + d) * n_b + t[u]]) : Acc(0);
 #pragma unroll
-            for (int d = 0; d < DD; d++) {
-                const int64_t xo = off[d] * ldx;
+        for (int d = 0; d < DD; d++)
 #pragma unroll
-                for (int u = 0; u < U; u++) ld_slice<X, QV>(xr[u] + xo, true, QV, xv[d][u]);
-            }
-        } else {
+            for (int u = 0; u < U; u++) {
+                const int64_t j = r0 + t[u] + off[d];
+                if (t[u] < rows && j >= 0 && j < n) {
+                    ld_slice<X, QV>(xs + j * ldx, xvec, lim, xv[d][u]);
+                } else {
 #pragma unroll
-            for (int d = 0; d < DD; d++)
-#pragma unroll
-                for (int u = 0; u < U; u++)
-                    v[d][u] = t[u] < rows ? wd(dia_val[(int64_t)(p + d) * n_b + t[u]]) : Acc(0);
-#pragma unroll
-            for (int d = 0; d < DD; d++)
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int64_t j = r0 + t[u] + off[d];
-                    if (t[u] < rows && j >= 0 && j < n) {
-                        ld_slice<X, QV>(xs + j * ldx, xvec, lim, xv[d][u]);
-                    } else {
-#pragma unroll
-                        for (int m = 0; m < QV; m++) xv[d][u][m] = X(0);
-                    }
+                    for (int m = 0; m < QV; m++) xv[d][u][m] = X(0);
                 }
-        }
+            }
 #pragma unroll
         for (int d = 0; d < DD; d++)
 #pragma unroll
@@ -267,8 +248,47 @@ k_mhdc_spmm(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles, int32_t c0, in
                 for (int m = 0; m < QV; m++) acc[u][m] = mm_fma(v[d][u], wd(xv[d][u][m]), acc[u][m]);
         p += DD;
     };
-    for (; p + D <= p1;) group(std::integral_constant<int, D>{});
-    for (; p < p1;) group(std::integral_constant<int, 1>{});
+    // the block's offsets ascend, so its first and last diagonal bound the
+    // X rows of the whole tile: a tile inside [0, n) for all of them runs a
+    // loop without per-group checks, the value pointer advanced per group
+    bool all_in = full && xvec && p1 > p0;
+    if (all_in) {
+        const int64_t omin = dia_offset[p0], omax = dia_offset[p1 - 1];
+        all_in = jlo + omin >= 0 && jhi + omax <= n;
+    }
+    if (all_in) {
+        const VT *vp = dia_val + (int64_t)p0 * n_b + tw + g;
+        auto fgroup = [&](auto Dc) {
+            constexpr int DD = decltype(Dc)::value;
+            int64_t xo[DD];
+#pragma unroll
+            for (int d = 0; d < DD; d++) xo[d] = (int64_t)dia_offset[p + d] * ldx;
+            Acc v[DD][U];
+            X xv[DD][U][QV];
+#pragma unroll
+            for (int d = 0; d < DD; d++)
+#pragma unroll
+                for (int u = 0; u < U; u++) v[d][u] = wd(vp[(int64_t)d * n_b + G * u]);
+#pragma unroll
+            for (int d = 0; d < DD; d++)
+#pragma unroll
+                for (int u = 0; u < U; u++) ld_slice<X, QV>(xr[u] + xo[d], true, QV, xv[d][u]);
+#pragma unroll
+            for (int d = 0; d < DD; d++)
+#pragma unroll
+                for (int u = 0; u < U; u++)
+#pragma unroll
+                    for (int m = 0; m < QV; m++)
+                        acc[u][m] = mm_fma(v[d][u], wd(xv[d][u][m]), acc[u][m]);
+            p += DD;
+            vp += (int64_t)DD * n_b;
+        };
+        for (; p + D <= p1;) fgroup(std::integral_constant<int, D>{});
+        for (; p < p1;) fgroup(std::integral_constant<int, 1>{});
+    } else {
+        for (; p + D <= p1;) group(std::integral_constant<int, D>{});
+        for (; p < p1;) group(std::integral_constant<int, 1>{});
+    }
 
     if (lim <= 0) return;
 #pragma unroll

@@ -279,8 +279,9 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
     // the block's partial diagonals (Fig. 13, second loop)
     const int64_t xrow0 = r0 + tw;  // x index of the tile's first row at offset 0
     int32_t p = p0;
-    auto group = [&](auto Dc) {
+    auto group = [&](auto Dc, auto Fc) {
         constexpr int DD = decltype(Dc)::value;
+        constexpr bool FAST = decltype(Fc)::value;
         int64_t off[DD];
 #pragma unroll
         for (int d = 0; d < DD; d++) off[d] = dia_offset[p + d];
@@ -310,9 +311,9 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
             const int64_t jw = xrow0 + off[d];
             const int64_t r = ((jw % V) + V) % V;  // warp-uniform misalignment in elements
             // warp-uniform: the whole tile reads x inside [0, n)
-            if (full && jw >= 0 && jw + RW <= n) {
+            if (FAST || (full && jw >= 0 && jw + RW <= n)) {
                 if constexpr (VEC && V * sizeof(X) == 16 && V > 2) {
-                    if (x_al && r != 0 && jw - r + RW + V <= n) {
+                    if (x_al && r != 0 && (FAST || jw - r + RW + V <= n)) {
                         // two aligned 16-byte loads and a byte shift per vector
 #pragma unroll
                         for (int u = 0; u < U; u++) {
@@ -361,8 +362,18 @@ reg_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restri
                 for (int m = 0; m < V; m++) acc[u][m] += widen(v[d][u][m]) * widen(xv[d][u][m]);
         p += DD;
     };
-    for (; p + D <= p1;) group(std::integral_constant<int, D>{});
-    for (; p < p1;) group(std::integral_constant<int, 1>{});
+    // Offsets ascend inside a block, so when the first and the last diagonal
+    // keep the whole tile's x window (plus one vector for the shifted loads)
+    // inside [0, n), every diagonal does and the groups skip their x checks.
+    bool all_in = !CK && full && p1 > p0;
+    if (all_in) all_in = xrow0 + dia_offset[p0] >= 0 && xrow0 + dia_offset[p1 - 1] + RW + V <= n;
+    if (all_in) {
+        for (; p + D <= p1;) group(std::integral_constant<int, D>{}, std::true_type{});
+        for (; p < p1;) group(std::integral_constant<int, 1>{}, std::true_type{});
+    } else {
+        for (; p + D <= p1;) group(std::integral_constant<int, D>{}, std::false_type{});
+        for (; p < p1;) group(std::integral_constant<int, 1>{}, std::false_type{});
+    }
 
 #pragma unroll
     for (int u = 0; u < U; u++) {
@@ -543,8 +554,9 @@ dw_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restric
 
     const int64_t xrow0 = r0 + tw;
     int32_t p = p0;
-    auto group = [&](auto Dc) {
+    auto group = [&](auto Dc, auto Fc) {
         constexpr int DD = decltype(Dc)::value;
+        constexpr bool FAST = decltype(Fc)::value;
         int64_t off[DD];
 #pragma unroll
         for (int d = 0; d < DD; d++) off[d] = dia_offset[p + d];
@@ -554,7 +566,7 @@ dw_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restric
             const float2 *vp = dia_dw + (int64_t)(p + d) * n_b;
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                if (full || tl[u] < rows) {
+                if (FAST || full || tl[u] < rows) {
                     const uint4 r = ld_stream16(vp + tl[u]);
                     memcpy(v[d][u], &r, 16);
                 } else {
@@ -566,7 +578,7 @@ dw_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restric
 #pragma unroll
         for (int d = 0; d < DD; d++) {
             const int64_t jw = xrow0 + off[d];
-            if (full && jw >= 0 && jw + RW <= n) {
+            if (FAST || (full && jw >= 0 && jw + RW <= n)) {
                 const bool al = (jw & 1) == 0;
 #pragma unroll
                 for (int u = 0; u < U; u++) {
@@ -599,8 +611,16 @@ dw_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restric
                 for (int m = 0; m < V; m++) dw::dw_fma(sh[u][m], sl[u][m], v[d][u][m], xv[d][u][m]);
         p += DD;
     };
-    for (; p + D <= p1;) group(std::integral_constant<int, D>{});
-    for (; p < p1;) group(std::integral_constant<int, 1>{});
+    // ascending offsets: the first and last diagonal bound every x window
+    bool all_in = full && p1 > p0;
+    if (all_in) all_in = xrow0 + dia_offset[p0] >= 0 && xrow0 + dia_offset[p1 - 1] + RW <= n;
+    if (all_in) {
+        for (; p + D <= p1;) group(std::integral_constant<int, D>{}, std::true_type{});
+        for (; p < p1;) group(std::integral_constant<int, 1>{}, std::true_type{});
+    } else {
+        for (; p + D <= p1;) group(std::integral_constant<int, D>{}, std::false_type{});
+        for (; p < p1;) group(std::integral_constant<int, 1>{}, std::false_type{});
+    }
 
 #pragma unroll
     for (int u = 0; u < U; u++)
