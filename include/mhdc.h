@@ -194,9 +194,11 @@ int mhdc_host_wait(mhdc_handle A);
  * dimensions are aligned to the slice (else element by element).
  * Asynchronous on `stream`.
  *
- * mhdc_spmm_set_variant -- SpMM tile shape v (0..MHDC_NUM_SPMM_VARIANTS-1:
- *   (rows per lane, diagonals per load group) = (1,4), (2,2), (2,4), (4,2);
- *   -1: the default, 2).  Every shape gives the same Y.
+ * mhdc_spmm_set_variant -- SpMM tile shape v (0..MHDC_NUM_SPMM_VARIANTS-1;
+ *   -1: the default, 2): 0, 2, 3 give each lane 3, 4, 5 consecutive rows and
+ *   share X rows between the diagonals of a run of consecutive offsets; 1
+ *   gives each lane 2 strided rows and loads 2 diagonals at a time.  Every
+ *   shape gives the same Y.
  * mhdc_spmm_tune -- time every shape on (d_X, d_Y) with k columns (Y is
  *   overwritten), keep the fastest in the handle, write its id to *best and,
  *   if times_us is not NULL, each shape's mean time in microseconds to

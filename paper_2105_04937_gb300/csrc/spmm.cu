@@ -7,13 +7,14 @@
 // rows of X form one contiguous run of G * KC elements per warp load -- every
 // byte a warp fetches through L1 is used (a lane-per-row layout instead reads
 // 16 bytes out of every KC-element row per load and wastes most of each
-// line).  A warp tile is RW = G * U rows of one row block: lane (g, c) owns
-// rows tw + g + G u (u < U) and columns [c * QV, c * QV + QV) of the pass.
-// Per diagonal a lane loads one value per owned row (the L lanes of a row
-// read the same address) and one X slice per row; D diagonals are loaded
-// before their FMAs, so a warp keeps D * U loads of each kind in flight.
-// Each (row, column) accumulates the CSR remainder first, in column order,
-// then the diagonals in ascending order: the operations of the SpMV kernel.
+// line).  A warp tile is RW = G * U rows of one row block; lane (g, c) owns
+// columns [c * QV, c * QV + QV) of the pass and U rows of the tile, either
+// strided (tw + g + G u: per diagonal one value and one X slice per row, D
+// diagonals loaded before their FMAs) or consecutive (tw + g U + u: a run of
+// consecutive offsets shares X rows between its diagonals, see the run
+// tiles below).  Each (row, column) accumulates the CSR remainder first, in
+// column order, then the diagonals in ascending order: the operations of the
+// SpMV kernel, whatever the tile.
 #include <cstring>
 #include <type_traits>
 
@@ -124,6 +125,71 @@ struct Slice {
     static constexpr int G = 32 / L;   // rows of X per warp load
 };
 
+// CSR remainder rows (Fig. 13, first loop) of the lane's rows t[u] into
+// acc: each row in column order from zero; a row longer than REM_LONG under
+// FP32 accumulation is summed per column in FP64 and rounded once, as
+// rem_row_add does for one column.
+template <typename VT, int KC, int U>
+__device__ __forceinline__ void
+mm_remainder(const int32_t (&t)[U], int32_t tw, int32_t tend, int32_t rows, int64_t r0,
+             const int32_t *__restrict__ csr_row_ptr, const int32_t *__restrict__ csr_col,
+             const VT *__restrict__ csr_val, const typename MmTr<VT>::X *__restrict__ xs,
+             int64_t ldx, bool xvec, int lim,
+             typename MmTr<VT>::Acc (&acc)[U][Slice<typename MmTr<VT>::X, KC>::QV])
+{
+    using X = typename MmTr<VT>::X;
+    using Acc = typename MmTr<VT>::Acc;
+    constexpr int QV = Slice<X, KC>::QV;
+    if (csr_row_ptr[r0 + tw] == csr_row_ptr[r0 + tend]) return;  // warp-uniform
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        if (t[u] >= rows) continue;
+        const int64_t i = r0 + t[u];
+        const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
+        if constexpr (sizeof(Acc) < sizeof(double)) {
+            if (b - a > REM_LONG) {
+#pragma unroll
+                for (int m = 0; m < QV; m++) {
+                    if (m >= lim) continue;
+                    double s = 0.0;
+                    for (int32_t q = a; q < b; q++)
+                        s = fma((double)wd(csr_val[q]),
+                                (double)wd(__ldg(xs + (int64_t)csr_col[q] * ldx + m)), s);
+                    acc[u][m] = (Acc)s;
+                }
+                continue;
+            }
+        }
+        for (int32_t q = a; q < b; q++) {
+            const Acc av = wd(csr_val[q]);
+            X xv[QV];
+            ld_slice<X, QV>(xs + (int64_t)csr_col[q] * ldx, xvec, lim, xv);
+#pragma unroll
+            for (int m = 0; m < QV; m++) acc[u][m] = mm_fma(av, wd(xv[m]), acc[u][m]);
+        }
+    }
+}
+
+// Y rows t[u] of the lane's slice from acc.
+template <typename VT, int KC, int U>
+__device__ __forceinline__ void
+mm_store(const int32_t (&t)[U], int32_t rows, int64_t r0, typename MmTr<VT>::Y *__restrict__ ys,
+         int64_t ldy, bool yvec, int lim,
+         const typename MmTr<VT>::Acc (&acc)[U][Slice<typename MmTr<VT>::X, KC>::QV])
+{
+    using Y = typename MmTr<VT>::Y;
+    constexpr int QV = Slice<typename MmTr<VT>::X, KC>::QV;
+    if (lim <= 0) return;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        if (t[u] >= rows) continue;
+        Y out[QV];
+#pragma unroll
+        for (int m = 0; m < QV; m++) out[m] = (Y)acc[u][m];
+        st_slice<Y, QV>(ys + (r0 + t[u]) * ldy, yvec, lim, out);
+    }
+}
+
 template <typename VT, int KC, int U, int D>
 __global__ void __launch_bounds__(MM_THREADS, mm_min_blocks(U, D))
 k_mhdc_spmm(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles, int32_t c0, int32_t k,
@@ -169,41 +235,8 @@ k_mhdc_spmm(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles, int32_t c0, in
 
     const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
 
-    // CSR remainder rows (Fig. 13, first loop)
-    {
-        const int32_t tend = (tw + RW < rows) ? tw + RW : rows;
-        if (csr_row_ptr[r0 + tw] != csr_row_ptr[r0 + tend]) {
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                if (t[u] >= rows) continue;
-                const int64_t i = r0 + t[u];
-                const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
-                if constexpr (sizeof(Acc) < sizeof(double)) {
-                    if (b - a > REM_LONG) {
-                        // a long row: each column summed in FP64 from zero and
-                        // rounded once, as rem_row_add does for one column
-#pragma unroll
-                        for (int m = 0; m < QV; m++) {
-                            if (m >= lim) continue;
-                            double s = 0.0;
-                            for (int32_t q = a; q < b; q++)
-                                s = fma((double)wd(csr_val[q]),
-                                        (double)wd(__ldg(xs + (int64_t)csr_col[q] * ldx + m)), s);
-                            acc[u][m] = (Acc)s;
-                        }
-                        continue;
-                    }
-                }
-                for (int32_t q = a; q < b; q++) {
-                    const Acc av = wd(csr_val[q]);
-                    X xv[QV];
-                    ld_slice<X, QV>(xs + (int64_t)csr_col[q] * ldx, xvec, lim, xv);
-#pragma unroll
-                    for (int m = 0; m < QV; m++) acc[u][m] = mm_fma(av, wd(xv[m]), acc[u][m]);
-                }
-            }
-        }
-    }
+    mm_remainder<VT, KC, U>(t, tw, (tw + RW < rows) ? tw + RW : rows, rows, r0, csr_row_ptr, csr_col,
+                            csr_val, xs, ldx, xvec, lim, acc);
 
     // the block's partial diagonals (Fig. 13, second loop), D at a time.
     // Addresses: the lane's X row pointers are set once; per diagonal only
@@ -290,20 +323,143 @@ k_mhdc_spmm(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles, int32_t c0, in
         for (; p < p1;) group(std::integral_constant<int, 1>{});
     }
 
-    if (lim <= 0) return;
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-        if (t[u] >= rows) continue;
-        Y out[QV];
-#pragma unroll
-        for (int m = 0; m < QV; m++) out[m] = (Y)acc[u][m];
-        st_slice<Y, QV>(Ym + (r0 + t[u]) * ldy + c0 + cq, yvec, lim, out);
-    }
+    mm_store<VT, KC, U>(t, rows, r0, Ym + c0 + cq, ldy, yvec, lim, acc);
 }
 
-// Tile shapes (U rows per lane, D diagonals per load group); index = the
-// handle's SpMM variant.  Passes of one or two columns use shape 2 only.
-constexpr int SPMM_SHAPES[MHDC_NUM_SPMM_VARIANTS][2] = {{1, 4}, {2, 2}, {2, 4}, {4, 2}};
+// Run tiles: lane (g, c) owns the U consecutive rows tw + g U + u (u < U).
+// For a run of MM consecutive offsets off, off + 1, ..., the lane's rows need
+// X rows off .. off + U + MM - 2 past its first row, so U + MM - 1 slice loads
+// serve MM U (row, diagonal) pairs -- a stencil's runs of three offsets
+// (off - 1, off, off + 1) load each X row once instead of three times.  Runs
+// are found from dia_offset as the tile walks its diagonals (at most three
+// a run).  Every accumulator still adds its diagonals in ascending order:
+// the same Y as the other shapes.
+// Resident CTAs per SM: four (64 registers) where the run's values, X rows
+// and accumulators fit without spilling (FP32 up to U = 4, FP64 up to U = 3),
+// else three (80 registers; BF16 slices widen to eight FP32 values).
+constexpr int mm_run_min_blocks(int U, int vt_bytes)
+{
+    return (vt_bytes == 4 && U <= 4) || (vt_bytes == 8 && U <= 3) ? 4 : 3;
+}
+
+template <typename VT, int KC, int U>
+__global__ void __launch_bounds__(MM_THREADS, mm_run_min_blocks(U, (int)sizeof(VT)))
+k_mhdc_spmm_run(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles, int32_t c0, int32_t k,
+                const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
+                const VT *__restrict__ dia_val, const int32_t *__restrict__ csr_row_ptr,
+                const int32_t *__restrict__ csr_col, const VT *__restrict__ csr_val,
+                const typename MmTr<VT>::X *__restrict__ Xm, int64_t ldx,
+                typename MmTr<VT>::Y *__restrict__ Ym, int64_t ldy)
+{
+    using X = typename MmTr<VT>::X;
+    using Y = typename MmTr<VT>::Y;
+    using Acc = typename MmTr<VT>::Acc;
+    constexpr int QV = Slice<X, KC>::QV, L = Slice<X, KC>::L, G = Slice<X, KC>::G;
+    constexpr int RW = G * U;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * MM_WARPS + (threadIdx.x >> 5);
+    if (w >= n_tiles) return;
+    const int64_t ib = w / tpb;
+    const int32_t tw = (int32_t)(w - ib * tpb) * RW;
+    const int64_t r0 = ib * (int64_t)n_b;
+    const int32_t rows = (int32_t)((n - r0 < n_b) ? (n - r0) : n_b);
+    if (tw >= rows) return;  // warp-uniform
+    const int g = lane / L;
+    const int cq = (lane % L) * QV;
+    const int kc = (k - c0 < KC) ? k - c0 : KC;
+    const int lim = kc - cq;
+    constexpr int BX = QV * (int)sizeof(X);
+    constexpr int BY = (QV * (int)sizeof(Y) >= 16) ? 16 : QV * (int)sizeof(Y);
+    const bool xvec = kc == KC && (reinterpret_cast<uintptr_t>(Xm + c0) % BX) == 0 &&
+                      ((ldx * (int64_t)sizeof(X)) % BX) == 0;
+    const bool yvec = kc == KC && (reinterpret_cast<uintptr_t>(Ym + c0) % BY) == 0 &&
+                      ((ldy * (int64_t)sizeof(Y)) % BY) == 0;
+    const X *__restrict__ xs = Xm + c0 + cq;
+
+    int32_t t[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) t[u] = tw + g * U + u;
+    Acc acc[U][QV];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+#pragma unroll
+        for (int m = 0; m < QV; m++) acc[u][m] = Acc(0);
+    const int32_t p0 = dia_ptr[ib], p1 = dia_ptr[ib + 1];
+    mm_remainder<VT, KC, U>(t, tw, (tw + RW < rows) ? tw + RW : rows, rows, r0, csr_row_ptr, csr_col,
+                            csr_val, xs, ldx, xvec, lim, acc);
+
+    const bool full = tw + RW <= rows;
+    const int64_t jlo = r0 + tw, jhi = r0 + tw + RW;  // the tile's rows, [jlo, jhi)
+    int32_t p = p0;
+    // ascending offsets: the first and last diagonal bound the tile's X rows
+    bool all_in = full && xvec && p1 > p0;
+    if (all_in) {
+        const int64_t omin = dia_offset[p0], omax = dia_offset[p1 - 1];
+        all_in = jlo + omin >= 0 && jhi + omax <= n;
+    }
+    if (all_in) {
+        const X *xb = xs + (r0 + tw + g * U) * ldx;  // the lane's first row at offset 0
+        const VT *vb = dia_val + tw + g * U;
+        // the lane's U values of a diagonal in one load when they are aligned
+        const bool vvec = (U & (U - 1)) == 0 && (n_b % U) == 0;
+        auto run = [&](auto Mc, int32_t off) {
+            constexpr int MM = decltype(Mc)::value;
+            VT v[MM][U];
+            X xv[U + MM - 1][QV];
+            const VT *vp = vb + (int64_t)p * n_b;
+#pragma unroll
+            for (int d = 0; d < MM; d++) ld_slice<VT, U>(vp + (int64_t)d * n_b, vvec, U, v[d]);
+            const X *xp = xb + (int64_t)off * ldx;
+#pragma unroll
+            for (int j = 0; j < U + MM - 1; j++)
+                ld_slice<X, QV>(xp + (int64_t)j * ldx, true, QV, xv[j]);
+#pragma unroll
+            for (int d = 0; d < MM; d++)
+#pragma unroll
+                for (int u = 0; u < U; u++)
+#pragma unroll
+                    for (int m = 0; m < QV; m++)
+                        acc[u][m] = mm_fma(wd(v[d][u]), wd(xv[u + d][m]), acc[u][m]);
+            p += MM;
+        };
+        while (p < p1) {
+            const int32_t o0 = dia_offset[p];
+            int m = 1;
+            if (p + 1 < p1 && dia_offset[p + 1] == o0 + 1) {
+                m = 2;
+                if (p + 2 < p1 && dia_offset[p + 2] == o0 + 2) m = 3;
+            }
+            if (m == 3) run(std::integral_constant<int, 3>{}, o0);
+            else if (m == 2) run(std::integral_constant<int, 2>{}, o0);
+            else run(std::integral_constant<int, 1>{}, o0);
+        }
+    } else {
+        // edge tiles: one diagonal at a time, every row checked
+        for (; p < p1; p++) {
+            const int64_t off = dia_offset[p];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const Acc v = t[u] < rows ? wd(dia_val[(int64_t)p * n_b + t[u]]) : Acc(0);
+                const int64_t j = r0 + t[u] + off;
+                X xv[QV];
+                if (t[u] < rows && j >= 0 && j < n) {
+                    ld_slice<X, QV>(xs + j * ldx, xvec, lim, xv);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < QV; m++) xv[m] = X(0);
+                }
+#pragma unroll
+                for (int m = 0; m < QV; m++) acc[u][m] = mm_fma(v, wd(xv[m]), acc[u][m]);
+            }
+        }
+    }
+    mm_store<VT, KC, U>(t, rows, r0, Ym + c0 + cq, ldy, yvec, lim, acc);
+}
+
+// Tile shapes; index = the handle's SpMM variant: 0, 2, 3 run tiles with
+// U = 3, 4, 5 rows per lane, 1 the strided tile (U, D) = (2, 2), which keeps
+// two diagonals' loads in flight where a matrix has no runs of offsets.
+// Passes of one or two columns use the strided tile (2, 4) only.
 constexpr int SPMM_DEFAULT = 2;
 
 template <typename VT, int KC, int U, int D>
@@ -324,6 +480,24 @@ int spmm_pass(const mhdc_matrix *A, int32_t c0, int32_t k, const void *X, int64_
     return MHDC_OK;
 }
 
+template <typename VT, int KC, int U>
+int spmm_run_pass(const mhdc_matrix *A, int32_t c0, int32_t k, const void *X, int64_t ldx, void *Y,
+                  int64_t ldy, cudaStream_t st)
+{
+    using XT = typename MmTr<VT>::X;
+    constexpr int RW = Slice<XT, KC>::G * U;
+    const int32_t tpb = (int32_t)((A->n_b + RW - 1) / RW);
+    const int64_t tiles = (int64_t)tpb * A->n_blocks;
+    const int64_t grid = (tiles + MM_WARPS - 1) / MM_WARPS;
+    k_mhdc_spmm_run<VT, KC, U><<<(unsigned)grid, MM_THREADS, 0, st>>>(
+        A->n, A->n_b, tpb, tiles, c0, k, A->dia_ptr, A->dia_offset,
+        static_cast<const VT *>(A->dia_val), A->csr_row_ptr, A->csr_col,
+        static_cast<const VT *>(A->csr_val), static_cast<const XT *>(X), ldx,
+        static_cast<typename MmTr<VT>::Y *>(Y), ldy);
+    MHDC_LAUNCH_CHECK("k_mhdc_spmm_run");
+    return MHDC_OK;
+}
+
 template <typename VT, int KC>
 int spmm_shape(int v, const mhdc_matrix *A, int32_t c0, int32_t k, const void *X, int64_t ldx,
                void *Y, int64_t ldy, cudaStream_t st)
@@ -332,10 +506,10 @@ int spmm_shape(int v, const mhdc_matrix *A, int32_t c0, int32_t k, const void *X
         return spmm_pass<VT, KC, 2, 4>(A, c0, k, X, ldx, Y, ldy, st);
     } else {
         switch (v) {
-        case 0: return spmm_pass<VT, KC, 1, 4>(A, c0, k, X, ldx, Y, ldy, st);
+        case 0: return spmm_run_pass<VT, KC, 3>(A, c0, k, X, ldx, Y, ldy, st);
         case 1: return spmm_pass<VT, KC, 2, 2>(A, c0, k, X, ldx, Y, ldy, st);
-        case 3: return spmm_pass<VT, KC, 4, 2>(A, c0, k, X, ldx, Y, ldy, st);
-        default: return spmm_pass<VT, KC, 2, 4>(A, c0, k, X, ldx, Y, ldy, st);
+        case 3: return spmm_run_pass<VT, KC, 5>(A, c0, k, X, ldx, Y, ldy, st);
+        default: return spmm_run_pass<VT, KC, 4>(A, c0, k, X, ldx, Y, ldy, st);
         }
     }
 }

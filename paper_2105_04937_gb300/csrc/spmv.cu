@@ -471,16 +471,47 @@ __device__ __forceinline__ bool split_dw(double xd, float2 &o)
     return true;
 }
 
-__global__ void __launch_bounds__(256)
+// Two elements a thread (one 16-byte load of x where x is 16-byte aligned,
+// one 16-byte store into x_dw).  The product launched after it may start its
+// CTAs at once (griddepcontrol.launch_dependents); they wait for this grid's
+// completion and memory before reading x_dw or the flag.
+constexpr int SPLIT_THREADS = 256;
+
+__global__ void __launch_bounds__(SPLIT_THREADS)
 k_split_x(int64_t n, const double *__restrict__ x, float2 *__restrict__ x_dw,
           unsigned long long *__restrict__ flag, unsigned long long epoch)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    asm volatile("griddepcontrol.launch_dependents;");
+    // launched as a programmatic dependent of the stream's previous kernel:
+    // x (possibly that kernel's output) and x_dw (read by the previous
+    // product of this handle) are free after this wait
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int64_t i = 2 * ((int64_t)blockIdx.x * SPLIT_THREADS + threadIdx.x);
     if (i == 0) atomicMax(flag, epoch << 1);
     if (i >= n) return;
-    float2 o;
-    if (!split_dw(__ldg(x + i), o)) atomicMax(flag, (epoch << 1) | 1ull);
-    x_dw[i] = o;
+    const bool two = i + 1 < n;
+    double a, b = 0.0;
+    if (two && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(x + i));
+        a = v.x;
+        b = v.y;
+    } else {
+        a = __ldg(x + i);
+        if (two) b = __ldg(x + i + 1);
+    }
+    float2 o0, o1;
+    bool ok = split_dw(a, o0);
+    if (two) ok = split_dw(b, o1) && ok;
+    if (!ok) atomicMax(flag, (epoch << 1) | 1ull);
+    if (two)  // x_dw is a device allocation: x_dw + i (i even) is 16-byte aligned
+        *reinterpret_cast<float4 *>(x_dw + i) = make_float4(o0.x, o0.y, o1.x, o1.y);
+    else
+        x_dw[i] = o0;
+}
+
+inline unsigned split_grid(int64_t n)
+{
+    return (unsigned)(((n + 1) / 2 + SPLIT_THREADS - 1) / SPLIT_THREADS);
 }
 
 // One warp tile of the emulated product: the rows and tile geometry of
@@ -642,6 +673,10 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
 {
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= n_tiles) return;
+    asm volatile("griddepcontrol.launch_dependents;");
+    // launched as a programmatic dependent of k_split_x: its x_dw and flag
+    // are complete and visible after this wait (a no-op for a plain launch)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (*flag != (epoch << 1)) {  // x outside the window: native FP64 tile
         reg_tile<double, U, D, true>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_val, csr_row_ptr,
                                      csr_col, csr_val, x, y);
@@ -898,20 +933,46 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
     const int threads = tiles < 2 * SPMV_WARPS * (int64_t)num_sms() ? 32 : SPMV_THREADS;
     const int64_t grid = (tiles + threads / 32 - 1) / (threads / 32);
     const unsigned long long epoch = ++A->dw_epoch;
-    k_split_x<<<(unsigned)((A->n + 255) / 256), 256, 0, stream>>>(
-        A->n, (const double *)d_x, A->x_dw, A->dw_flag, epoch);
-    MHDC_LAUNCH_CHECK("k_split_x");
-    auto args = [&](auto kern) {
-        kern<<<(unsigned)grid, threads, 0, stream>>>(
-            A->n, A->n_b, tpb, tiles, A->dia_ptr, A->dia_offset, A->dia_dw, A->csr_row_ptr,
-            A->csr_col, A->csr_dw, A->x_dw, A->dw_flag, epoch, (const double *)A->dia_val,
-            (const double *)A->csr_val, (const double *)d_x, (double *)d_y);
-    };
-    switch (shape) {
-    case 0: args(k_mhdc_spmv_dw<1, 2>); break;
-    case 1: args(k_mhdc_spmv_dw<2, 2>); break;
-    default: args(k_mhdc_spmv_dw<1, 4>); break;
+    // programmatic dependent launches: each kernel's CTAs are scheduled while
+    // the one before drains and wait in-kernel for its completion
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    {
+        cudaLaunchConfig_t sc = {};
+        sc.gridDim = dim3(split_grid(A->n));
+        sc.blockDim = dim3(SPLIT_THREADS);
+        sc.stream = stream;
+        sc.attrs = attr;
+        sc.numAttrs = 1;
+        MHDC_CUDA_TRY(cudaLaunchKernelEx(&sc, k_split_x, A->n, (const double *)d_x, A->x_dw,
+                                         A->dw_flag, epoch));
     }
+    MHDC_LAUNCH_CHECK("k_split_x");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    auto args = [&](auto kern) -> int {
+        MHDC_CUDA_TRY(cudaLaunchKernelEx(
+            &cfg, kern, A->n, A->n_b, tpb, tiles, (const int32_t *)A->dia_ptr,
+            (const int32_t *)A->dia_offset, (const float2 *)A->dia_dw,
+            (const int32_t *)A->csr_row_ptr, (const int32_t *)A->csr_col,
+            (const float2 *)A->csr_dw, (const float2 *)A->x_dw,
+            (const unsigned long long *)A->dw_flag, epoch, (const double *)A->dia_val,
+            (const double *)A->csr_val, (const double *)d_x, (double *)d_y));
+        return MHDC_OK;
+    };
+    int rc;
+    switch (shape) {
+    case 0: rc = args(k_mhdc_spmv_dw<1, 2>); break;
+    case 1: rc = args(k_mhdc_spmv_dw<2, 2>); break;
+    default: rc = args(k_mhdc_spmv_dw<1, 4>); break;
+    }
+    if (rc != MHDC_OK) return rc;
     MHDC_LAUNCH_CHECK("k_mhdc_spmv_dw");
     return MHDC_OK;
 }
@@ -962,7 +1023,7 @@ int launch_variant(mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStrea
         if (emulation_possible(A)) {
             if (id < FIRST_TMA_DW_VARIANT) return launch_dw(A, id - FIRST_DW_VARIANT, d_x, d_y, stream);
             const unsigned long long epoch = ++A->dw_epoch;
-            k_split_x<<<(unsigned)((A->n + 255) / 256), 256, 0, stream>>>(
+            k_split_x<<<split_grid(A->n), SPLIT_THREADS, 0, stream>>>(
                 A->n, (const double *)d_x, A->x_dw, A->dw_flag, epoch);
             MHDC_LAUNCH_CHECK("k_split_x");
             return launch_spmv_tma_dw(A, id - FIRST_TMA_DW_VARIANT, d_x, d_y, epoch, stream);
