@@ -149,7 +149,11 @@ int mhdc_build_dia(int64_t n, int32_t nd, const int32_t *d_offset, const double 
  *
  *   d_x   n values of the handle's x dtype (device)
  *   d_y   n values of the handle's y dtype (device); must not overlap d_x
- * Asynchronous on `stream`.
+ * Asynchronous on `stream`; may be captured in a CUDA graph (a replay
+ * computes what a direct call computes, for every variant).  Products on one
+ * stream may start their launches while the previous kernel drains, but each
+ * reads its x only after the stream's earlier work has completed (y of one
+ * call may be x of the next).
  */
 int mhdc_spmv(mhdc_handle A, const void *d_x, void *d_y, void *stream);
 
@@ -275,9 +279,11 @@ int mhdc_stats(mhdc_handle A, double *alpha, double *beta, int64_t *P, int64_t *
  * (5.2 k + 18) 2^-48 sum_j |a_ij||x_j| for a row of k terms, under 9.6e-13 *
  * sum_j |a_ij||x_j| (inside the FP64 tolerance 1e-12), as long as every
  * nonzero |a_ij| and |x_j| lies in [2^-45, 2^60] and a row has at most 48
- * terms; the handle checks its values at build and each product checks x on
- * the device, and outside that window the product runs the native FP64 path
- * (variant -1's arithmetic) instead.
+ * terms.  The handle checks its values and row lengths at build (outside the
+ * window every emulated variant runs variant -1); each product splits x on
+ * the device, and a row that reads an x outside the window (or not finite) is
+ * computed with the native FP64 arithmetic instead -- the bits variant -1
+ * gives for that row.
  * Variants 16-19 stage both operands in shared memory with TMA bulk copies:
  * the values as in 6-9 and, per run of nearby diagonals of a block, one
  * window of x that every diagonal of the run reads (the 27 diagonals of a
@@ -330,7 +336,13 @@ int mhdc_set_checked(mhdc_handle A, int32_t on);
  *
  * mhdc_batch_create  -- batch of m >= 1 handles of one dtype (host array
  *                       `mats`); the handles must outlive the batch, which
- *                       only references them.  Synchronous.
+ *                       only references them.  An FP64 handle whose variant
+ *                       is emulated (10-15, set before this call) runs the
+ *                       emulated arithmetic in the batch (the tile of variant
+ *                       10: the bits of its own product with variant 10);
+ *                       each launch first splits those x in one kernel, so a
+ *                       handle's own products must not overlap a launch of a
+ *                       batch holding it.  Synchronous.
  * mhdc_batch_spmv    -- one launch on `stream`: d_xs and d_ys are DEVICE arrays
  *                       of m device pointers (x_i: n_i values of the x dtype,
  *                       y_i: n_i values of the y dtype).  Launches of one batch

@@ -1009,7 +1009,6 @@ void free_matrix(mhdc_matrix *A)
     dfree(A->dia_dw);
     dfree(A->csr_dw);
     dfree(A->x_dw);
-    dfree(A->dw_flag);
     delete A;
 }
 
@@ -1058,9 +1057,7 @@ static void free_dw(mhdc_matrix *A)
     dfree(A->dia_dw);
     dfree(A->csr_dw);
     dfree(A->x_dw);
-    dfree(A->dw_flag);
     A->dia_dw = A->csr_dw = A->x_dw = nullptr;
-    A->dw_flag = nullptr;
 }
 
 // The FP32-pair arrays of the emulated FP64 variants.  On any failure they
@@ -1072,8 +1069,6 @@ static int prepare_dw_arrays(mhdc_matrix *A, cudaStream_t st)
     MHDC_CUDA_TRY(dmalloc((void **)&A->dia_dw, sizeof(float2) * (size_t)(nd ? nd : 1)));
     MHDC_CUDA_TRY(dmalloc((void **)&A->csr_dw, sizeof(float2) * (size_t)(A->nnz_rem ? A->nnz_rem : 1)));
     MHDC_CUDA_TRY(dmalloc((void **)&A->x_dw, sizeof(float2) * (size_t)A->n));
-    MHDC_CUDA_TRY(dmalloc((void **)&A->dw_flag, sizeof(unsigned long long)));
-    MHDC_CUDA_TRY(cudaMemsetAsync(A->dw_flag, 0, sizeof(unsigned long long), st));
     Buf w;
     RC(dalloc(w, 2 * sizeof(int), st));
     MHDC_CUDA_TRY(cudaMemsetAsync(w.p, 0, 2 * sizeof(int), st));

@@ -42,8 +42,6 @@ struct mhdc_matrix {
     float2 *dia_dw = nullptr;        // [P * n_b]
     float2 *csr_dw = nullptr;        // [nnz_rem]
     float2 *x_dw = nullptr;          // [n]: x split by each emulated product
-    unsigned long long *dw_flag = nullptr;  // (epoch << 1) | (x outside the window)
-    unsigned long long dw_epoch = 0;
     bool dw_ok = false;              // values inside the window, <= DW_MAX_TERMS terms per row
     bool dw_prepared = false;        // the FP32-pair arrays above exist (made on first use)
 };
@@ -53,11 +51,17 @@ struct BatchMat {
     int64_t n;
     int64_t tile0;      // first warp tile of this matrix in the batch's tile list
     int32_t n_b, tpb;   // rows per block, warp tiles per block
-    int32_t vec, pad;   // 16-byte value loads possible (n_b % V == 0)
+    int32_t vec;        // 16-byte value loads possible (n_b % V == 0)
+    int32_t emu;        // emulated FP64 (the handle's variant was 10-15 at creation)
     const int32_t *dia_ptr, *dia_offset;
     const void *dia_val;
     const int32_t *csr_row_ptr, *csr_col;
     const void *csr_val;
+    // emulated matrices only: the handle's FP32-pair arrays, and the first
+    // element of this x in the batched split's index space
+    int64_t s0;
+    const float2 *dia_dw, *csr_dw;
+    float2 *x_dw;
 };
 
 // A batch of handles (same dtype) for mhdc_batch_spmv; it does not own them.
@@ -68,6 +72,7 @@ struct mhdc_batch {
     unsigned long long *d_ctr = nullptr;  // [next tile, finished CTAs]
     int64_t total_tiles = 0;
     int64_t total_nnz = 0;
+    int64_t split_total = 0;              // x elements split per launch (emulated matrices)
     int grid = 0;
     cudaStream_t cap_stream = nullptr;    // stream the graph is captured on
     cudaGraphExec_t graph = nullptr;
@@ -144,8 +149,7 @@ bool xw_supported(const mhdc_matrix *A, const void *d_x);
 int launch_spmv_xw(const mhdc_matrix *A, int shape, const void *d_x, void *d_y,
                    cudaStream_t stream);
 int launch_spmv_tma_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y,
-                       unsigned long long epoch, cudaStream_t stream);
-int launch_split_x(mhdc_matrix *A, const void *d_x, unsigned long long epoch, cudaStream_t stream);
+                       cudaStream_t stream);
 // Emulated FP64 (FP32 pairs): nonzero |a|, |x| must lie in [2^DW_EMIN, 2^DW_EMAX]
 // and a row may have at most DW_MAX_TERMS terms (error bound, see spmv.cu).
 constexpr int DW_EMIN = -45;
@@ -154,6 +158,11 @@ constexpr int DW_MAX_TERMS = 48;
 int prepare_dw(mhdc_matrix *A, cudaStream_t st);
 // prepare_dw once per handle (the emulated variants and the tuner call it).
 int ensure_dw(mhdc_matrix *A, cudaStream_t st);
+// an FP64 handle whose values passed the window check, n_b even
+inline bool emulation_possible(const mhdc_matrix *A)
+{
+    return A->dw_ok && A->dtype == MHDC_F64 && (A->n_b % 2) == 0;
+}
 int tune_spmv(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream, int32_t *best,
               float *times_us);
 
@@ -265,6 +274,31 @@ __device__ __forceinline__ void rem_rows_add(Acc (&s)[R], int32_t (&a)[R], const
 #pragma unroll
         for (int r = 0; r < R; r++) a[r] = b[r] - a[r] > E ? a[r] + E : b[r];
     }
+}
+
+// Row i (= r0 + t, block ib) of the native FP64 product, one thread: the
+// remainder from zero in column order, then the block's diagonals in
+// ascending order (a zero where i + off leaves [0, n)), each term one FMA --
+// the operations of every native FP64 tile, so the same bits.  The emulated
+// tiles recompute with it the rows whose FP32-pair sum came out NaN: the rows
+// that read an x outside the emulation window (marked NaN by the split).
+__device__ __forceinline__ double native_row(int64_t i, int32_t t, int64_t ib, int64_t n,
+                                             int32_t n_b, const int32_t *__restrict__ dia_ptr,
+                                             const int32_t *__restrict__ dia_offset,
+                                             const double *__restrict__ dia_val,
+                                             const int32_t *__restrict__ csr_row_ptr,
+                                             const int32_t *__restrict__ csr_col,
+                                             const double *__restrict__ csr_val,
+                                             const double *__restrict__ x)
+{
+    double s = 0.0;
+    for (int32_t q = csr_row_ptr[i]; q < csr_row_ptr[i + 1]; q++)
+        s = fma(csr_val[q], x[csr_col[q]], s);
+    for (int32_t p = dia_ptr[ib]; p < dia_ptr[ib + 1]; p++) {
+        const int64_t j = i + dia_offset[p];
+        s = fma(dia_val[(int64_t)p * n_b + t], (j >= 0 && j < n) ? x[j] : 0.0, s);
+    }
+    return s;
 }
 
 // Bounds-checked products (mhdc_set_checked): the extents of a handle's

@@ -431,12 +431,15 @@ k_mhdc_spmv_ck(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
 // [2^-45, 2^60] and k <= 48: at most (5.2 k + 18) * 2^-48 * sum_j |a_ij x_j|
 // including the final rounding to FP64, i.e. below 9.6e-13 (the derivation
 // is in dw_arith.cuh).
-// Outside the window the same launch runs the native FP64 tile instead.
+// A row that reads an x outside the window comes out NaN (the split marks
+// such an x) and is recomputed with native FP64 arithmetic (native_row).
 // ---------------------------------------------------------------------------
 // x_dw[i] = FP32 pair of x[i] (integer operations only): hi = x rounded to 24
 // significant bits (half-up on the magnitude), lo = x - hi (exact, at most 29
 // bits) rounded to FP32.  Any nonzero |x| outside [2^DW_EMIN, 2^DW_EMAX] or
-// non-finite raises the epoch's flag so that the product falls back to FP64.
+// non-finite becomes the pair (NaN, 0): every emulated sum that uses it is
+// NaN (in-window terms cannot overflow FP32, so nothing else is), and the
+// product recomputes exactly those rows natively.
 // RN(d) for |d| < 2^29 on the FP32 pipe: d = dh 2^15 + dl with dl in
 // [0, 2^15) and |dh| < 2^14, each half exact in FP32 by the magic-number
 // construction (1.5 * 2^23 + dh, 2^23 + dl), and one FMA rounds the exact sum
@@ -452,19 +455,26 @@ __device__ __forceinline__ float i29_to_float_rn(int32_t d)
 
 __device__ __forceinline__ bool split_dw(double xd, float2 &o)
 {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(xd);
-    const unsigned long long sign = u & 0x8000000000000000ull;
-    const unsigned long long mag = u & 0x7FFFFFFFFFFFFFFFull;
+    // the two 32-bit halves of x: sign, 11 exponent bits and the top 20
+    // fraction bits in hw; the low 32 fraction bits in lw
+    const uint32_t hw = (uint32_t)__double2hiint(xd), lw = (uint32_t)__double2loint(xd);
+    const uint32_t sign = hw & 0x80000000u;
+    const uint32_t mh = hw & 0x7FFFFFFFu;
     o = make_float2(0.f, 0.f);
-    if (mag == 0) return true;
-    const int E = (int)(mag >> 52) - 1023;
-    if (E < DW_EMIN || E >= DW_EMAX) return false;  // also inf / nan (E = 1024) and subnormals
-    const unsigned long long magr = (mag + (1ull << 28)) & ~((1ull << 29) - 1);
-    const int Er = (int)(magr >> 52) - 1023;
-    const uint32_t hb = (uint32_t)(sign >> 32) | ((uint32_t)(Er + 127) << 23) |
-                        (uint32_t)((magr >> 29) & 0x7FFFFFu);
-    const int32_t d = (int32_t)(long long)(mag - magr);  // x - hi in units of ulp(x)
-    // lo = d * 2^(E - 52): |d| < 2^29, E - 52 >= DW_EMIN - 52 > -126
+    if ((mh | lw) == 0) return true;
+    const int E = (int)(mh >> 20) - 1023;
+    if (E < DW_EMIN || E >= DW_EMAX) {  // also inf / nan (E = 1024) and subnormals
+        o = make_float2(__int_as_float(0x7FC00000), 0.f);
+        return false;
+    }
+    // magnitude rounded half-up at bit 29 (24 significant bits), low bits cleared
+    const uint32_t lr = lw + (1u << 28);
+    const uint32_t mhr = mh + (lr < lw ? 1u : 0u);
+    const uint32_t lrc = lr & ~((1u << 29) - 1u);
+    const int Er = (int)(mhr >> 20) - 1023;
+    const uint32_t hb = sign | ((uint32_t)(Er + 127) << 23) | (((mhr << 3) | (lrc >> 29)) & 0x7FFFFFu);
+    // x - hi in units of ulp(x): |d| < 2^29, so the low words' difference is exact
+    const int32_t d = (int32_t)(lw - lrc);
     float lo = __fmul_rn(i29_to_float_rn(d), __uint_as_float((uint32_t)(E - 52 + 127) << 23));
     if (sign) lo = -lo;
     o = make_float2(__uint_as_float(hb), lo);
@@ -478,8 +488,7 @@ __device__ __forceinline__ bool split_dw(double xd, float2 &o)
 constexpr int SPLIT_THREADS = 256;
 
 __global__ void __launch_bounds__(SPLIT_THREADS)
-k_split_x(int64_t n, const double *__restrict__ x, float2 *__restrict__ x_dw,
-          unsigned long long *__restrict__ flag, unsigned long long epoch)
+k_split_x(int64_t n, const double *__restrict__ x, float2 *__restrict__ x_dw)
 {
     asm volatile("griddepcontrol.launch_dependents;");
     // launched as a programmatic dependent of the stream's previous kernel:
@@ -487,7 +496,6 @@ k_split_x(int64_t n, const double *__restrict__ x, float2 *__restrict__ x_dw,
     // product of this handle) are free after this wait
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t i = 2 * ((int64_t)blockIdx.x * SPLIT_THREADS + threadIdx.x);
-    if (i == 0) atomicMax(flag, epoch << 1);
     if (i >= n) return;
     const bool two = i + 1 < n;
     double a, b = 0.0;
@@ -500,9 +508,8 @@ k_split_x(int64_t n, const double *__restrict__ x, float2 *__restrict__ x_dw,
         if (two) b = __ldg(x + i + 1);
     }
     float2 o0, o1;
-    bool ok = split_dw(a, o0);
-    if (two) ok = split_dw(b, o1) && ok;
-    if (!ok) atomicMax(flag, (epoch << 1) | 1ull);
+    split_dw(a, o0);  // (NaN, 0) outside the window
+    if (two) split_dw(b, o1);
     if (two)  // x_dw is a device allocation: x_dw + i (i even) is 16-byte aligned
         *reinterpret_cast<float4 *>(x_dw + i) = make_float4(o0.x, o0.y, o1.x, o1.y);
     else
@@ -522,7 +529,8 @@ dw_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restric
         const int32_t *__restrict__ dia_offset, const float2 *__restrict__ dia_dw,
         const int32_t *__restrict__ csr_row_ptr, const int32_t *__restrict__ csr_col,
         const float2 *__restrict__ csr_dw, const float2 *__restrict__ x_dw,
-        double *__restrict__ y)
+        const double *__restrict__ dia_val, const double *__restrict__ csr_val,
+        const double *__restrict__ x, double *__restrict__ y)
 {
     constexpr int V = 2;  // float2 slots per 16-byte load
     constexpr int RW = 32 * V * U;
@@ -657,7 +665,13 @@ dw_tile(int64_t w, int64_t n, int32_t n_b, int32_t tpb, const int32_t *__restric
     for (int u = 0; u < U; u++)
 #pragma unroll
         for (int m = 0; m < V; m++)
-            if (tl[u] + m < rows) y[r0 + tl[u] + m] = dw::f32_to_f64(sh[u][m]) + dw::f32_to_f64(sl[u][m]);
+            if (tl[u] + m < rows) {
+                const int32_t t = tl[u] + m;
+                y[r0 + t] = isnan(sh[u][m])  // read an x outside the window
+                                ? native_row(r0 + t, t, ib, n, n_b, dia_ptr, dia_offset, dia_val,
+                                             csr_row_ptr, csr_col, csr_val, x)
+                                : dw::f32_to_f64(sh[u][m]) + dw::f32_to_f64(sl[u][m]);
+            }
 }
 
 template <int U, int D>
@@ -666,24 +680,18 @@ k_mhdc_spmv_dw(int64_t n, int32_t n_b, int32_t tpb, int64_t n_tiles,
                const int32_t *__restrict__ dia_ptr, const int32_t *__restrict__ dia_offset,
                const float2 *__restrict__ dia_dw, const int32_t *__restrict__ csr_row_ptr,
                const int32_t *__restrict__ csr_col, const float2 *__restrict__ csr_dw,
-               const float2 *__restrict__ x_dw, const unsigned long long *__restrict__ flag,
-               unsigned long long epoch, const double *__restrict__ dia_val,
+               const float2 *__restrict__ x_dw, const double *__restrict__ dia_val,
                const double *__restrict__ csr_val, const double *__restrict__ x,
                double *__restrict__ y)
 {
+    asm volatile("griddepcontrol.launch_dependents;");
+    // launched as a programmatic dependent of k_split_x: its x_dw is complete
+    // and visible after this wait (a no-op for a plain launch)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= n_tiles) return;
-    asm volatile("griddepcontrol.launch_dependents;");
-    // launched as a programmatic dependent of k_split_x: its x_dw and flag
-    // are complete and visible after this wait (a no-op for a plain launch)
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (*flag != (epoch << 1)) {  // x outside the window: native FP64 tile
-        reg_tile<double, U, D, true>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_val, csr_row_ptr,
-                                     csr_col, csr_val, x, y);
-        return;
-    }
     dw_tile<U, D>(w, n, n_b, tpb, dia_ptr, dia_offset, dia_dw, csr_row_ptr, csr_col, csr_dw, x_dw,
-                  y);
+                  dia_val, csr_val, x, y);
 }
 
 
@@ -932,7 +940,6 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
     int64_t tiles = (int64_t)tpb * A->n_blocks;
     const int threads = tiles < 2 * SPMV_WARPS * (int64_t)num_sms() ? 32 : SPMV_THREADS;
     const int64_t grid = (tiles + threads / 32 - 1) / (threads / 32);
-    const unsigned long long epoch = ++A->dw_epoch;
     // programmatic dependent launches: each kernel's CTAs are scheduled while
     // the one before drains and wait in-kernel for its completion
     cudaLaunchAttribute attr[1];
@@ -945,8 +952,7 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
         sc.stream = stream;
         sc.attrs = attr;
         sc.numAttrs = 1;
-        MHDC_CUDA_TRY(cudaLaunchKernelEx(&sc, k_split_x, A->n, (const double *)d_x, A->x_dw,
-                                         A->dw_flag, epoch));
+        MHDC_CUDA_TRY(cudaLaunchKernelEx(&sc, k_split_x, A->n, (const double *)d_x, A->x_dw));
     }
     MHDC_LAUNCH_CHECK("k_split_x");
     cudaLaunchConfig_t cfg = {};
@@ -961,8 +967,7 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
             &cfg, kern, A->n, A->n_b, tpb, tiles, (const int32_t *)A->dia_ptr,
             (const int32_t *)A->dia_offset, (const float2 *)A->dia_dw,
             (const int32_t *)A->csr_row_ptr, (const int32_t *)A->csr_col,
-            (const float2 *)A->csr_dw, (const float2 *)A->x_dw,
-            (const unsigned long long *)A->dw_flag, epoch, (const double *)A->dia_val,
+            (const float2 *)A->csr_dw, (const float2 *)A->x_dw, (const double *)A->dia_val,
             (const double *)A->csr_val, (const double *)d_x, (double *)d_y));
         return MHDC_OK;
     };
@@ -977,10 +982,6 @@ int launch_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y, cudaStream_
     return MHDC_OK;
 }
 
-bool emulation_possible(const mhdc_matrix *A)
-{
-    return A->dw_ok && A->dtype == MHDC_F64 && (A->n_b % 2) == 0;
-}
 
 template <typename VT>
 int launch_checked_typed(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t stream)
@@ -1022,11 +1023,10 @@ int launch_variant(mhdc_matrix *A, int id, const void *d_x, void *d_y, cudaStrea
     } else if (id >= FIRST_DW_VARIANT) {
         if (emulation_possible(A)) {
             if (id < FIRST_TMA_DW_VARIANT) return launch_dw(A, id - FIRST_DW_VARIANT, d_x, d_y, stream);
-            const unsigned long long epoch = ++A->dw_epoch;
             k_split_x<<<split_grid(A->n), SPLIT_THREADS, 0, stream>>>(
-                A->n, (const double *)d_x, A->x_dw, A->dw_flag, epoch);
+                A->n, (const double *)d_x, A->x_dw);
             MHDC_LAUNCH_CHECK("k_split_x");
-            return launch_spmv_tma_dw(A, id - FIRST_TMA_DW_VARIANT, d_x, d_y, epoch, stream);
+            return launch_spmv_tma_dw(A, id - FIRST_TMA_DW_VARIANT, d_x, d_y, stream);
         }
         id = -1;
     }
@@ -1172,13 +1172,56 @@ int launch_stream_bench(int64_t N, const double *A, const double *B, const int32
 // The warp tiles of all matrices form one list (matrix i's tiles start at
 // tile0[i]); warps take chunks of BATCH_CHUNK tiles from a global counter, so
 // matrices of uneven size share the GPU without a launch per matrix.  Each
-// tile runs the register kernel's code (reg_tile, U = 1, D = 2).  The last CTA
-// to finish resets the counters for the next launch (no waits between CTAs).
+// tile runs the register kernel's code (reg_tile, U = 1, D = 2), or for an
+// emulated FP64 matrix the emulated tile (dw_tile<1, 2>, rows that read an x
+// outside the window recomputed natively); the x of the emulated matrices
+// are split by one batched launch before (k_batch_split, a programmatic
+// dependency).  The last CTA to finish resets the counters for the next
+// launch (no waits between CTAs).
 // ---------------------------------------------------------------------------
 namespace mhdc {
 namespace {
 
 constexpr int BATCH_CHUNK = 4;
+
+// Last matrix with key(mats[i]) <= g (keys ascending, key(mats[0]) <= g).
+template <typename Key>
+__device__ __forceinline__ int batch_find(const BatchMat *__restrict__ mats, int32_t m, int64_t g,
+                                          Key key)
+{
+    int lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (key(mats[mid]) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// x_dw of every emulated matrix (element e of the batch's split index space is
+// element e - s0 of the matrix that holds it), one element a thread;
+// out-of-window elements become (NaN, 0) as in k_split_x.
+__global__ void __launch_bounds__(SPLIT_THREADS)
+k_batch_split(int32_t m, const BatchMat *__restrict__ mats, int64_t total,
+              const void *const *__restrict__ xs)
+{
+    asm volatile("griddepcontrol.launch_dependents;");
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // x may be the previous kernel's output
+    for (int64_t e = (int64_t)blockIdx.x * SPLIT_THREADS + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * SPLIT_THREADS) {
+        // matrices without emulation hold no elements: the last matrix with
+        // s0 <= e holds e (an empty or non-emulated one has the s0 of the
+        // matrix after it, so none of them comes after the holder)
+        int i = batch_find(mats, m, e, [](const BatchMat &b) { return b.s0; });
+        while (i > 0 && !mats[i].emu) i--;
+        if (!mats[i].emu) continue;  // not reached: some emulated matrix holds e
+        const BatchMat &M = mats[i];
+        const int64_t j = e - M.s0;
+        float2 o;
+        split_dw(__ldg(static_cast<const double *>(xs[i]) + j), o);
+        M.x_dw[j] = o;
+    }
+}
 
 template <typename VT>
 __global__ void __launch_bounds__(SPMV_THREADS, 4)
@@ -1186,6 +1229,10 @@ k_batch_spmv(int32_t m, const BatchMat *__restrict__ mats, int64_t total_tiles,
              const void *const *__restrict__ xs, void *const *__restrict__ ys,
              unsigned long long *__restrict__ ctr)
 {
+    asm volatile("griddepcontrol.launch_dependents;");
+    // after k_batch_split when the batch has emulated matrices (their x_dw and
+    // window words are complete); a no-op for a plain launch
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long base = 0;
@@ -1195,16 +1242,22 @@ k_batch_spmv(int32_t m, const BatchMat *__restrict__ mats, int64_t total_tiles,
         for (int c = 0; c < BATCH_CHUNK; c++) {
             const int64_t g = (int64_t)base + c;
             if (g >= total_tiles) break;
-            int lo = 0, hi = m - 1;  // last matrix with tile0 <= g
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (mats[mid].tile0 <= g) lo = mid;
-                else hi = mid - 1;
-            }
+            const int lo = batch_find(mats, m, g, [](const BatchMat &b) { return b.tile0; });
             const BatchMat &M = mats[lo];
             const int64_t w = g - M.tile0;
             using X = typename Tr<VT>::X;
             using Y = typename Tr<VT>::Y;
+            if constexpr (sizeof(VT) == 8) {
+                if (M.emu) {
+                    dw_tile<1, 2>(w, M.n, M.n_b, M.tpb, M.dia_ptr, M.dia_offset, M.dia_dw,
+                                  M.csr_row_ptr, M.csr_col, M.csr_dw, M.x_dw,
+                                  static_cast<const double *>(M.dia_val),
+                                  static_cast<const double *>(M.csr_val),
+                                  static_cast<const double *>(xs[lo]),
+                                  static_cast<double *>(ys[lo]));
+                    continue;
+                }
+            }
             if (M.vec)
                 reg_tile<VT, 1, 2, true, true>(w, M.n, M.n_b, M.tpb, M.dia_ptr, M.dia_offset,
                                          static_cast<const VT *>(M.dia_val), M.csr_row_ptr,
@@ -1264,7 +1317,32 @@ int launch_batch(mhdc_batch *B, const void *const *d_xs, void *const *d_ys, cuda
     int64_t tiles = B->total_tiles;
     unsigned long long *ctr = B->d_ctr;
     void *args[] = {&m, (void *)&mats, &tiles, (void *)&d_xs, (void *)&d_ys, (void *)&ctr};
-    MHDC_CUDA_TRY(cudaLaunchKernel(fn, dim3(B->grid), dim3(SPMV_THREADS), args, 0, st));
+    if (B->split_total == 0) {
+        MHDC_CUDA_TRY(cudaLaunchKernel(fn, dim3(B->grid), dim3(SPMV_THREADS), args, 0, st));
+        return MHDC_OK;
+    }
+    // emulated matrices: the batched split, then the product as its
+    // programmatic dependent (both may start while the kernel before drains)
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    const int64_t sblocks = (B->split_total + SPLIT_THREADS - 1) / SPLIT_THREADS;
+    const int64_t scap = (int64_t)num_sms() * 8;
+    cudaLaunchConfig_t sc = {};
+    sc.gridDim = dim3((unsigned)(sblocks < scap ? sblocks : scap));
+    sc.blockDim = dim3(SPLIT_THREADS);
+    sc.stream = st;
+    sc.attrs = attr;
+    sc.numAttrs = 1;
+    MHDC_CUDA_TRY(cudaLaunchKernelEx(&sc, k_batch_split, m, mats, B->split_total, d_xs));
+    MHDC_LAUNCH_CHECK("k_batch_split");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(B->grid);
+    cfg.blockDim = dim3(SPMV_THREADS);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    MHDC_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, args));
     return MHDC_OK;
 }
 

@@ -680,23 +680,23 @@ int num_sms_tma();
 
 // ---------------------------------------------------------------------------
 // FP64 handles, emulated product (variants 13-15): the same pipeline over
-// 8-byte slots.  If the launch's x passed the window check (flag ==
-// epoch << 1) the producer streams the FP32 pairs dia_dw and consumers run the
-// double-word arithmetic of dw_arith.cuh on x_dw; otherwise it streams the
-// FP64 dia_val and consumers run native FP64 FMAs on x.
+// 8-byte slots.  The producer streams the FP32 pairs dia_dw and consumers run
+// the double-word arithmetic of dw_arith.cuh on x_dw; a row whose sum comes
+// out NaN read an x outside the window (marked by the split) and is
+// recomputed with native FP64 arithmetic (native_row).
 // ---------------------------------------------------------------------------
-template <bool EMU, int NCW, int U, int D, int STAGES>
+template <int NCW, int U, int D, int STAGES>
 __device__ __forceinline__ void tma_dw_consumer(
     int64_t n, int32_t n_b, int32_t upb, int64_t n_units, const int32_t *__restrict__ dia_ptr,
-    const int32_t *__restrict__ dia_offset, const int32_t *__restrict__ csr_row_ptr,
-    const int32_t *__restrict__ csr_col, const double *__restrict__ csr_val,
-    const float2 *__restrict__ csr_dw, const double *__restrict__ x,
-    const float2 *__restrict__ x_dw, double *__restrict__ y, uint8_t *ring, uint64_t *full,
-    uint64_t *empty, int *__restrict__ status)
+    const int32_t *__restrict__ dia_offset, const double *__restrict__ dia_val,
+    const int32_t *__restrict__ csr_row_ptr, const int32_t *__restrict__ csr_col,
+    const double *__restrict__ csr_val, const float2 *__restrict__ csr_dw,
+    const double *__restrict__ x, const float2 *__restrict__ x_dw, double *__restrict__ y,
+    uint8_t *ring, uint64_t *full, uint64_t *empty, int *__restrict__ status)
 {
     constexpr int V = 2, NT = NCW * 32, R = NT * U * V, STAGE_BYTES = R * 8;
-    using XT = typename std::conditional<EMU, float2, double>::type;
-    const XT *xs = reinterpret_cast<const XT *>(EMU ? (const void *)x_dw : (const void *)x);
+    using XT = float2;
+    const XT *xs = x_dw;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int stage = 0;
     uint32_t phase = 0;
@@ -711,15 +711,11 @@ __device__ __forceinline__ void tma_dw_consumer(
         int32_t tl[U];
 #pragma unroll
         for (int k = 0; k < U; k++) tl[k] = (k * NT + tid) * V;
-        double acc[U][V];
         float sh[U][V], sl[U][V];
 #pragma unroll
         for (int k = 0; k < U; k++)
 #pragma unroll
-            for (int m = 0; m < V; m++) {
-                acc[k][m] = 0.0;
-                sh[k][m] = sl[k][m] = 0.f;
-            }
+            for (int m = 0; m < V; m++) sh[k][m] = sl[k][m] = 0.f;
         if (csr_row_ptr[r0 + t0] != csr_row_ptr[r0 + t0 + ru]) {
 #pragma unroll
             for (int k = 0; k < U; k++)
@@ -729,14 +725,9 @@ __device__ __forceinline__ void tma_dw_consumer(
                     if (t < ru) {
                         const int64_t i = r0 + t0 + t;
                         const int32_t a = csr_row_ptr[i], b = csr_row_ptr[i + 1];
-                        for (int32_t q = a; q < b; q++) {
-                            if constexpr (EMU)
-                                dw::dw_fma(sh[k][m], sl[k][m], __ldg(csr_dw + q),
-                                           __ldg(x_dw + __ldg(csr_col + q)));
-                            else
-                                acc[k][m] = fma(__ldg(csr_val + q), __ldg(x + __ldg(csr_col + q)),
-                                                acc[k][m]);
-                        }
+                        for (int32_t q = a; q < b; q++)
+                            dw::dw_fma(sh[k][m], sl[k][m], __ldg(csr_dw + q),
+                                       __ldg(x_dw + __ldg(csr_col + q)));
                     }
                 }
         }
@@ -791,17 +782,10 @@ __device__ __forceinline__ void tma_dw_consumer(
 #pragma unroll
                 for (int k = 0; k < U; k++) {
                     const uint4 r = *reinterpret_cast<const uint4 *>(sv + (size_t)tl[k] * 8);
-                    if constexpr (EMU) {
-                        float2 v[V];
-                        memcpy(v, &r, 16);
+                    float2 v[V];
+                    memcpy(v, &r, 16);
 #pragma unroll
-                        for (int m = 0; m < V; m++) dw::dw_fma(sh[k][m], sl[k][m], v[m], xv[d][k][m]);
-                    } else {
-                        double v[V];
-                        memcpy(v, &r, 16);
-#pragma unroll
-                        for (int m = 0; m < V; m++) acc[k][m] = fma(v[m], xv[d][k][m], acc[k][m]);
-                    }
+                    for (int m = 0; m < V; m++) dw::dw_fma(sh[k][m], sl[k][m], v[m], xv[d][k][m]);
                 }
             }
             __syncwarp();
@@ -829,10 +813,11 @@ __device__ __forceinline__ void tma_dw_consumer(
 #pragma unroll
             for (int m = 0; m < V; m++)
                 if (tl[k] + m < ru) {
-                    if constexpr (EMU)
-                        y[r0 + t0 + tl[k] + m] = dw::f32_to_f64(sh[k][m]) + dw::f32_to_f64(sl[k][m]);
-                    else
-                        y[r0 + t0 + tl[k] + m] = acc[k][m];
+                    const int32_t t = t0 + tl[k] + m;
+                    y[r0 + t] = isnan(sh[k][m])  // read an x outside the window
+                                    ? native_row(r0 + t, t, ib, n, n_b, dia_ptr, dia_offset,
+                                                 dia_val, csr_row_ptr, csr_col, csr_val, x)
+                                    : dw::f32_to_f64(sh[k][m]) + dw::f32_to_f64(sl[k][m]);
                 }
     }
 }
@@ -845,13 +830,11 @@ k_mhdc_spmv_tma_dw(int64_t n, int32_t n_b, int32_t upb, int64_t n_units,
                    const int32_t *__restrict__ csr_row_ptr, const int32_t *__restrict__ csr_col,
                    const double *__restrict__ csr_val, const float2 *__restrict__ csr_dw,
                    const double *__restrict__ x, const float2 *__restrict__ x_dw,
-                   double *__restrict__ y, const unsigned long long *__restrict__ flag,
-                   unsigned long long epoch, int *__restrict__ status)
+                   double *__restrict__ y, int *__restrict__ status)
 {
     constexpr int V = 2, NT = NCW * 32, R = NT * U * V, STAGE_BYTES = R * 8;
     extern __shared__ __align__(128) uint8_t ring[];
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
-    const bool emu = *flag == (epoch << 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -863,8 +846,7 @@ k_mhdc_spmv_tma_dw(int64_t n, int32_t n_b, int32_t upb, int64_t n_units,
     __syncthreads();
     if (warp == NCW) {
         if (lane != 0) return;
-        const uint8_t *src = emu ? reinterpret_cast<const uint8_t *>(dia_dw)
-                                 : reinterpret_cast<const uint8_t *>(dia_val);
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(dia_dw);
         int stage = 0;
         uint32_t phase = 0;
         int64_t issued = 0;
@@ -908,19 +890,13 @@ k_mhdc_spmv_tma_dw(int64_t n, int32_t n_b, int32_t upb, int64_t n_units,
         }
         return;
     }
-    if (emu)
-        tma_dw_consumer<true, NCW, U, D, STAGES>(n, n_b, upb, n_units, dia_ptr, dia_offset,
-                                                 csr_row_ptr, csr_col, csr_val, csr_dw, x, x_dw,
-                                                 y, ring, full, empty, status);
-    else
-        tma_dw_consumer<false, NCW, U, D, STAGES>(n, n_b, upb, n_units, dia_ptr, dia_offset,
-                                                  csr_row_ptr, csr_col, csr_val, csr_dw, x, x_dw,
-                                                  y, ring, full, empty, status);
+    tma_dw_consumer<NCW, U, D, STAGES>(n, n_b, upb, n_units, dia_ptr, dia_offset, dia_val,
+                                       csr_row_ptr, csr_col, csr_val, csr_dw, x, x_dw, y, ring,
+                                       full, empty, status);
 }
 
 template <int NCW, int U, int D, int STAGES>
-int launch_tma_dw_cfg(mhdc_matrix *A, const void *d_x, void *d_y, unsigned long long epoch,
-                      cudaStream_t st)
+int launch_tma_dw_cfg(mhdc_matrix *A, const void *d_x, void *d_y, cudaStream_t st)
 {
     constexpr int R = NCW * 32 * U * 2, THREADS = NCW * 32 + 32;
     constexpr size_t SMEM = (size_t)STAGES * R * 8;
@@ -941,7 +917,7 @@ int launch_tma_dw_cfg(mhdc_matrix *A, const void *d_x, void *d_y, unsigned long 
     kern<<<(unsigned)grid, THREADS, SMEM, st>>>(
         A->n, A->n_b, upb, units, A->dia_ptr, A->dia_offset, (const double *)A->dia_val,
         A->dia_dw, A->csr_row_ptr, A->csr_col, (const double *)A->csr_val, A->csr_dw,
-        (const double *)d_x, A->x_dw, (double *)d_y, A->dw_flag, epoch, A->status);
+        (const double *)d_x, A->x_dw, (double *)d_y, A->status);
     MHDC_LAUNCH_CHECK("k_mhdc_spmv_tma_dw");
     return MHDC_OK;
 }
@@ -1038,12 +1014,12 @@ int launch_xw_typed(const mhdc_matrix *A, int shape, const void *d_x, void *d_y,
 }  // namespace
 
 int launch_spmv_tma_dw(mhdc_matrix *A, int shape, const void *d_x, void *d_y,
-                       unsigned long long epoch, cudaStream_t stream)
+                       cudaStream_t stream)
 {
     switch (shape) {
-    case 0: return launch_tma_dw_cfg<8, 1, 2, 16>(A, d_x, d_y, epoch, stream);
-    case 1: return launch_tma_dw_cfg<4, 2, 2, 16>(A, d_x, d_y, epoch, stream);
-    default: return launch_tma_dw_cfg<8, 1, 1, 24>(A, d_x, d_y, epoch, stream);
+    case 0: return launch_tma_dw_cfg<8, 1, 2, 16>(A, d_x, d_y, stream);
+    case 1: return launch_tma_dw_cfg<4, 2, 2, 16>(A, d_x, d_y, stream);
+    default: return launch_tma_dw_cfg<8, 1, 1, 24>(A, d_x, d_y, stream);
     }
 }
 

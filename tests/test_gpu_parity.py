@@ -240,11 +240,17 @@ def test_misaligned_x_gives_identical_result(mh):
             mh.mhdc_spmv(h, xd, y1)
             mh.mhdc_spmv(h, buf[1:], y2)
             assert t.equal(y1, y2), (dt, v)
-        # an x far outside the emulation window sends FP64 variants down the
-        # native path, which also reads the unaligned x
+        # an x far outside the emulation window sends the rows that read it
+        # down the native path, which also reads the unaligned x: those rows
+        # equal native FP64 bit for bit, the others stay within tolerance
         if dt == "f64":
-            buf[1 + A.n // 2] = 1e300
+            j = A.n // 2
+            buf[1 + j] = 1e300
             xal = buf[1:].clone()
+            rows_of = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+            reads_j = t.from_numpy(np.unique(rows_of[A.col == j])).cuda()
+            xh = xal.cpu().numpy()
+            tol = t.from_numpy(oracle.FP64_ROW_TOL * oracle.csr_absrow(A, xh)).cuda()
             for v in mh.EMULATED_VARIANTS:
                 mh.mhdc_set_variant(h, v)
                 y1 = y_empty(A.n, dt)
@@ -255,7 +261,8 @@ def test_misaligned_x_gives_identical_result(mh):
                 mh.mhdc_set_variant(h, -1)
                 y2 = y_empty(A.n, dt)
                 mh.mhdc_spmv(h, buf[1:], y2)
-                assert t.equal(y1, y2), v
+                assert t.equal(y1[reads_j], y2[reads_j]), v
+                assert bool(((y1 - y2).abs() <= 2 * tol).all()), v
         mh.mhdc_check(h)
 
 
@@ -467,6 +474,11 @@ def _native_and_emulated(mh, h, x):
 
 
 def test_emulated_fp64_falls_back_outside_its_window(mh):
+    # An x outside the window is marked NaN by the split, so exactly the rows
+    # that read it (through an entry or a padded slot of its column) come out
+    # NaN in FP32 pairs and are recomputed with native FP64 arithmetic: the
+    # rows holding an entry in that column equal native FP64 bit for bit (NaN
+    # where native has NaN), every other row stays within the FP64 tolerance.
     t = torch()
     A = synth.config_matrix("stencil27_128", scale=0.25)
     h = build(mh, A, 4096, 0.6, "f64")
@@ -476,21 +488,26 @@ def test_emulated_fp64_falls_back_outside_its_window(mh):
     y0, ys = _native_and_emulated(mh, h, t.from_numpy(base).cuda())
     for v, y in zip(mh.EMULATED_VARIANTS, ys):
         assert not t.equal(y, y0), v
+    j = A.n // 3
+    rows_of = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    reads_j = np.unique(rows_of[A.col == j])
+    assert reads_j.size > 1
     for bad in (1e30, -3e19, 1e-20, 2.0 ** -60, float("inf"), float("nan")):
         xb = base.copy()
-        xb[A.n // 3] = bad
+        xb[j] = bad
         xd = t.from_numpy(xb).cuda()
         y0, ys = _native_and_emulated(mh, h, xd)
-        for y in ys:   # the native arithmetic ran: bit-identical, NaN where native has NaN
-            a, b = y0.cpu().numpy(), y.cpu().numpy()
-            assert np.array_equal(np.isnan(a), np.isnan(b)), bad
-            assert np.array_equal(a[~np.isnan(a)], b[~np.isnan(b)]), bad
+        a = y0.cpu().numpy()
+        with np.errstate(invalid="ignore", over="ignore"):
+            tol = oracle.FP64_ROW_TOL * oracle.csr_absrow(A, xb)
+        fin = np.isfinite(a) & np.isfinite(tol)
+        for v, y in zip(mh.EMULATED_VARIANTS, ys):
+            b = y.cpu().numpy()
+            assert np.array_equal(np.isnan(a), np.isnan(b)), (bad, v)
+            assert np.array_equal(a[reads_j], b[reads_j], equal_nan=True), (bad, v)
+            assert np.all(np.abs(a[fin] - b[fin]) <= 2 * tol[fin]), (bad, v)
         mh.mhdc_check(h)
-    # a good x again after the fallbacks: the emulated arithmetic resumes.  Its
-    # rounding differs from native FP64 in some rows of this 32,768-row
-    # matrix, while every fallback above was bit-identical to native, so a
-    # bitwise difference shows which arithmetic ran (the first product of
-    # the test, before any fallback, differs the same way)
+    # a good x again: every row emulated (some rows differ from native FP64)
     xd = t.from_numpy(base).cuda()
     y0, ys = _native_and_emulated(mh, h, xd)
     for v, y in zip(mh.EMULATED_VARIANTS, ys):
@@ -499,6 +516,61 @@ def test_emulated_fp64_falls_back_outside_its_window(mh):
     for v in mh.EMULATED_VARIANTS:
         mh.mhdc_set_variant(h, v)
         check_spmv(mh, h, M, A, base, "f64")
+
+
+def test_emulated_chain_and_graph_replay(mh):
+    # Products whose x is the previous product's y, launched back to back
+    # (the split and the product are programmatic dependent launches, no host
+    # wait between calls), equal the same chain with a device
+    # synchronisation after every product, bit for bit.  So does the chain
+    # captured in a CUDA graph and replayed twice: the window word and the
+    # CTA ticket are left clear by every product, so a replayed product sees
+    # the state a direct call sees.  Three products a chain (an odd count),
+    # one-warp and 8-warp CTAs (the two matrix sizes), every emulated
+    # variant; the first product differs from native FP64 as in the test
+    # above, so the emulated arithmetic ran.
+    t = torch()
+    steps = 3
+    for scale in (0.25, 0.75):
+        A = synth.config_matrix("stencil27_128", scale=scale)
+        h = build(mh, A, 4096, 0.6, "f64")
+        x0 = t.from_numpy(synth.uniform_vector(A.n, 6)).cuda()
+        mh.mhdc_set_variant(h, -1)
+        y_native = y_empty(A.n, "f64")
+        mh.mhdc_spmv(h, x0, y_native)
+        for v in mh.EMULATED_VARIANTS:
+            mh.mhdc_set_variant(h, v)
+
+            def chain(sync):
+                a, b = x0.clone(), t.empty_like(x0)
+                firsts = []
+                for _ in range(steps):
+                    mh.mhdc_spmv(h, a, b)
+                    if sync:
+                        t.cuda.synchronize()
+                        if not firsts:
+                            firsts.append(b.clone())
+                    a, b = b, a
+                t.cuda.synchronize()
+                return a.clone(), (firsts[0] if firsts else None)
+
+            ref, first = chain(True)
+            assert not t.equal(first, y_native), (scale, v)
+            got, _ = chain(False)
+            assert t.equal(got, ref), (scale, v)
+            a, b = x0.clone(), t.empty_like(x0)
+            g = t.cuda.CUDAGraph()
+            with t.cuda.graph(g):
+                mh.mhdc_spmv(h, a, b)
+                mh.mhdc_spmv(h, b, a)
+                mh.mhdc_spmv(h, a, b)
+            for _ in range(2):
+                a.copy_(x0)
+                g.replay()
+                t.cuda.synchronize()
+                assert t.equal(b, ref), (scale, v)
+            mh.mhdc_check(h)
+        h.destroy()
 
 
 def test_emulated_fp64_disabled_by_values_or_row_length(mh):
@@ -645,6 +717,62 @@ def test_batch_matches_oracle_and_graph_replays(mh, dt):
         mh.mhdc_spmv(h, x, yy)
         if h.info["n_b"] % {"f64": 2, "f32": 4, "bf16": 8}[dt] == 0:
             assert t.equal(yy, y)
+    B.destroy()
+
+
+def test_batch_with_emulated_matrices(mh):
+    # An FP64 batch whose even matrices use an emulated variant: their x are
+    # split by one batched launch and their tiles run the FP32-pair
+    # arithmetic.  Each y_i equals its handle's own product bit for bit
+    # (emulated: the variant-10 tile; native: variant 5), directly and from
+    # the graph; with an x outside the window in one emulated matrix, the rows
+    # that read it are native in both.  Every y_i is checked against the
+    # oracle within the FP64 tolerance.
+    t = torch()
+    mats, hs, Ms, xs = _batch_case(mh, "f64", 2)
+    emu = [q % 2 == 0 for q in range(len(hs))]
+    for h, e in zip(hs, emu):
+        mh.mhdc_set_variant(h, mh.FIRST_EMULATED_VARIANT if e else 5)
+        if e:
+            assert h.info["emulated_ok"] == 1
+    B = mh.mhdc_batch_create(hs)
+    xd = [t.from_numpy(x).cuda() for x in xs]
+    ys = [y_empty(A.n, "f64") for A in mats]
+    XP, YP = mh.pointer_array(xd), mh.pointer_array(ys)
+
+    def own(h, x):
+        yy = y_empty(h.n, "f64")
+        mh.mhdc_spmv(h, x, yy)
+        return yy
+
+    for bad in (None, 1e-30):
+        if bad is not None:
+            xs[0][len(xs[0]) // 2] = bad
+            xd[0].copy_(t.from_numpy(xs[0]))
+        mh.mhdc_batch_spmv(B, XP, YP)
+        t.cuda.synchronize()
+        direct = [y.clone() for y in ys]
+        for rep in range(2):
+            for y in ys:
+                y.fill_(float("nan"))
+            mh.mhdc_batch_spmv_graph(B, XP, YP)
+            t.cuda.synchronize()
+            for y, d in zip(ys, direct):
+                assert t.equal(y, d)
+        differs = 0
+        for h, e, x, y, A in zip(hs, emu, xd, ys, mats):
+            mine = own(h, x)
+            if e or h.info["n_b"] % 2 == 0:
+                assert t.equal(mine, y), (h.info["n_b"], e, bad)
+            if e:
+                mh.mhdc_set_variant(h, -1)
+                differs += not t.equal(own(h, x), y)
+                mh.mhdc_set_variant(h, mh.FIRST_EMULATED_VARIANT)
+        assert differs > 0   # the emulated arithmetic ran in some matrix
+        for A, x, y in zip(mats, xs, ys):
+            ref = oracle.csr_spmv(A, x)
+            assert np.all(np.abs(y.cpu().numpy() - ref)
+                          <= oracle.FP64_ROW_TOL * oracle.csr_absrow(A, x))
     B.destroy()
 
 
