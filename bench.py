@@ -556,18 +556,6 @@ def measure_rows(mh, torch, stream, args, H, A, rp, col, val, log):
         tot, mean = time_launches(fn, 30, 3, stream, torch)
         bt[nm_] = {"us": round(mean * 1e3, 1), "gflops": round(gflops(nnz_b, mean / 1e3), 1)}
     B.destroy()
-    # the same batch with every handle on the emulated FP64 tile (variant 10):
-    # one batched split of the 64 x, then the persistent launch
-    for h in hs:
-        mh.mhdc_set_variant(h, 10)
-    B = mh.mhdc_batch_create(hs)
-    em = {"variant": 10}
-    for nm_, fn in (("persistent_launch", lambda: mh.mhdc_batch_spmv(B, XP, YP, stream)),
-                    ("graph_replay", lambda: mh.mhdc_batch_spmv_graph(B, XP, YP, stream))):
-        tot, mean = time_launches(fn, 30, 3, stream, torch)
-        em[nm_] = {"us": round(mean * 1e3, 1), "gflops": round(gflops(nnz_b, mean / 1e3), 1)}
-    bt["emulated_fp64"] = em
-    B.destroy()
     for h in hs:
         h.destroy()
     out["a9_batched_fp64"] = bt

@@ -336,13 +336,10 @@ int mhdc_set_checked(mhdc_handle A, int32_t on);
  *
  * mhdc_batch_create  -- batch of m >= 1 handles of one dtype (host array
  *                       `mats`); the handles must outlive the batch, which
- *                       only references them.  An FP64 handle whose variant
- *                       is emulated (10-15, set before this call) runs the
- *                       emulated arithmetic in the batch (the tile of variant
- *                       10: the bits of its own product with variant 10);
- *                       each launch first splits those x in one kernel, so a
- *                       handle's own products must not overlap a launch of a
- *                       batch holding it.  Synchronous.
+ *                       only references them.  Every matrix runs the native
+ *                       arithmetic of its dtype (the register tile of
+ *                       variants 0-5), whatever its handle's variant.
+ *                       Synchronous.
  * mhdc_batch_spmv    -- one launch on `stream`: d_xs and d_ys are DEVICE arrays
  *                       of m device pointers (x_i: n_i values of the x dtype,
  *                       y_i: n_i values of the y dtype).  Launches of one batch

@@ -332,7 +332,7 @@ int mhdc_batch_create(int32_t m, const mhdc_handle *mats, mhdc_batch_handle *out
         }
     }
     std::vector<BatchMat> h((size_t)m);
-    int64_t tiles = 0, nnz = 0, split = 0;
+    int64_t tiles = 0, nnz = 0;
     for (int32_t i = 0; i < m; i++) {
         const mhdc_matrix *A = mats[i];
         int vec = 0;
@@ -342,13 +342,7 @@ int mhdc_batch_create(int32_t m, const mhdc_handle *mats, mhdc_batch_handle *out
         b.n_b = A->n_b;
         b.tpb = (int32_t)((A->n_b + rw - 1) / rw);
         b.vec = vec;
-        b.emu = A->dtype == MHDC_F64 && A->variant >= FIRST_DW_VARIANT &&
-                A->variant < FIRST_XW_VARIANT && A->dw_prepared && emulation_possible(A);
-        b.s0 = split;
-        b.dia_dw = b.emu ? A->dia_dw : nullptr;
-        b.csr_dw = b.emu ? A->csr_dw : nullptr;
-        b.x_dw = b.emu ? A->x_dw : nullptr;
-        if (b.emu) split += A->n;
+        b.pad = 0;
         b.tile0 = tiles;
         b.dia_ptr = A->dia_ptr;
         b.dia_offset = A->dia_offset;
@@ -364,7 +358,6 @@ int mhdc_batch_create(int32_t m, const mhdc_handle *mats, mhdc_batch_handle *out
     B->dtype = mats[0]->dtype;
     B->total_tiles = tiles;
     B->total_nnz = nnz;
-    B->split_total = split;
     cudaGetDevice(&B->device);
     cudaError_t e = dmalloc((void **)&B->d_mats, sizeof(BatchMat) * (size_t)m);
     if (e == cudaSuccess) e = dmalloc((void **)&B->d_ctr, 2 * sizeof(unsigned long long));

@@ -51,17 +51,11 @@ struct BatchMat {
     int64_t n;
     int64_t tile0;      // first warp tile of this matrix in the batch's tile list
     int32_t n_b, tpb;   // rows per block, warp tiles per block
-    int32_t vec;        // 16-byte value loads possible (n_b % V == 0)
-    int32_t emu;        // emulated FP64 (the handle's variant was 10-15 at creation)
+    int32_t vec, pad;   // 16-byte value loads possible (n_b % V == 0)
     const int32_t *dia_ptr, *dia_offset;
     const void *dia_val;
     const int32_t *csr_row_ptr, *csr_col;
     const void *csr_val;
-    // emulated matrices only: the handle's FP32-pair arrays, and the first
-    // element of this x in the batched split's index space
-    int64_t s0;
-    const float2 *dia_dw, *csr_dw;
-    float2 *x_dw;
 };
 
 // A batch of handles (same dtype) for mhdc_batch_spmv; it does not own them.
@@ -72,7 +66,6 @@ struct mhdc_batch {
     unsigned long long *d_ctr = nullptr;  // [next tile, finished CTAs]
     int64_t total_tiles = 0;
     int64_t total_nnz = 0;
-    int64_t split_total = 0;              // x elements split per launch (emulated matrices)
     int grid = 0;
     cudaStream_t cap_stream = nullptr;    // stream the graph is captured on
     cudaGraphExec_t graph = nullptr;

@@ -1172,55 +1172,24 @@ int launch_stream_bench(int64_t N, const double *A, const double *B, const int32
 // The warp tiles of all matrices form one list (matrix i's tiles start at
 // tile0[i]); warps take chunks of BATCH_CHUNK tiles from a global counter, so
 // matrices of uneven size share the GPU without a launch per matrix.  Each
-// tile runs the register kernel's code (reg_tile, U = 1, D = 2), or for an
-// emulated FP64 matrix the emulated tile (dw_tile<1, 2>, rows that read an x
-// outside the window recomputed natively); the x of the emulated matrices
-// are split by one batched launch before (k_batch_split, a programmatic
-// dependency).  The last CTA to finish resets the counters for the next
-// launch (no waits between CTAs).
+// tile runs the register kernel's code (reg_tile, U = 1, D = 2).  The last CTA
+// to finish resets the counters for the next launch (no waits between CTAs).
 // ---------------------------------------------------------------------------
 namespace mhdc {
 namespace {
 
 constexpr int BATCH_CHUNK = 4;
 
-// Last matrix with key(mats[i]) <= g (keys ascending, key(mats[0]) <= g).
-template <typename Key>
-__device__ __forceinline__ int batch_find(const BatchMat *__restrict__ mats, int32_t m, int64_t g,
-                                          Key key)
+// Last matrix whose first tile is <= g (tile0 ascending, mats[0].tile0 = 0).
+__device__ __forceinline__ int batch_find(const BatchMat *__restrict__ mats, int32_t m, int64_t g)
 {
     int lo = 0, hi = m - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (key(mats[mid]) <= g) lo = mid;
+        if (mats[mid].tile0 <= g) lo = mid;
         else hi = mid - 1;
     }
     return lo;
-}
-
-// x_dw of every emulated matrix (element e of the batch's split index space is
-// element e - s0 of the matrix that holds it), one element a thread;
-// out-of-window elements become (NaN, 0) as in k_split_x.
-__global__ void __launch_bounds__(SPLIT_THREADS)
-k_batch_split(int32_t m, const BatchMat *__restrict__ mats, int64_t total,
-              const void *const *__restrict__ xs)
-{
-    asm volatile("griddepcontrol.launch_dependents;");
-    asm volatile("griddepcontrol.wait;" ::: "memory");  // x may be the previous kernel's output
-    for (int64_t e = (int64_t)blockIdx.x * SPLIT_THREADS + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * SPLIT_THREADS) {
-        // matrices without emulation hold no elements: the last matrix with
-        // s0 <= e holds e (an empty or non-emulated one has the s0 of the
-        // matrix after it, so none of them comes after the holder)
-        int i = batch_find(mats, m, e, [](const BatchMat &b) { return b.s0; });
-        while (i > 0 && !mats[i].emu) i--;
-        if (!mats[i].emu) continue;  // not reached: some emulated matrix holds e
-        const BatchMat &M = mats[i];
-        const int64_t j = e - M.s0;
-        float2 o;
-        split_dw(__ldg(static_cast<const double *>(xs[i]) + j), o);
-        M.x_dw[j] = o;
-    }
 }
 
 template <typename VT>
@@ -1229,10 +1198,6 @@ k_batch_spmv(int32_t m, const BatchMat *__restrict__ mats, int64_t total_tiles,
              const void *const *__restrict__ xs, void *const *__restrict__ ys,
              unsigned long long *__restrict__ ctr)
 {
-    asm volatile("griddepcontrol.launch_dependents;");
-    // after k_batch_split when the batch has emulated matrices (their x_dw and
-    // window words are complete); a no-op for a plain launch
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long base = 0;
@@ -1242,22 +1207,11 @@ k_batch_spmv(int32_t m, const BatchMat *__restrict__ mats, int64_t total_tiles,
         for (int c = 0; c < BATCH_CHUNK; c++) {
             const int64_t g = (int64_t)base + c;
             if (g >= total_tiles) break;
-            const int lo = batch_find(mats, m, g, [](const BatchMat &b) { return b.tile0; });
+            const int lo = batch_find(mats, m, g);
             const BatchMat &M = mats[lo];
             const int64_t w = g - M.tile0;
             using X = typename Tr<VT>::X;
             using Y = typename Tr<VT>::Y;
-            if constexpr (sizeof(VT) == 8) {
-                if (M.emu) {
-                    dw_tile<1, 2>(w, M.n, M.n_b, M.tpb, M.dia_ptr, M.dia_offset, M.dia_dw,
-                                  M.csr_row_ptr, M.csr_col, M.csr_dw, M.x_dw,
-                                  static_cast<const double *>(M.dia_val),
-                                  static_cast<const double *>(M.csr_val),
-                                  static_cast<const double *>(xs[lo]),
-                                  static_cast<double *>(ys[lo]));
-                    continue;
-                }
-            }
             if (M.vec)
                 reg_tile<VT, 1, 2, true, true>(w, M.n, M.n_b, M.tpb, M.dia_ptr, M.dia_offset,
                                          static_cast<const VT *>(M.dia_val), M.csr_row_ptr,
@@ -1317,32 +1271,7 @@ int launch_batch(mhdc_batch *B, const void *const *d_xs, void *const *d_ys, cuda
     int64_t tiles = B->total_tiles;
     unsigned long long *ctr = B->d_ctr;
     void *args[] = {&m, (void *)&mats, &tiles, (void *)&d_xs, (void *)&d_ys, (void *)&ctr};
-    if (B->split_total == 0) {
-        MHDC_CUDA_TRY(cudaLaunchKernel(fn, dim3(B->grid), dim3(SPMV_THREADS), args, 0, st));
-        return MHDC_OK;
-    }
-    // emulated matrices: the batched split, then the product as its
-    // programmatic dependent (both may start while the kernel before drains)
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    const int64_t sblocks = (B->split_total + SPLIT_THREADS - 1) / SPLIT_THREADS;
-    const int64_t scap = (int64_t)num_sms() * 8;
-    cudaLaunchConfig_t sc = {};
-    sc.gridDim = dim3((unsigned)(sblocks < scap ? sblocks : scap));
-    sc.blockDim = dim3(SPLIT_THREADS);
-    sc.stream = st;
-    sc.attrs = attr;
-    sc.numAttrs = 1;
-    MHDC_CUDA_TRY(cudaLaunchKernelEx(&sc, k_batch_split, m, mats, B->split_total, d_xs));
-    MHDC_LAUNCH_CHECK("k_batch_split");
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(B->grid);
-    cfg.blockDim = dim3(SPMV_THREADS);
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    MHDC_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, args));
+    MHDC_CUDA_TRY(cudaLaunchKernel(fn, dim3(B->grid), dim3(SPMV_THREADS), args, 0, st));
     return MHDC_OK;
 }
 

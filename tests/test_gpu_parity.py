@@ -720,62 +720,6 @@ def test_batch_matches_oracle_and_graph_replays(mh, dt):
     B.destroy()
 
 
-def test_batch_with_emulated_matrices(mh):
-    # An FP64 batch whose even matrices use an emulated variant: their x are
-    # split by one batched launch and their tiles run the FP32-pair
-    # arithmetic.  Each y_i equals its handle's own product bit for bit
-    # (emulated: the variant-10 tile; native: variant 5), directly and from
-    # the graph; with an x outside the window in one emulated matrix, the rows
-    # that read it are native in both.  Every y_i is checked against the
-    # oracle within the FP64 tolerance.
-    t = torch()
-    mats, hs, Ms, xs = _batch_case(mh, "f64", 2)
-    emu = [q % 2 == 0 for q in range(len(hs))]
-    for h, e in zip(hs, emu):
-        mh.mhdc_set_variant(h, mh.FIRST_EMULATED_VARIANT if e else 5)
-        if e:
-            assert h.info["emulated_ok"] == 1
-    B = mh.mhdc_batch_create(hs)
-    xd = [t.from_numpy(x).cuda() for x in xs]
-    ys = [y_empty(A.n, "f64") for A in mats]
-    XP, YP = mh.pointer_array(xd), mh.pointer_array(ys)
-
-    def own(h, x):
-        yy = y_empty(h.n, "f64")
-        mh.mhdc_spmv(h, x, yy)
-        return yy
-
-    for bad in (None, 1e-30):
-        if bad is not None:
-            xs[0][len(xs[0]) // 2] = bad
-            xd[0].copy_(t.from_numpy(xs[0]))
-        mh.mhdc_batch_spmv(B, XP, YP)
-        t.cuda.synchronize()
-        direct = [y.clone() for y in ys]
-        for rep in range(2):
-            for y in ys:
-                y.fill_(float("nan"))
-            mh.mhdc_batch_spmv_graph(B, XP, YP)
-            t.cuda.synchronize()
-            for y, d in zip(ys, direct):
-                assert t.equal(y, d)
-        differs = 0
-        for h, e, x, y, A in zip(hs, emu, xd, ys, mats):
-            mine = own(h, x)
-            if e or h.info["n_b"] % 2 == 0:
-                assert t.equal(mine, y), (h.info["n_b"], e, bad)
-            if e:
-                mh.mhdc_set_variant(h, -1)
-                differs += not t.equal(own(h, x), y)
-                mh.mhdc_set_variant(h, mh.FIRST_EMULATED_VARIANT)
-        assert differs > 0   # the emulated arithmetic ran in some matrix
-        for A, x, y in zip(mats, xs, ys):
-            ref = oracle.csr_spmv(A, x)
-            assert np.all(np.abs(y.cpu().numpy() - ref)
-                          <= oracle.FP64_ROW_TOL * oracle.csr_absrow(A, x))
-    B.destroy()
-
-
 def test_batch_64_stencils_full_size(mh):
     # 64 seeded 7-/27-point stencils, grid edges uniform in [16, 96], FP64
     t = torch()
