@@ -481,11 +481,14 @@ __device__ __forceinline__ bool split_dw(double xd, float2 &o)
     return true;
 }
 
-// Two elements a thread (one 16-byte load of x where x is 16-byte aligned,
-// one 16-byte store into x_dw).  The product launched after it may start its
-// CTAs at once (griddepcontrol.launch_dependents); they wait for this grid's
-// completion and memory before reading x_dw or the flag.
+// Pairs of elements (one 16-byte load of x where x is 16-byte aligned, one
+// 16-byte store into x_dw), consecutive threads on consecutive pairs.  The
+// product launched after it may start its CTAs at once
+// (griddepcontrol.launch_dependents); they wait for this grid's completion
+// and memory before reading x_dw.
 constexpr int SPLIT_THREADS = 256;
+
+constexpr int SPLIT_EPT = 4;  // elements a thread, in pairs (2 and 8 measured slower)
 
 __global__ void __launch_bounds__(SPLIT_THREADS)
 k_split_x(int64_t n, const double *__restrict__ x, float2 *__restrict__ x_dw)
@@ -495,30 +498,38 @@ k_split_x(int64_t n, const double *__restrict__ x, float2 *__restrict__ x_dw)
     // x (possibly that kernel's output) and x_dw (read by the previous
     // product of this handle) are free after this wait
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int64_t i = 2 * ((int64_t)blockIdx.x * SPLIT_THREADS + threadIdx.x);
-    if (i >= n) return;
-    const bool two = i + 1 < n;
-    double a, b = 0.0;
-    if (two && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
-        const double2 v = __ldg(reinterpret_cast<const double2 *>(x + i));
-        a = v.x;
-        b = v.y;
-    } else {
-        a = __ldg(x + i);
-        if (two) b = __ldg(x + i + 1);
+    const int64_t base = (int64_t)blockIdx.x * SPLIT_THREADS * SPLIT_EPT;
+    const bool al = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+#pragma unroll
+    for (int q = 0; q < SPLIT_EPT / 2; q++) {
+        // pair q of the thread: consecutive threads take consecutive pairs
+        const int64_t i = base + 2 * ((int64_t)q * SPLIT_THREADS + threadIdx.x);
+        if (i >= n) break;
+        const bool two = i + 1 < n;
+        double a, b = 0.0;
+        if (two && al) {
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(x + i));
+            a = v.x;
+            b = v.y;
+        } else {
+            a = __ldg(x + i);
+            if (two) b = __ldg(x + i + 1);
+        }
+        float2 o0, o1;
+        split_dw(a, o0);
+        if (two) {
+            split_dw(b, o1);
+            *reinterpret_cast<float4 *>(x_dw + i) = make_float4(o0.x, o0.y, o1.x, o1.y);
+        } else {
+            x_dw[i] = o0;
+        }
     }
-    float2 o0, o1;
-    split_dw(a, o0);  // (NaN, 0) outside the window
-    if (two) split_dw(b, o1);
-    if (two)  // x_dw is a device allocation: x_dw + i (i even) is 16-byte aligned
-        *reinterpret_cast<float4 *>(x_dw + i) = make_float4(o0.x, o0.y, o1.x, o1.y);
-    else
-        x_dw[i] = o0;
 }
 
 inline unsigned split_grid(int64_t n)
 {
-    return (unsigned)(((n + 1) / 2 + SPLIT_THREADS - 1) / SPLIT_THREADS);
+    const int64_t per = (int64_t)SPLIT_THREADS * SPLIT_EPT;
+    return (unsigned)((n + per - 1) / per);
 }
 
 // One warp tile of the emulated product: the rows and tile geometry of
