@@ -153,7 +153,10 @@ int mhdc_build_dia(int64_t n, int32_t nd, const int32_t *d_offset, const double 
  * computes what a direct call computes, for every variant).  Products on one
  * stream may start their launches while the previous kernel drains, but each
  * reads its x only after the stream's earlier work has completed (y of one
- * call may be x of the next).
+ * call may be x of the next).  Products of one handle must not overlap on
+ * the GPU (issue them on one stream): the emulated variants split x into a
+ * buffer of the handle, and a matrix whose CSR remainder holds 5 % or more
+ * of the nonzeros hands its row tiles out through a counter of the handle.
  */
 int mhdc_spmv(mhdc_handle A, const void *d_x, void *d_y, void *stream);
 

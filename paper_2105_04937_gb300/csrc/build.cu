@@ -1006,6 +1006,7 @@ void free_matrix(mhdc_matrix *A)
     if (A->as_comp) cudaStreamDestroy(A->as_comp);
     if (A->as_out) cudaStreamDestroy(A->as_out);
     dfree(A->status);
+    dfree(A->sched);
     dfree(A->dia_dw);
     dfree(A->csr_dw);
     dfree(A->x_dw);
@@ -1125,6 +1126,8 @@ static int build_into(mhdc_matrix *A, const int32_t *rp, const int32_t *col, con
     const int64_t n = A->n;
     RC(dalloc_raw((void **)&A->status, sizeof(int)));
     MHDC_CUDA_TRY(cudaMemsetAsync(A->status, 0, sizeof(int), st));
+    RC(dalloc_raw((void **)&A->sched, 2 * sizeof(unsigned long long)));
+    MHDC_CUDA_TRY(cudaMemsetAsync(A->sched, 0, 2 * sizeof(unsigned long long), st));
     if (n == 0) {
         RC(dalloc_raw((void **)&A->dia_ptr, sizeof(int32_t)));
         RC(dalloc_raw((void **)&A->csr_row_ptr, sizeof(int32_t)));
@@ -1413,6 +1416,8 @@ int build_dia_into(mhdc_matrix *A, int32_t nd, const int32_t *off, const double 
     const int64_t n = A->n, nb = A->n_blocks;
     RC(dalloc_raw((void **)&A->status, sizeof(int)));
     MHDC_CUDA_TRY(cudaMemsetAsync(A->status, 0, sizeof(int), st));
+    RC(dalloc_raw((void **)&A->sched, 2 * sizeof(unsigned long long)));
+    MHDC_CUDA_TRY(cudaMemsetAsync(A->sched, 0, 2 * sizeof(unsigned long long), st));
     Buf err, cnt, keep, sel_cnt, scr, total;
     RC(dalloc(err, sizeof(int), st));
     MHDC_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), st));

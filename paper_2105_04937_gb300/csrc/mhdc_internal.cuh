@@ -37,6 +37,8 @@ struct mhdc_matrix {
     int spmm_variant = -1;           // SpMM tile shape (-1: default)
     int *status = nullptr;           // device word: bit 0 = a bounded wait gave up,
                                      // bit 1 = a bounds check of a checked product failed
+    unsigned long long *sched = nullptr;  // [2] next tile, finished CTAs of a product
+                                          // with persistent tile scheduling (zero between)
     bool checked = false;            // products run the bounds-checked kernel
     // FP64 handles: values split into FP32 (hi, lo) pairs for the emulated product
     float2 *dia_dw = nullptr;        // [P * n_b]

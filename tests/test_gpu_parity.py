@@ -395,6 +395,47 @@ def test_every_variant_is_bit_identical_and_tune_picks_one(mh):
         mh.mhdc_set_variant(h, mh.MHDC_NUM_VARIANTS)
 
 
+def test_persistent_tiles_on_a_remainder_heavy_matrix(mh):
+    # A matrix whose CSR remainder holds 21 % of the nonzeros (enough 8-warp
+    # CTAs) runs its one-vector tiles (variants 0 and 5, and the emulated 10
+    # and 11) with persistent tile scheduling: the same bits as the tiles that
+    # take one tile a warp (variants 1-4, 6-9; emulated 12), launch after
+    # launch (the tile counter is cleared by each launch), and within the
+    # oracle's bound.
+    t = torch()
+    A = synth.config_matrix("scattered_4m", 1 / 4)
+    x = synth.loguniform_vector(A.n, 2)
+    for dt in DTYPES:
+        h, M = check_build(mh, A, 2048, 0.6, dt)
+        assert M["nnz_rem"] * 20 >= A.nnz
+        xd, _ = x_device(x, dt)
+        ref = None
+        for v in mh.NATIVE_VARIANTS:
+            mh.mhdc_set_variant(h, v)
+            for rep in range(3):
+                y = y_empty(A.n, dt)
+                mh.mhdc_spmv(h, xd, y)
+                if ref is None:
+                    ref = y
+                assert t.equal(y, ref), (dt, v, rep)
+        mh.mhdc_set_variant(h, 5)
+        check_spmv(mh, h, M, A, x, dt)
+        if dt == "f64":
+            ys = []
+            for v in (10, 11, 12):
+                mh.mhdc_set_variant(h, v)
+                for rep in range(3):
+                    y = y_empty(A.n, dt)
+                    mh.mhdc_spmv(h, xd, y)
+                    ys.append(y)
+            for y in ys[1:]:
+                assert t.equal(y, ys[0])
+            mh.mhdc_set_variant(h, 11)
+            check_spmv(mh, h, M, A, x, dt)
+        mh.mhdc_check(h)
+        h.destroy()
+
+
 def test_read_bench_xor(mh):
     t = torch()
     N = (1 << 22) + 6
