@@ -268,7 +268,9 @@ int mhdc_stats(mhdc_handle A, double *alpha, double *beta, int64_t *P, int64_t *
 /*
  * Tile shapes of the M-HDC product (no counterpart in the paper, whose kernel
  * is a CPU loop nest): variants 0-5 load dia_val into registers (a warp owns
- * 32 x 16 B x U rows and loads D diagonals before accumulating); variants 6-9
+ * 32 x 16 B x U rows and loads D diagonals before accumulating; a matrix too
+ * small to fill the GPU with such tiles runs 32-row tiles of one row a lane
+ * instead, whatever the variant, with the same sums); variants 6-9
  * stream dia_val through shared memory with TMA bulk copies (one producer
  * warp, several consumer warps, an mbarrier ring; they need n_b * value size
  * to be a multiple of 16 bytes, else they run variant -1).  Variants 0-9
